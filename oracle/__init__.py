@@ -1,0 +1,11 @@
+"""CPU oracle for epsilon-relative Gaussian summation.
+
+TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's
+CPU-baseline / reference leg may import anything from this package.  It shares
+no code with the CUDA path (paper_1206_6857_gb300) and never imports it.
+
+Modules:
+  exhaustive  -- FP64 compensated exhaustive sum (the definition, Section 1)
+  series      -- FP64 multi-index Hermite/Taylor algebra (Sections 2-4)
+  lscv        -- least-squares cross-validation score from exact sums (Section 7)
+"""
