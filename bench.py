@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Benchmark: effective kernel evaluations per second (M*N*#h / wall time) of
+the epsilon-relative Gaussian summation on the D=3 bandwidth-sweep workload
+(1e6 monochromatic FP32 points from a 16-component anisotropic mixture plus 5%
+uniform background, 16 log-spaced bandwidths from 1e-3 to 1 times the data
+diameter, eps = 1e-2).
+
+One step = one pass of the whole path over the workload, inputs resident in
+HBM: `--mode sum` (default) runs gs_sum with eps=1e-2 (tree build, frontier,
+series, base case, downward pass); `--mode exhaustive` runs the exhaustive
+sum (eps=0) instead.  The L2 cache is flushed before every timed step (inputs
+are 12 MB, smaller than L2).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded query sample of the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective kernel evals/s (M*N*#h / wall time) at rel. err eps vs GPU exhaustive"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--mode", default="exhaustive", choices=["sum", "exhaustive"])
+    ap.add_argument("--scale", type=float, default=1.0, help="workload size factor (1 = full)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(scale):
+    from workloads import synth
+    return synth.config2(scale)
+
+
+def wl_config(wl, mode, eps):
+    return {"workload": "kde_sweep_d3_n%d_mono_16h" % wl.N, "M": wl.M, "N": wl.N, "D": wl.D,
+            "nh": int(wl.h.size), "eps": eps, "mode": mode, "leaf_size": wl.leaf_size,
+            "h_range_x_diameter": [1e-3, 1.0], "diameter": round(wl.diameter, 6),
+            "input_dtype": "f32", "l2": "flushed before every timed step (256 MB write)",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = (bus_id or "").lower()
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        self.proc = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if self.bus_id:
+            mine = [r for r in rows if self.bus_id.endswith(r[1].lower()[-12:]) or r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[6 + k] and "Not" not in r[6 + k]})
+        load = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": float(np.median(load)) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(wl, nq, seed=0):
+    from oracle import exhaustive as oracle_ex
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(wl.M, nq, replace=False))
+    t0 = time.perf_counter()
+    oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, wl.h)
+    dt = time.perf_counter() - t0
+    return nq * wl.N * wl.h.size / dt, dt, oracle_ex.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args.scale)
+    from oracle import build as ob
+    ob.build()
+    nq = max(1, int(200 * min(1.0, 1.0 / args.scale)))   # ~3e9 evals per step at full size
+    for _ in range(args.warmup):
+        oracle_sample_rate(wl, max(1, nq // 8), seed=99)
+    rates, secs = [], []
+    for k in range(args.steps):
+        r, dt, cores = oracle_sample_rate(wl, nq, seed=k)
+        rates.append(r)
+        secs.append(dt)
+    value = float(np.mean(rates))
+    sample = "%d seeded queries x all %d refs x %d bandwidths per step" % (nq, wl.N, wl.h.size)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": wl_config(wl, "oracle_exhaustive", 0.0),
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1206_6857_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel, sha):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if e and e.get("src_sha") == sha:
+        return e.get("bytes_per_launch")
+    return None
+
+
+def run_gs(args):
+    import torch
+
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1206_6857_gb300 import build as gbuild
+    from paper_1206_6857_gb300 import gs
+    if rank == 0:
+        gbuild.build()
+    if world > 1:
+        dist.barrier()
+    gs.load()
+
+    wl = workload(args.scale)
+    eps = 0.0 if args.mode == "exhaustive" else wl.eps
+    dev = torch.device("cuda", local)
+    tq = torch.from_numpy(wl.queries).to(dev)
+    tw = torch.from_numpy(wl.weights).to(dev)
+    out = torch.empty((wl.M, wl.h.size), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(stats=None):
+        gs.gs_sum(tq, tq, tw, wl.h, eps, out=out, stream=stream, stats=stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    sampler = ClockSampler(bus)
+    sampler.start()
+    time.sleep(0.3)
+    evs = []
+    stats_list = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        st = gs.gs_stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(st)
+        e1.record(stream)
+        evs.append((e0, e1))
+        stats_list.append(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = float(sum(a.elapsed_time(b) for a, b in evs)) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    units = float(wl.M) * wl.N * wl.h.size          # kernel evaluations one step stands for
+    value = units * world / (ms / 1e3)
+    base_ms = float(np.mean([s.ms_phase[gs.GS_PH_BASE] / max(1, s.launches_base) for s in stats_list]))
+    evals_base = float(np.mean([s.point_pairs_base / max(1, s.launches_base) for s in stats_list]))
+    launches = int(np.mean([s.launches for s in stats_list]))
+
+    # roofline: the base-case / exhaustive kernel is bound by the MUFU ex2 rate
+    # (one ex2 per term); peak = measured ex2 lanes/SM/clk x SMs x SM clock
+    ex2_rate, ffma_rate = gs.gs_probe_rates()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = ex2_rate * props.multi_processor_count * sm_mhz * 1e6 / 1e12
+    achieved = evals_base / (base_ms / 1e3) / 1e12
+    kname = "k_exhaustive" if args.mode == "exhaustive" else "k_basecase"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
+            "frac": achieved / peak if peak else None,
+            "traffic": load_traffic(kname, source_sha()),
+            "kernel": kname, "peak_basis": "measured %.1f ex2 lanes/SM/clk x %d SMs x %.0f MHz (median SM clock under load)"
+            % (ex2_rate, props.multi_processor_count, sm_mhz),
+            "ffma_lanes_per_sm_clk": ffma_rate, "kernel_ms_per_launch": base_ms}
+
+    # end to end: host (pinned) buffers through the C-ABI host entry point
+    e2e = None
+    if not args.no_e2e:
+        hq = torch.from_numpy(wl.queries).pin_memory().numpy()
+        hw = torch.from_numpy(wl.weights).pin_memory().numpy()
+        hout = torch.empty((wl.M, wl.h.size), dtype=torch.float64).pin_memory().numpy()
+        gs.gs_sum_host(hq, hq, hw, wl.h, eps, out=hout)
+        torch.cuda.synchronize()
+        n_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            gs.gs_sum_host(hq, hq, hw, wl.h, eps, out=hout)
+        dt = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": int(hq.nbytes + hw.nbytes),
+               "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import build as ob
+        ob.build()
+        nq = max(1, int(400 * min(1.0, 1.0 / args.scale)))
+        r, dt, cores = oracle_sample_rate(wl, nq)
+        cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": "%d seeded queries x all %d refs x %d bandwidths (%.1f s)" % (nq, wl.N, wl.h.size, dt)}
+
+    if rank == 0:
+        s0 = stats_list[-1]
+        line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": wl_config(wl, args.mode, eps), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": launches * args.steps,
+                "stats": {k: v for k, v in s0.as_dict().items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gs(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * gs.h -- C ABI of the GB300 epsilon-relative Gaussian summation library.
+ *
+ * The library computes, for M query points x_q, N weighted reference points
+ * x_r (weights w_r > 0) in D dimensions and nh bandwidths h_j,
+ *
+ *     G(x_q; h_j) = sum_{r=1..N} w_r exp(-||x_q - x_r||^2 / (2 h_j^2))
+ *
+ * (Lee & Gray, "Faster Gaussian Summation: Theory and Experiment", Section 1),
+ * either exhaustively (eps == 0) or by the dual-tree method of Sections 5-6
+ * with every result within relative error eps of the exact sum.
+ *
+ * Conventions shared by every entry point
+ *   - Point arrays are row-major (point-major): element (i, d) at i*D + d,
+ *     float (GS_F32) or double (GS_F64) as the dtype argument says.
+ *   - Unless an argument says "host", every array pointer is DEVICE memory on
+ *     the current CUDA device, owned by the caller, and must stay valid until
+ *     the call returns.  The library never frees caller memory.
+ *   - Bandwidth lists h and scalars are HOST values.
+ *   - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Work is enqueued on that stream; each call synchronises with
+ *     the stream once at its end to read the device status word, so outputs
+ *     are ready when the call returns GS_OK.
+ *   - Scratch memory is taken with cudaMallocAsync on the stream and returned
+ *     before the call returns.
+ *   - Return value: GS_OK (0) or one of the negative GS_ERR_* codes below; a
+ *     short description of the last error is available from gs_last_error().
+ *     No C++ exception crosses this boundary.  On error the contents of out
+ *     are unspecified.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GS_OK               0
+#define GS_ERR_ARG         -1   /* bad size, pointer, dtype, h <= 0, eps outside [0,1) ... */
+#define GS_ERR_WEIGHT      -2   /* a weight <= 0 (Section 1 requires w_r > 0)              */
+#define GS_ERR_NONFINITE   -3   /* a coordinate or weight is NaN or infinite               */
+#define GS_ERR_OOM         -4   /* device scratch allocation failed                        */
+#define GS_ERR_CAPACITY    -5   /* a device work list outgrew its capacity (see gs_opts)   */
+#define GS_ERR_TIMEOUT     -6   /* a bounded device wait gave up                           */
+#define GS_ERR_CUDA        -7   /* a CUDA runtime call or kernel launch failed             */
+#define GS_ERR_UNSUPPORTED -8   /* valid request this build does not implement             */
+
+/* ---- element types ---------------------------------------------------- */
+#define GS_F32 0
+#define GS_F64 1
+
+/* ---- traversal method selectors (gs_opts.selector) --------------------- */
+#define GS_SEL_RULE        0    /* FD, then the cheapest certified series method (Fig. 6)  */
+#define GS_SEL_MLP         1    /* learned ordering of the same certified choices          */
+#define GS_SEL_FD_ONLY     2    /* finite-difference pruning only (DFD / DFDO)             */
+#define GS_SEL_EXHAUSTIVE  3    /* no pruning: every pair summed exactly                   */
+
+/* Tuning and behaviour switches.  Zero-initialised fields take defaults, so
+ * `gs_opts o = {0};` (or a NULL pointer) is the default configuration. */
+typedef struct gs_opts {
+    int32_t leaf_size;      /* kd-tree leaf capacity L; 0 -> 32                          */
+    int32_t plimit;         /* highest series order PLIMIT; 0 -> Section 6 table by D   */
+    int32_t selector;       /* GS_SEL_*                                                  */
+    int32_t no_tokens;      /* 1 disables the W_T token scheme (plain Theorem 2 rule)   */
+    int32_t floor_log2;     /* relative floor: results are certified to
+                               |G~ - G| <= eps * max(G, 2^floor_log2 * W), W = sum w;
+                               0 -> -40                                                 */
+    int32_t reserved0;
+    int64_t pair_capacity;  /* frontier / work-list capacity in pairs; 0 -> automatic  */
+    int64_t reserved[4];
+} gs_opts;
+
+/* Phases timed into gs_stats.ms_phase (CUDA events on the call's stream). */
+#define GS_PH_INGEST    0   /* input checks and packing                              */
+#define GS_PH_TREE      1   /* kd-tree build, node statistics, moments (a2, a3)      */
+#define GS_PH_FRONTIER  2   /* node-pair frontier iterations (a4)                    */
+#define GS_PH_SERIES    3   /* DH / DL / H2L kernels (a5-a7)                         */
+#define GS_PH_BASE      4   /* exhaustive or leaf-leaf base-case kernel (a8, a14)    */
+#define GS_PH_DOWN      5   /* downward pass and output (a9)                         */
+#define GS_PH_OTHER     6   /* everything else (e.g. LSCV reduction)                 */
+#define GS_NPHASE       8
+
+/* Per-call counters (host struct filled by the call when non-NULL; timing
+ * events are only recorded when it is non-NULL). */
+typedef struct gs_stats {
+    int64_t pairs_fd;        /* node pairs pruned by finite differences                 */
+    int64_t pairs_dh;        /* ... by direct Hermite evaluation (Lemma 4)              */
+    int64_t pairs_dl;        /* ... by direct local accumulation (Lemma 5)              */
+    int64_t pairs_h2l;       /* ... by Hermite-to-local translation (Lemma 6)           */
+    int64_t pairs_base;      /* leaf-leaf pairs summed exhaustively                     */
+    int64_t pairs_split;     /* node pairs split into children                          */
+    int64_t point_pairs_base;/* point-point kernel evaluations (x bandwidths) in the
+                                base case or exhaustive kernel                          */
+    int64_t launches;        /* kernels this call launched                              */
+    int64_t launches_base;   /* of which base-case / exhaustive kernels                 */
+    int32_t levels;          /* frontier iterations                                     */
+    int32_t retries;         /* capacity-driven reruns                                  */
+    double  fp32_rel_bound;  /* a-priori relative error bound of the FP32 base case     */
+    double  eps_traversal;   /* eps left for pruning after the FP32 charge              */
+    double  ms_total;        /* device time of the whole call (CUDA events)             */
+    double  ms_phase[GS_NPHASE]; /* device time per GS_PH_* phase                       */
+    double  reserved[4];
+} gs_stats;
+
+/* Library version string (static storage). */
+const char *gs_version(void);
+
+/* Description of the last error returned on the calling host thread
+ * (static thread-local storage; "" when none). */
+const char *gs_last_error(void);
+
+/* Fill *o with the defaults; returns GS_OK, or GS_ERR_ARG when o is NULL. */
+int gs_opts_default(gs_opts *o);
+
+/*
+ * gs_sum -- Gaussian sums of M queries against N weighted references for nh
+ * bandwidths (Section 1's G(x_q); Sections 5-6 for eps > 0).
+ *
+ *   queries  device, M x D, dtype                  (may equal refs: monochromatic)
+ *   M        number of queries, >= 1
+ *   refs     device, N x D, dtype
+ *   weights  device, N floats, every w_r > 0 and finite
+ *   N        number of references, >= 1
+ *   D        dimension, 1 <= D <= 32
+ *   dtype    GS_F32 or GS_F64 (both point arrays)
+ *   h        HOST, nh bandwidths, each finite and > 0
+ *   nh       1 <= nh <= 64
+ *   eps      0 selects the exhaustive sum (every term, FP32 kernel arithmetic
+ *            with FP64 per-query accumulation); 0 < eps < 1 selects the
+ *            dual-tree method with |G~ - G| <= eps * max(G, floor) per query
+ *   out      device, M x nh doubles, row-major: out[q*nh + j] = G~(x_q; h_j),
+ *            queries in the caller's order
+ *   opts     host, may be NULL (defaults)
+ *   stream   cudaStream_t as void*, may be NULL
+ *   stats    host, may be NULL
+ */
+int gs_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+           int D, int dtype, const double *h, int nh, double eps, double *out,
+           const gs_opts *opts, void *stream, gs_stats *stats);
+
+/*
+ * gs_sum_host -- gs_sum for callers whose data lives in HOST memory: every
+ * array argument (queries, refs, weights, out) is host memory.  The call
+ * copies the inputs to device scratch, runs gs_sum on `stream`, copies out
+ * back and returns when out is ready.  Same argument meaning and errors as
+ * gs_sum.
+ */
+int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+                int D, int dtype, const double *h, int nh, double eps, double *out,
+                const gs_opts *opts, void *stream, gs_stats *stats);
+
+/*
+ * gs_probe_rates -- measures this device's throughput, in lanes per SM per
+ * SM clock cycle, of the two instructions the base case is built from: MUFU
+ * ex2.approx.ftz.f32 and FP32 FFMA.  A short kernel with independent chains
+ * on every SM is timed with the SM cycle counter, so the figures do not depend
+ * on the clock the GPU happens to run at.  Used for roofline reporting.
+ *   ex2_per_sm_clk, ffma_per_sm_clk   HOST doubles, written on success
+ * Returns GS_OK, GS_ERR_ARG (NULL pointer) or GS_ERR_CUDA.
+ */
+int gs_probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

@@ -1,0 +1,204 @@
+// C-ABI entry points: argument checks, scratch management, dispatch to the
+// exhaustive or dual-tree path, and the single end-of-call status read.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
+}
+
+static int check_common(const void *queries, int64_t M, const void *refs, const float *weights,
+                        int64_t N, int D, int dtype, const double *h, int nh, double eps,
+                        double *out) {
+    if (!queries || !refs || !weights || !out || !h) {
+        set_error("NULL array argument");
+        return GS_ERR_ARG;
+    }
+    if (M < 1 || N < 1) {
+        set_error("M=%lld and N=%lld must be >= 1", (long long)M, (long long)N);
+        return GS_ERR_ARG;
+    }
+    if (D < 1 || D > 32) {
+        set_error("D=%d outside [1, 32]", D);
+        return GS_ERR_ARG;
+    }
+    if (dtype != GS_F32 && dtype != GS_F64) {
+        set_error("dtype %d is neither GS_F32 nor GS_F64", dtype);
+        return GS_ERR_ARG;
+    }
+    if (nh < 1 || nh > 64) {
+        set_error("nh=%d outside [1, 64]", nh);
+        return GS_ERR_ARG;
+    }
+    for (int j = 0; j < nh; ++j)
+        if (!(h[j] > 0.0) || !isfinite(h[j])) {
+            set_error("bandwidth h[%d]=%g is not finite and positive", j, h[j]);
+            return GS_ERR_ARG;
+        }
+    if (!(eps >= 0.0 && eps < 1.0)) {
+        set_error("eps=%g outside [0, 1)", eps);
+        return GS_ERR_ARG;
+    }
+    return GS_OK;
+}
+
+static int status_to_code(unsigned st) {
+    if (st & ST_NONFINITE) {
+        set_error("non-finite coordinate or weight");
+        return GS_ERR_NONFINITE;
+    }
+    if (st & ST_WEIGHT) {
+        set_error("a weight is <= 0 (weights must be positive)");
+        return GS_ERR_WEIGHT;
+    }
+    if (st & ST_CAPACITY) {
+        set_error("a device work list exceeded its capacity");
+        return GS_ERR_CAPACITY;
+    }
+    if (st & ST_TIMEOUT) {
+        set_error("a bounded device wait gave up");
+        return GS_ERR_TIMEOUT;
+    }
+    if (st & ST_INTERNAL) {
+        set_error("internal consistency check failed on the device");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+const char *gs_version(void) { return "gbsum 0.1 (sm_103a)"; }
+
+const char *gs_last_error(void) { return g_err; }
+
+int gs_opts_default(gs_opts *o) {
+    if (!o) {
+        set_error("gs_opts_default: NULL");
+        return GS_ERR_ARG;
+    }
+    memset(o, 0, sizeof(*o));
+    o->leaf_size = 32;
+    o->floor_log2 = -40;
+    o->selector = GS_SEL_RULE;
+    return GS_OK;
+}
+
+int gs_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+           int D, int dtype, const double *h, int nh, double eps, double *out,
+           const gs_opts *opts, void *stream, gs_stats *stats) {
+    g_err[0] = 0;
+    int rc = check_common(queries, M, refs, weights, N, D, dtype, h, nh, eps, out);
+    if (rc) return rc;
+    gs_opts o;
+    gs_opts_default(&o);
+    if (opts) {
+        o = *opts;
+        if (o.leaf_size == 0) o.leaf_size = 32;
+        if (o.floor_log2 == 0) o.floor_log2 = -40;
+    }
+    if (stats) memset(stats, 0, sizeof(*stats));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool exhaustive = eps == 0.0 || o.selector == GS_SEL_EXHAUSTIVE;
+    if (!exhaustive) {
+        set_error("the dual-tree path is not built into this library yet");
+        return GS_ERR_UNSUPPORTED;
+    }
+
+    CallCtx cx;
+    cx.st = st;
+    cx.stats = stats;
+    cx.phase(GS_PH_INGEST);
+    Ingest *ing = nullptr;
+    GS_CUDA_TRY(cudaMallocAsync((void **)&ing, sizeof(Ingest), st));
+    cudaError_t e = launch_ingest(ing, queries, M, refs, weights, N, D, dtype, cx);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(ing, st);
+        return cuda_fail(e, "ingest launch");
+    }
+    rc = exhaustive_sum(queries, M, refs, weights, N, D, dtype, h, nh, ing, out, cx);
+    Ingest hing;
+    if (rc == GS_OK) {
+        e = cudaMemcpyAsync(&hing, ing, sizeof(Ingest), cudaMemcpyDeviceToHost, st);
+        cx.end();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "gs_sum");
+    }
+    cudaFreeAsync(ing, st);
+    if (rc == GS_OK) rc = status_to_code(hing.status);
+    if (rc == GS_OK && stats) {
+        cx.finish();
+        stats->point_pairs_base = M * N * nh;
+    }
+    return rc;
+}
+
+int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+                int D, int dtype, const double *h, int nh, double eps, double *out,
+                const gs_opts *opts, void *stream, gs_stats *stats) {
+    g_err[0] = 0;
+    int rc = check_common(queries, M, refs, weights, N, D, dtype, h, nh, eps, out);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = dtype == GS_F64 ? sizeof(double) : sizeof(float);
+    const bool mono = queries == refs;
+    void *dq = nullptr, *dr = nullptr;
+    float *dw = nullptr;
+    double *dout = nullptr;
+    GS_CUDA_TRY(cudaMallocAsync(&dr, (size_t)N * D * es, st));
+    if (!mono) GS_CUDA_TRY(cudaMallocAsync(&dq, (size_t)M * D * es, st));
+    GS_CUDA_TRY(cudaMallocAsync((void **)&dw, (size_t)N * sizeof(float), st));
+    GS_CUDA_TRY(cudaMallocAsync((void **)&dout, (size_t)M * nh * sizeof(double), st));
+    if (mono) dq = dr;
+    cudaError_t e = cudaMemcpyAsync(dr, refs, (size_t)N * D * es, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !mono)
+        e = cudaMemcpyAsync(dq, queries, (size_t)M * D * es, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dw, weights, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "gs_sum_host upload");
+    } else {
+        rc = gs_sum(dq, M, dr, dw, N, D, dtype, h, nh, eps, dout, opts, stream, stats);
+        if (rc == GS_OK) {
+            e = cudaMemcpyAsync(out, dout, (size_t)M * nh * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "gs_sum_host download");
+        }
+    }
+    cudaFreeAsync(dr, st);
+    if (!mono) cudaFreeAsync(dq, st);
+    cudaFreeAsync(dw, st);
+    cudaFreeAsync(dout, st);
+    return rc;
+}
+
+int gs_probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, void *stream) {
+    g_err[0] = 0;
+    if (!ex2_per_sm_clk || !ffma_per_sm_clk) {
+        set_error("gs_probe_rates: NULL output");
+        return GS_ERR_ARG;
+    }
+    return probe_rates(ex2_per_sm_clk, ffma_per_sm_clk, (cudaStream_t)stream);
+}
+
+}  // extern "C"

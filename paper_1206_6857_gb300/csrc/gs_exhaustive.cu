@@ -1,0 +1,438 @@
+// Input checks, reference packing and the exhaustive Gaussian sum.
+//
+// The exhaustive sum is the plain definition of Section 1,
+//     G(x_q; h_j) = sum_r w_r exp(-||x_q - x_r||^2 / (2 h_j^2)),
+// evaluated for every (query, reference, bandwidth).  It is the dual-tree
+// method's comparison point ("Naive" in the Section 7 tables) and its
+// exhaustive (eps = 0) mode.
+//
+// Arithmetic: the squared distance is formed in FP32 from coordinate
+// differences (FP64 differences rounded to FP32 when the input is FP64), the
+// weight is folded into the exponent as l_r = log2(w_r / w_max), and each
+// term is 2^(d^2 * (-log2(e) / 2h^2) + l_r) on the MUFU ex2 unit.  Terms are
+// summed in FP32 over runs of 64 references and the runs in FP64 per query;
+// w_max is multiplied back at the end.
+//
+// Layout: references are repacked once into 16-byte-aligned records
+// (coordinates, l_r) padded to a whole number of shared-memory tiles with
+// l = -inf records; CTAs stage one tile at a time in shared memory and every
+// thread reads each record as a broadcast, holding QPT queries and NJ
+// bandwidths in registers.  A 3-D grid spans query blocks x reference splits
+// x bandwidth chunks; splits are chosen so the grid covers every SM several
+// times even when M is small, and then accumulate with FP64 atomics.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "gs_device.cuh"
+#include "gs_internal.h"
+
+namespace gs {
+
+// --------------------------------------------------------------------------
+// Ingest: finiteness, positivity, weight range
+// --------------------------------------------------------------------------
+__global__ void k_ingest_reset(Ingest *ing) {
+    ing->status = 0;
+    ing->wmax_bits = 0;
+    ing->wmin_bits = 0x7f800000u;
+    ing->pad = 0;
+    ing->wsum = 0.0;
+}
+
+template <typename T>
+__global__ void k_ingest_points(const T *__restrict__ x, int64_t n, Ingest *ing) {
+    unsigned bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite((double)x[i])) bad = ST_NONFINITE;
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(&ing->status, bad);
+}
+
+__global__ void k_ingest_weights(const float *__restrict__ w, int64_t n, Ingest *ing) {
+    unsigned bad = 0;
+    float wmax = 0.f, wmin = INFINITY;
+    double wsum = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float wi = w[i];
+        if (!isfinite(wi)) {
+            bad |= ST_NONFINITE;
+        } else if (!(wi > 0.f)) {
+            bad |= ST_WEIGHT;
+        } else {
+            wmax = fmaxf(wmax, wi);
+            wmin = fminf(wmin, wi);
+            wsum += wi;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    for (int o = 16; o > 0; o >>= 1) {
+        wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&ing->status, bad);
+        atomicMax(&ing->wmax_bits, __float_as_uint(wmax));
+        atomicMin(&ing->wmin_bits, __float_as_uint(wmin));
+        atomicAdd(&ing->wsum, wsum);
+    }
+}
+
+static int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+cudaError_t launch_ingest(Ingest *ing, const void *queries, int64_t M, const void *refs,
+                          const float *weights, int64_t N, int D, int dtype, CallCtx &cx) {
+    cudaStream_t st = cx.st;
+    cx.launches += 3 + (queries != refs);
+    k_ingest_reset<<<1, 1, 0, st>>>(ing);
+    const int64_t nq = M * D, nr = N * D;
+    if (dtype == GS_F64) {
+        k_ingest_points<double><<<grid_for(nr, 256), 256, 0, st>>>((const double *)refs, nr, ing);
+        if (queries != refs)
+            k_ingest_points<double><<<grid_for(nq, 256), 256, 0, st>>>((const double *)queries, nq, ing);
+    } else {
+        k_ingest_points<float><<<grid_for(nr, 256), 256, 0, st>>>((const float *)refs, nr, ing);
+        if (queries != refs)
+            k_ingest_points<float><<<grid_for(nq, 256), 256, 0, st>>>((const float *)queries, nq, ing);
+    }
+    k_ingest_weights<<<grid_for(N, 256), 256, 0, st>>>(weights, N, ing);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Reference packing
+// --------------------------------------------------------------------------
+template <typename T, int DP>
+__global__ void k_pack_refs(const T *__restrict__ x, const float *__restrict__ w, int64_t N,
+                            int64_t Npad, int D, const Ingest *__restrict__ ing, T *__restrict__ rec) {
+    constexpr int NT = RefRec<T, DP>::NT;
+    const double wmax = (double)__uint_as_float(ing->wmax_bits);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Npad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        T *o = rec + i * NT;
+        if (i < N) {
+            for (int d = 0; d < DP; ++d) o[d] = d < D ? x[i * D + d] : (T)0;
+            o[DP] = (T)log2((double)w[i] / wmax);
+        } else {
+            for (int d = 0; d < DP; ++d) o[d] = (T)0;
+            o[DP] = (T)(-INFINITY);
+        }
+        for (int k = DP + 1; k < NT; ++k) o[k] = (T)0;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Exhaustive kernel
+// --------------------------------------------------------------------------
+struct NegC {
+    float v[64];   // -log2(e) / (2 h_j^2), j < nh
+};
+
+constexpr int kThreads = 256;
+constexpr int kRun = 64;   // references per FP32 partial sum
+
+template <typename T, int DP>
+struct TileCfg {
+    static constexpr int NT = RefRec<T, DP>::NT;
+    static constexpr int TILE = (NT * sizeof(T) <= 64) ? 128 : 64;
+};
+
+template <typename T, int NT>
+__device__ __forceinline__ void load_rec(const T *p, T (&v)[NT]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int k = 0; k < NT / 4; ++k) {
+            float4 f = p4[k];
+            v[4 * k] = f.x; v[4 * k + 1] = f.y; v[4 * k + 2] = f.z; v[4 * k + 3] = f.w;
+        }
+    } else {
+        const double2 *p2 = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+        for (int k = 0; k < NT / 2; ++k) {
+            double2 f = p2[k];
+            v[2 * k] = f.x; v[2 * k + 1] = f.y;
+        }
+    }
+}
+
+template <typename T, int DP, int NJ, int QPT>
+__global__ void __launch_bounds__(kThreads)
+k_exhaustive(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ rec,
+             int64_t chunk, int64_t Npad, NegC negc, int nh, const Ingest *__restrict__ ing,
+             double *__restrict__ out, int atomic) {
+    using Cfg = TileCfg<T, DP>;
+    constexpr int NT = Cfg::NT, TILE = Cfg::TILE;
+    __shared__ __align__(16) T tile[TILE * NT];
+
+    const int j0 = blockIdx.z * NJ;
+    float nc[NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) nc[jj] = (j0 + jj < nh) ? negc.v[j0 + jj] : 0.f;
+
+    T xq[QPT][DP];
+    int64_t qi[QPT];
+#pragma unroll
+    for (int k = 0; k < QPT; ++k) {
+        qi[k] = (int64_t)blockIdx.x * (kThreads * QPT) + k * kThreads + threadIdx.x;
+        const int64_t qs = qi[k] < M ? qi[k] : M - 1;
+#pragma unroll
+        for (int d = 0; d < DP; ++d) xq[k][d] = d < D ? qx[qs * D + d] : (T)0;
+    }
+
+    double acc[QPT][NJ];
+#pragma unroll
+    for (int k = 0; k < QPT; ++k)
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj) acc[k][jj] = 0.0;
+
+    const int64_t r0 = blockIdx.y * chunk;
+    const int64_t r1 = min(r0 + chunk, Npad);
+    for (int64_t t0 = r0; t0 < r1; t0 += TILE) {
+        __syncthreads();
+        {
+            // TILE*NT elements of T = TILE*NT*sizeof(T)/16 vectors of 16 bytes
+            const float4 *src = reinterpret_cast<const float4 *>(rec + t0 * NT);
+            float4 *dst = reinterpret_cast<float4 *>(tile);
+            constexpr int NV = TILE * NT * (int)sizeof(T) / 16;
+            for (int v = threadIdx.x; v < NV; v += kThreads) dst[v] = src[v];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int rr0 = 0; rr0 < TILE; rr0 += kRun) {
+            float part[QPT][NJ];
+#pragma unroll
+            for (int k = 0; k < QPT; ++k)
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) part[k][jj] = 0.f;
+#pragma unroll 4
+            for (int rr = rr0; rr < rr0 + kRun; ++rr) {
+                T rv[NT];
+                load_rec<T, NT>(tile + rr * NT, rv);
+                const float l = (float)rv[DP];
+#pragma unroll
+                for (int k = 0; k < QPT; ++k) {
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int d = 0; d < DP; ++d) {
+                        const float df = (float)(xq[k][d] - rv[d]);
+                        d2 = fmaf(df, df, d2);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) part[k][jj] += ex2_approx(fmaf(d2, nc[jj], l));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < QPT; ++k)
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) acc[k][jj] += (double)part[k][jj];
+        }
+    }
+
+    const double wmax = (double)__uint_as_float(ing->wmax_bits);
+#pragma unroll
+    for (int k = 0; k < QPT; ++k) {
+        if (qi[k] >= M) continue;
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj) {
+            const int j = j0 + jj;
+            if (j >= nh) continue;
+            const double v = acc[k][jj] * wmax;
+            if (atomic)
+                atomicAdd(out + qi[k] * nh + j, v);
+            else
+                out[qi[k] * nh + j] = v;
+        }
+    }
+}
+
+static int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+template <typename T, int DP, int NJ>
+static int run_exhaustive(const void *queries, int64_t M, const void *refs, const float *weights,
+                          int64_t N, int D, const double *h, int nh, const Ingest *ing,
+                          double *out, CallCtx &cx) {
+    cudaStream_t st = cx.st;
+    using Cfg = TileCfg<T, DP>;
+    constexpr int NT = Cfg::NT, TILE = Cfg::TILE;
+    constexpr int QPT = (DP <= 8) ? 2 : 1;
+    const int64_t Npad = (N + TILE - 1) / TILE * TILE;
+    T *rec = nullptr;
+    GS_CUDA_TRY(cudaMallocAsync((void **)&rec, (size_t)Npad * NT * sizeof(T), st));
+    k_pack_refs<T, DP><<<grid_for(Npad, 256), 256, 0, st>>>((const T *)refs, weights, N, Npad, D,
+                                                              ing, rec);
+    cx.launches += 1;
+    NegC nc;
+    for (int j = 0; j < 64; ++j) nc.v[j] = 0.f;
+    for (int j = 0; j < nh; ++j) nc.v[j] = (float)(-1.4426950408889634 / (2.0 * h[j] * h[j]));
+
+    const int64_t bx = (M + kThreads * QPT - 1) / (kThreads * QPT);
+    const int nz = (nh + NJ - 1) / NJ;
+    const int64_t tiles = Npad / TILE;
+    const int64_t target = (int64_t)num_sms() * 8;
+    int64_t splits = (target + bx * nz - 1) / (bx * nz);
+    if (splits < 1) splits = 1;
+    if (splits > tiles) splits = tiles;
+    if (splits > 65535) splits = 65535;
+    const int64_t chunk = (tiles + splits - 1) / splits * TILE;
+    splits = (Npad + chunk - 1) / chunk;
+    if (bx > 2147483647LL) {
+        cudaFreeAsync(rec, st);
+        set_error("too many queries for one launch");
+        return GS_ERR_ARG;
+    }
+    if (splits > 1) GS_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)M * nh * sizeof(double), st));
+    dim3 grid((unsigned)bx, (unsigned)splits, (unsigned)nz);
+    cx.phase(GS_PH_BASE);
+    k_exhaustive<T, DP, NJ, QPT><<<grid, kThreads, 0, st>>>((const T *)queries, M, D, rec, chunk,
+                                                           Npad, nc, nh, ing, out, splits > 1);
+    cx.launches += 1;
+    cx.launches_base += 1;
+    cx.phase(GS_PH_OTHER);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(rec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_exhaustive launch");
+    return GS_OK;
+}
+
+template <typename T, int DP>
+static int dispatch_nj(const void *q, int64_t M, const void *r, const float *w, int64_t N, int D,
+                       const double *h, int nh, const Ingest *ing, double *out, CallCtx &st) {
+    if (nh <= 1) return run_exhaustive<T, DP, 1>(q, M, r, w, N, D, h, nh, ing, out, st);
+    if (nh <= 2) return run_exhaustive<T, DP, 2>(q, M, r, w, N, D, h, nh, ing, out, st);
+    if (nh <= 4) return run_exhaustive<T, DP, 4>(q, M, r, w, N, D, h, nh, ing, out, st);
+    return run_exhaustive<T, DP, 8>(q, M, r, w, N, D, h, nh, ing, out, st);
+}
+
+template <typename T>
+static int dispatch_d(const void *q, int64_t M, const void *r, const float *w, int64_t N, int D,
+                      const double *h, int nh, const Ingest *ing, double *out, CallCtx &st) {
+#define GS_CASE(DPV) \
+    if (D <= DPV) return dispatch_nj<T, DPV>(q, M, r, w, N, D, h, nh, ing, out, st);
+    GS_CASE(1) GS_CASE(2) GS_CASE(3) GS_CASE(4) GS_CASE(5) GS_CASE(6) GS_CASE(7) GS_CASE(8)
+    GS_CASE(12) GS_CASE(16) GS_CASE(24) GS_CASE(32)
+#undef GS_CASE
+    set_error("D=%d exceeds 32", D);
+    return GS_ERR_ARG;
+}
+
+int exhaustive_sum(const void *queries, int64_t M, const void *refs, const float *weights,
+                   int64_t N, int D, int dtype, const double *h, int nh, const Ingest *ing,
+                   double *out, CallCtx &st) {
+    if (dtype == GS_F64)
+        return dispatch_d<double>(queries, M, refs, weights, N, D, h, nh, ing, out, st);
+    return dispatch_d<float>(queries, M, refs, weights, N, D, h, nh, ing, out, st);
+}
+
+// --------------------------------------------------------------------------
+// Instruction-rate probe: independent ex2 / FFMA chains on every SM, timed
+// with the per-SM cycle counter.  Each block records its SM and its start and
+// end cycle; an SM's rate is the work of all blocks it ran over the span from
+// the first start to the last end (one counter per SM, so spans are exact).
+// --------------------------------------------------------------------------
+constexpr int kProbeIters = 4096;
+constexpr int kProbeChains = 8;
+
+__device__ __forceinline__ unsigned smid() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_probe(float *sink, long long *rec) {
+    float v[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) v[c] = 0.1f + 0.01f * c + 1e-6f * threadIdx.x;
+    __syncthreads();
+    const long long t0 = clock64();
+#pragma unroll 4
+    for (int i = 0; i < kProbeIters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) {
+            if (KIND == 0)
+                v[c] = ex2_approx(-v[c]);
+            else
+                v[c] = fmaf(v[c], 0.9999f, 1e-4f);
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) s += v[c];
+    if (s == 12345.f) sink[threadIdx.x] = s;   // keeps the chains live
+    if (threadIdx.x == 0) {
+        rec[3 * blockIdx.x] = t0;
+        rec[3 * blockIdx.x + 1] = t1;
+        rec[3 * blockIdx.x + 2] = (long long)smid();
+    }
+}
+
+int probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, cudaStream_t st) {
+    const int sms = num_sms();
+    const int threads = 256;
+    const int nb = sms * 4;
+    float *sink = nullptr;
+    long long *rec = nullptr;
+    GS_CUDA_TRY(cudaMallocAsync((void **)&sink, 256 * sizeof(float), st));
+    GS_CUDA_TRY(cudaMallocAsync((void **)&rec, 3 * nb * sizeof(long long), st));
+    long long *hr = (long long *)malloc(3 * nb * sizeof(long long));
+    const int maxsm = 1024;
+    long long *lo = (long long *)malloc(maxsm * sizeof(long long));
+    long long *hi = (long long *)malloc(maxsm * sizeof(long long));
+    int *cnt = (int *)malloc(maxsm * sizeof(int));
+    double rates[2] = {0, 0};
+    int rc = GS_OK;
+    for (int kind = 0; kind < 2 && rc == GS_OK; ++kind) {
+        for (int rep = 0; rep < 2; ++rep) {   // the first launch warms up
+            if (kind == 0)
+                k_probe<0><<<nb, threads, 0, st>>>(sink, rec);
+            else
+                k_probe<1><<<nb, threads, 0, st>>>(sink, rec);
+        }
+        cudaError_t e = cudaMemcpyAsync(hr, rec, 3 * nb * sizeof(long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "probe");
+            break;
+        }
+        for (int i = 0; i < maxsm; ++i) { lo[i] = (long long)9e18; hi[i] = 0; cnt[i] = 0; }
+        for (int b = 0; b < nb; ++b) {
+            int sm = (int)hr[3 * b + 2];
+            if (sm < 0 || sm >= maxsm) continue;
+            if (hr[3 * b] < lo[sm]) lo[sm] = hr[3 * b];
+            if (hr[3 * b + 1] > hi[sm]) hi[sm] = hr[3 * b + 1];
+            cnt[sm]++;
+        }
+        double sum = 0;
+        int used = 0;
+        const double per_block = (double)threads * kProbeIters * kProbeChains;
+        for (int i = 0; i < maxsm; ++i)
+            if (cnt[i] > 0 && hi[i] > lo[i]) {
+                sum += per_block * cnt[i] / (double)(hi[i] - lo[i]);
+                used++;
+            }
+        rates[kind] = used ? sum / used : 0.0;
+    }
+    free(hr); free(lo); free(hi); free(cnt);
+    cudaFreeAsync(sink, st);
+    cudaFreeAsync(rec, st);
+    if (rc != GS_OK) return rc;
+    *ex2_per_sm_clk = rates[0];
+    *ffma_per_sm_clk = rates[1];
+    return GS_OK;
+}
+
+}  // namespace gs
