@@ -1,0 +1,479 @@
+"""CPU reference of the dual-tree method as this library restates it for a
+breadth-first, data-parallel traversal.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain numpy and Python
+loops; it shares no code with the CUDA path.  It serves two purposes:
+
+ 1. the tree partition and the per-iteration pair decisions it produces are
+    the bit-exact reference for the GPU's kd-tree build and frontier;
+ 2. its own estimate G~ (every approximation evaluated in FP64 with the
+    series reference, every leaf-leaf pair summed exactly) is checked against
+    the exhaustive oracle, which pins its error control to Theorem 2.
+
+The traversal follows the paper's DITO procedure (Fig. 7) and its pieces:
+FD pruning (Section 5), bestMethod (Fig. 6) over DH / DL / H2L with the Lemma
+4-6 bounds, the Theorem 2 rule with the W_T token scheme, exhaustive leaf-leaf
+base cases (DITOBase) and recursion into child pairs, and the breadth-first
+post-pass (Fig. 8).  Where the paper is silent this reference takes the
+readings listed in the design doc; in short:
+
+  * kd-tree: complete binary tree of depth d = min{k : ceil(n/2^k) <= L};
+    node (k, i) holds sorted positions [floor(i n/2^k), floor((i+1) n/2^k));
+    a node splits on its widest bounding-box dimension (lowest index on
+    ties) and its left child takes the smallest points by the key
+    (coordinate, original index); partitions are stable, so the points of
+    every node stay in ascending original-index order;
+  * node centre = bounding-box centre, r = half the widest extent;
+  * iteration t holds pairs (Q, R, j) with Q at depth min(t, dQ) and R at
+    depth min(t, dR); a pair that is neither pruned nor a leaf-leaf base case
+    splits into its child pairs (both sides when both are internal);
+  * the lower bound G^min of a group (Q, j) is the sum of W_R K(delta_max)
+    over every pair that covers Q (finished at Q or an ancestor, or in the
+    current frontier), raised to w_min(Q) in the monochromatic case and to
+    the floor 2^floor_log2 W;
+  * tokens: the group's token is split over its pairs in proportion to W_R;
+    each pair spends or banks from its share (need = W E / (eps G) - W_R),
+    leaf-leaf base cases bank W_R, splits return their share; children
+    inherit a copy of their parent's token and finished lower bound;
+  * all group sums use one fixed order: 32 strided partial sums followed by
+    an xor butterfly over the 32 partials;
+  * exp is evaluated with a Cody-Waite reduction and a degree-13 Taylor
+    polynomial (below), identically on both sides.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import exhaustive as _ex
+from . import series as _S
+
+# --------------------------------------------------------------------------
+# exp(x), x <= 0, by Cody & Waite (1980) argument reduction x = k ln2 + r,
+# |r| <= ln2/2, and the Taylor polynomial of e^r to degree 13 (truncation
+# below 2^-56), evaluated by Horner's rule with separately rounded products
+# and sums; 2^k is applied exactly.  Results below e^-708 are returned as 0.
+# --------------------------------------------------------------------------
+INV_LN2 = 1.4426950408889634
+LN2_HI = float.fromhex("0x1.62e42fee00000p-1")     # ln 2 with 21 trailing zero bits
+LN2_LO = 1.9082149292705877e-10                   # ln 2 - LN2_HI to double precision
+_TAYLOR = [1.0 / math.factorial(n) for n in range(14)]
+
+
+def exp_neg(x):
+    x = np.asarray(x, dtype=np.float64)
+    under = x < -708.0
+    x = np.where(under, 0.0, x)
+    k = np.rint(x * INV_LN2)
+    r = (x - k * LN2_HI) - k * LN2_LO
+    p = np.full(x.shape, _TAYLOR[13])
+    for n in range(12, -1, -1):
+        p = p * r + _TAYLOR[n]
+    out = np.ldexp(p, k.astype(np.int64))
+    return np.where(under, 0.0, out)
+
+
+# --------------------------------------------------------------------------
+# Fixed-order group reduction: 32 strided partials, then xor butterfly.
+# --------------------------------------------------------------------------
+def group_reduce(values: np.ndarray, group_of: np.ndarray, pos_in_group: np.ndarray, ngroups: int):
+    acc = np.zeros((ngroups, 32))
+    lane = pos_in_group % 32
+    order = np.lexsort((pos_in_group, group_of))       # sequential order within each lane
+    np.add.at(acc, (group_of[order], lane[order]), values[order])
+    for m in (16, 8, 4, 2, 1):
+        acc = acc + acc[:, np.arange(32) ^ m]
+    return acc[:, 0]
+
+
+# --------------------------------------------------------------------------
+# kd-tree
+# --------------------------------------------------------------------------
+def tree_depth(n: int, L: int) -> int:
+    d = 0
+    while -(-n // (1 << d)) > L:
+        d += 1
+    return d
+
+
+def level_bounds(n: int, k: int) -> np.ndarray:
+    nn = 1 << k
+    return (np.arange(nn + 1, dtype=np.int64) * n) // nn
+
+
+@dataclass
+class Tree:
+    n: int
+    D: int
+    depth: int
+    perm: np.ndarray          # sorted position -> original index
+    lo: np.ndarray            # (nodes, D) float64
+    hi: np.ndarray
+    center: np.ndarray
+    rad: np.ndarray           # half the widest extent
+    W: np.ndarray             # node weight sums
+    wmin: np.ndarray
+    begin: np.ndarray
+    end: np.ndarray
+    split_dim: np.ndarray     # -1 at leaves
+
+    @property
+    def nodes(self):
+        return (1 << (self.depth + 1)) - 1
+
+
+def build_tree(x: np.ndarray, w: np.ndarray, L: int) -> Tree:
+    n, D = x.shape
+    depth = tree_depth(n, L)
+    perm = np.arange(n, dtype=np.int64)
+    nodes = (1 << (depth + 1)) - 1
+    split_dim = np.full(nodes, -1, dtype=np.int64)
+    for k in range(depth):
+        b = level_bounds(n, k)
+        for i in range(1 << k):
+            seg = perm[b[i]:b[i + 1]]
+            pts = x[seg]
+            ext = pts.max(0).astype(np.float64) - pts.min(0).astype(np.float64)
+            s = int(np.argmax(ext))
+            split_dim[(1 << k) - 1 + i] = s
+            mid = ((2 * i + 1) * n) // (2 << k)
+            order = np.lexsort((seg, pts[:, s]))        # by coordinate, then original index
+            left = np.zeros(len(seg), dtype=bool)
+            left[order[:mid - b[i]]] = True
+            perm[b[i]:b[i + 1]] = np.concatenate([seg[left], seg[~left]])
+    lo = np.zeros((nodes, D))
+    hi = np.zeros((nodes, D))
+    W = np.zeros(nodes)
+    wmin = np.zeros(nodes)
+    begin = np.zeros(nodes, dtype=np.int64)
+    end = np.zeros(nodes, dtype=np.int64)
+    for k in range(depth + 1):
+        b = level_bounds(n, k)
+        for i in range(1 << k):
+            node = (1 << k) - 1 + i
+            seg = perm[b[i]:b[i + 1]]
+            begin[node], end[node] = b[i], b[i + 1]
+            pts = x[seg]
+            lo[node] = pts.min(0).astype(np.float64)
+            hi[node] = pts.max(0).astype(np.float64)
+            wmin[node] = float(np.min(w[seg]))
+    # weights: sequential FP64 sums over each leaf, then pairwise up the tree
+    b = level_bounds(n, depth)
+    for i in range(1 << depth):
+        node = (1 << depth) - 1 + i
+        W[node] = float(np.cumsum(w[perm[b[i]:b[i + 1]]].astype(np.float64))[-1])
+    for node in range((1 << depth) - 2, -1, -1):
+        W[node] = W[2 * node + 1] + W[2 * node + 2]
+    center = (lo + hi) * 0.5
+    rad = ((hi - lo) * 0.5).max(axis=1)
+    return Tree(n, D, depth, perm, lo, hi, center, rad, W, wmin, begin, end, split_dim)
+
+
+# --------------------------------------------------------------------------
+# error constants
+# --------------------------------------------------------------------------
+DEFAULT_PLIMIT = {1: 8, 2: 8, 3: 6, 4: 5, 5: 4, 6: 2}
+
+
+def plimit_for(D: int) -> int:
+    """Section 6 table (D=4 unstated: 5; D>6: 1; D=1 taken as 8)."""
+    return DEFAULT_PLIMIT.get(D, 1)
+
+
+def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int) -> float:
+    """A-priori relative error of the FP32 base case: per-term argument
+    rounding for exponents down to 2^-64 (ln2 * 64 * (D+4) u), the ex2.approx
+    bound 2^-21, FP32 accumulation over 64-term runs (64 u); terms below
+    2^-64 w_max are charged absolutely against the floor."""
+    u = 2.0 ** -24
+    rho = 0.6931471805599453 * 64.0 * (D + 4) * u
+    rho = rho + 2.0 ** -21
+    rho = rho + 64.0 * u
+    rho = rho + 2.0 ** (-63 - floor_log2) * ((N * w_max) / W)
+    return rho
+
+
+def bound_factor_table(D: int, P: int):
+    F = [0.0] * (P + 1)
+    BT = [0.0] * (P + 1)
+    for p in range(1, P + 1):
+        pp = p % D
+        prod = math.factorial(p // D) ** (D - pp) * math.factorial(-(-p // D)) ** pp
+        F[p] = float(math.comb(D + p - 1, D - 1)) / math.sqrt(float(prod))
+        BT[p] = float(math.comb(D + p - 1, D))
+    return F, BT
+
+
+def rpow(r, p):
+    out = np.ones_like(r)
+    for _ in range(p):
+        out = out * r
+    return out
+
+
+# --------------------------------------------------------------------------
+# traversal
+# --------------------------------------------------------------------------
+FD, DH, DL, H2L, BASE, SPLIT = 0, 1, 2, 3, 4, 5
+SEL_RULE, SEL_MLP, SEL_FD_ONLY, SEL_EXHAUSTIVE = 0, 1, 2, 3
+SQRT2 = 1.4142135623730951
+
+
+@dataclass
+class Traversal:
+    iters: list = field(default_factory=list)   # per iteration: dict of arrays
+    est: np.ndarray = None                       # (nodesQ, nh) FD estimates per node
+    eps_t: float = 0.0
+    rho: float = 0.0
+    W: float = 0.0
+
+
+def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None = None,
+             selector: int = SEL_RULE, tokens: bool = True, floor_log2: int = -40,
+             w_max: float = None):
+    """Run the level-synchronous traversal; returns a Traversal whose iters[t]
+    holds the frontier (q, r, j) and the decision (method, p, E) of every
+    pair in the exact order the GPU processes them."""
+    h = np.asarray(h, np.float64)
+    nh = h.size
+    D = qt.D
+    P = plimit_for(D) if not plimit else plimit
+    W = float(rt.W[0])
+    floorW = W * 2.0 ** floor_log2
+    rho = fp32_rho(D, rt.n, w_max, W, floor_log2)
+    eps_t = eps - rho
+    F, BT = bound_factor_table(D, P)
+    Dpow = [float(D) ** k for k in range(2 * P + 2)]
+    two_h2 = (2.0 * h) * h
+    inv_2h2 = 1.0 / two_h2
+    inv_4h2 = 1.0 / ((4.0 * h) * h)
+    inv_h = 1.0 / h
+    nQ = qt.nodes
+    fin = np.zeros((nQ, nh))
+    tok = np.zeros((nQ, nh))
+    est = np.zeros((nQ, nh))
+    cnt_q = (qt.end - qt.begin).astype(np.float64)
+    cnt_r = (rt.end - rt.begin).astype(np.float64)
+
+    pq = np.zeros(nh, dtype=np.int64)
+    pr = np.zeros(nh, dtype=np.int64)
+    pj = np.arange(nh, dtype=np.int64)
+    out = Traversal(eps_t=eps_t, rho=rho, W=W)
+    T = max(qt.depth, rt.depth)
+    for t in range(T + 1):
+        if pq.size == 0:
+            break
+        q_leaf = t >= qt.depth
+        r_leaf = t >= rt.depth
+        # groups: runs of equal (j, q) in the sorted frontier
+        key_change = np.ones(pq.size, dtype=bool)
+        key_change[1:] = (pq[1:] != pq[:-1]) | (pj[1:] != pj[:-1])
+        gid = np.cumsum(key_change) - 1
+        gstart = np.flatnonzero(key_change)
+        ng = gstart.size
+        pos = np.arange(pq.size) - gstart[gid]
+        gq = pq[gstart]
+        gj = pj[gstart]
+
+        # per-pair distance bounds (Section 5), summed dimension by dimension
+        dmin2 = np.zeros(pq.size)
+        dmax2 = np.zeros(pq.size)
+        for d in range(D):
+            g = np.maximum(0.0, np.maximum(rt.lo[pr, d] - qt.hi[pq, d], qt.lo[pq, d] - rt.hi[pr, d]))
+            f = np.maximum(qt.hi[pq, d] - rt.lo[pr, d], rt.hi[pr, d] - qt.lo[pq, d])
+            dmin2 = dmin2 + g * g
+            dmax2 = dmax2 + f * f
+        kmax = exp_neg(-(dmax2 * inv_2h2[pj]))
+        kmin = exp_neg(-(dmin2 * inv_2h2[pj]))
+        WR = rt.W[pr]
+        dl = WR * kmax
+        front = group_reduce(dl, gid, pos, ng)
+        Wg = group_reduce(WR, gid, pos, ng)
+        G = fin[gq, gj] + front
+        if mono:
+            G = np.maximum(G, qt.wmin[gq])
+        G = np.maximum(G, floorW)
+        Gp = G[gid]
+        allot = (tok[gq, gj][gid] * WR) / Wg[gid] if tokens else np.zeros(pq.size)
+
+        def need(E):
+            return (W * E) / (eps_t * Gp) - WR
+
+        e_fd = (WR * (kmin - kmax)) * 0.5
+        est_fd = (WR * (kmin + kmax)) * 0.5
+        method = np.full(pq.size, SPLIT if not (q_leaf and r_leaf) else BASE)
+        porder = np.zeros(pq.size, dtype=np.int64)
+        E = np.zeros(pq.size)
+        n_fd = need(e_fd)
+        use_fd = (n_fd <= allot) & (selector != SEL_EXHAUSTIVE)
+        method[use_fd] = FD
+        E[use_fd] = e_fd[use_fd]
+        leftover = np.where(use_fd, allot - n_fd, 0.0)
+
+        if selector in (SEL_RULE, SEL_MLP) and P >= 1:
+            e4 = exp_neg(-(dmin2 * inv_4h2[pj]))
+            base = (WR * e4)
+            rR = rt.rad[pr] * inv_h[pj]
+            rQ = qt.rad[pq] * inv_h[pj]
+            best_c = np.full(pq.size, np.inf)
+            best_m = np.full(pq.size, -1)
+            best_p = np.zeros(pq.size, dtype=np.int64)
+            best_need = np.zeros(pq.size)
+            best_E = np.zeros(pq.size)
+            x2 = SQRT2 * rQ
+            for m in (DH, DL, H2L):
+                pm = np.zeros(pq.size, dtype=np.int64)
+                needm = np.zeros(pq.size)
+                Em = np.zeros(pq.size)
+                for p in range(1, P + 1):
+                    if m == DH:
+                        Ep = (base * F[p]) * rpow(rR, p)
+                    elif m == DL:
+                        Ep = (base * F[p]) * rpow(rQ, p)
+                    else:
+                        expo = np.where(x2 <= 1.0, 0, p - 1)
+                        tail = np.where(expo == 0, 1.0, rpow(x2, p - 1))
+                        Ep = (base * F[p]) * (rpow(rQ, p) + (rpow(SQRT2 * rR, p) * BT[p]) * tail)
+                    np_ = need(Ep)
+                    ok = (pm == 0) & (np_ <= allot)
+                    pm[ok] = p
+                    needm[ok] = np_[ok]
+                    Em[ok] = Ep[ok]
+                found = pm > 0
+                if m == DH:
+                    c = cnt_q[pq] * np.array([Dpow[p + 1] for p in pm])
+                elif m == DL:
+                    c = cnt_r[pr] * np.array([Dpow[p + 1] for p in pm])
+                else:
+                    c = np.array([Dpow[2 * p + 1] for p in pm])
+                better = found & (c < best_c)
+                best_c[better] = c[better]
+                best_m[better] = m
+                best_p[better] = pm[better]
+                best_need[better] = needm[better]
+                best_E[better] = Em[better]
+            c_ex = (float(D) * cnt_q[pq]) * cnt_r[pr]
+            series = (~use_fd) & (best_m >= 0) & (best_c <= c_ex)   # ties favour the series method (Fig. 6)
+            method[series] = best_m[series]
+            porder[series] = best_p[series]
+            E[series] = best_E[series]
+            leftover = np.where(series, allot - best_need, leftover)
+        undecided = (method == SPLIT) | (method == BASE)
+        if tokens:
+            leftover = np.where(undecided & (method == BASE), allot + WR, leftover)
+            leftover = np.where(method == SPLIT, allot, leftover)
+        else:
+            leftover = np.zeros(pq.size)
+        finished = method != SPLIT
+        tok_new = group_reduce(leftover, gid, pos, ng)
+        fin_add = group_reduce(np.where(finished, dl, 0.0), gid, pos, ng)
+        est_add = group_reduce(np.where(method == FD, est_fd, 0.0), gid, pos, ng)
+        fin[gq, gj] = fin[gq, gj] + fin_add
+        tok[gq, gj] = tok_new
+        est[gq, gj] = est[gq, gj] + est_add
+
+        out.iters.append(dict(q=pq.copy(), r=pr.copy(), j=pj.copy(), method=method.copy(),
+                              p=porder.copy(), E=E.copy(), G=Gp.copy()))
+
+        # children of the split pairs, grouped by (j, child q) in sorted order
+        sp = method == SPLIT
+        if not sp.any():
+            pq = pq[:0]
+            break
+        if not q_leaf:
+            for g in range(ng):
+                qn = gq[g]
+                for c in (2 * qn + 1, 2 * qn + 2):
+                    fin[c, gj[g]] = fin[qn, gj[g]]
+                    tok[c, gj[g]] = tok[qn, gj[g]]
+        nq_, nr_, nj_ = [], [], []
+        gend = np.append(gstart[1:], pq.size)
+        for g in range(ng):
+            sel = np.flatnonzero(sp[gstart[g]:gend[g]]) + gstart[g]
+            if sel.size == 0:
+                continue
+            rs = pr[sel]
+            qn, jn = gq[g], gj[g]
+            if not q_leaf and not r_leaf:
+                for c in (2 * qn + 1, 2 * qn + 2):
+                    rr = np.stack([2 * rs + 1, 2 * rs + 2], axis=1).ravel()
+                    nq_.append(np.full(rr.size, c)); nr_.append(rr); nj_.append(np.full(rr.size, jn))
+            elif q_leaf:
+                rr = np.stack([2 * rs + 1, 2 * rs + 2], axis=1).ravel()
+                nq_.append(np.full(rr.size, qn)); nr_.append(rr); nj_.append(np.full(rr.size, jn))
+            else:
+                for c in (2 * qn + 1, 2 * qn + 2):
+                    nq_.append(np.full(rs.size, c)); nr_.append(rs.copy()); nj_.append(np.full(rs.size, jn))
+        pq = np.concatenate(nq_)
+        pr = np.concatenate(nr_)
+        pj = np.concatenate(nj_)
+    out.est = est
+    return out
+
+
+# --------------------------------------------------------------------------
+# the estimate G~ in FP64 from a traversal (Fig. 7 actions + Fig. 8)
+# --------------------------------------------------------------------------
+def estimate(qt: Tree, rt: Tree, xq: np.ndarray, xr: np.ndarray, w: np.ndarray, h, trav: Traversal,
+             plimit: int | None = None):
+    """G~(x_q; h_j) in FP64, caller query order.  Also returns, per query
+    and bandwidth, the sum of the error bounds charged to it."""
+    h = np.asarray(h, np.float64)
+    nh = h.size
+    D = qt.D
+    P = plimit_for(D) if not plimit else plimit
+    M = xq.shape[0]
+    Gs = np.zeros((qt.n, nh))                  # sorted query order
+    charged = np.zeros((qt.n, nh))
+    xqs = np.asarray(xq, np.float64)[qt.perm]
+    T_P = _S.num_terms(D, P)
+    B = np.zeros((qt.nodes, nh, T_P))
+
+    def pts_r(node):
+        idx = rt.perm[rt.begin[node]:rt.end[node]]
+        return np.asarray(xr, np.float64)[idx], np.asarray(w, np.float64)[idx]
+
+    for it in trav.iters:
+        for q, r, j, m, p, E in zip(it["q"], it["r"], it["j"], it["method"], it["p"], it["E"]):
+            b0, b1 = qt.begin[q], qt.end[q]
+            if m in (FD, DH, DL, H2L):
+                charged[b0:b1, j] += E
+            if m == DH:
+                xs, ws = pts_r(r)
+                A = _S.hermite_coeffs(xs, ws, rt.center[r], h[j], p)
+                Gs[b0:b1, j] += _S.eval_hermite(A, rt.center[r], h[j], xqs[b0:b1], p)
+            elif m == DL:
+                xs, ws = pts_r(r)
+                Bl = _S.local_coeffs_direct(xs, ws, qt.center[q], h[j], p)
+                B[q, j, :Bl.size] += Bl
+            elif m == H2L:
+                xs, ws = pts_r(r)
+                A = _S.hermite_coeffs(xs, ws, rt.center[r], h[j], p)
+                Bl = _S.h2l(A, rt.center[r], qt.center[q], h[j], p, p)
+                B[q, j, :Bl.size] += Bl
+            elif m == BASE:
+                xs, ws = pts_r(r)
+                Gs[b0:b1, j] += _ex.gauss_sum(xqs[b0:b1], xs, ws, [h[j]])[:, 0]
+    # downward pass: FD estimates and local expansions to the leaves
+    est = trav.est.copy()
+    for node in range((1 << qt.depth) - 1):
+        for c in (2 * node + 1, 2 * node + 2):
+            est[c] += est[node]
+            for j in range(nh):
+                if np.any(B[node, j]):
+                    B[c, j] += _S.l2l(B[node, j], qt.center[node], qt.center[c], h[j], P)
+    leaf0 = (1 << qt.depth) - 1
+    for i in range(1 << qt.depth):
+        node = leaf0 + i
+        b0, b1 = qt.begin[node], qt.end[node]
+        for j in range(nh):
+            Gs[b0:b1, j] += est[node, j]
+            if np.any(B[node, j]):
+                Gs[b0:b1, j] += _S.eval_local(B[node, j], qt.center[node], h[j], xqs[b0:b1], P)
+    out = np.empty((M, nh))
+    out[qt.perm] = Gs
+    ch = np.empty((M, nh))
+    ch[qt.perm] = charged
+    return out, ch

@@ -1,0 +1,154 @@
+"""Pins for the CPU dual-tree reference (tree, traversal, estimate).
+
+The tree is pinned by its defining invariants and by the 1-D case, where the
+partition must be the sorted order; the traversal by exact coverage (every
+(query, reference, bandwidth) triple lies in exactly one finished pair), by
+the Theorem 2 invariant on the error charged to every query, and by its FP64
+estimate against the exhaustive oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dualtree as T
+from oracle import exhaustive as oracle_ex
+from workloads import synth
+
+
+def test_exp_neg_accuracy_and_cutoff():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    xs = np.concatenate([-np.linspace(0, 708, 5001), np.random.default_rng(1).uniform(-708, 0, 500)])
+    got = T.exp_neg(xs)
+    for x, g in zip(xs[::7], got[::7]):
+        want = mp.e ** mp.mpf(float(x))
+        assert abs(g - float(want)) <= 2.5e-16 * float(want)
+    assert np.all(T.exp_neg(np.array([-708.5, -1e300])) == 0.0)
+    assert T.exp_neg(np.array([0.0]))[0] == 1.0
+
+
+def test_group_reduce_matches_exact_sums():
+    rng = np.random.default_rng(2)
+    sizes = [1, 5, 31, 32, 33, 64, 100, 1000]
+    vals, gid, pos = [], [], []
+    for g, s in enumerate(sizes):
+        vals.append(rng.uniform(0, 1, s))
+        gid.append(np.full(s, g))
+        pos.append(np.arange(s))
+    v = np.concatenate(vals)
+    got = T.group_reduce(v, np.concatenate(gid), np.concatenate(pos), len(sizes))
+    for g, x in enumerate(vals):
+        assert got[g] == pytest.approx(math.fsum(x), rel=1e-14)
+
+
+def _check_tree(x, w, L):
+    t = T.build_tree(x, w, L)
+    n = x.shape[0]
+    assert sorted(t.perm.tolist()) == list(range(n))
+    assert -(-n // (1 << t.depth)) <= L and (t.depth == 0 or -(-n // (1 << (t.depth - 1))) > L)
+    for k in range(t.depth + 1):
+        b = T.level_bounds(n, k)
+        for i in range(1 << k):
+            node = (1 << k) - 1 + i
+            seg = t.perm[b[i]:b[i + 1]]
+            assert len(seg) >= 1
+            if k == t.depth:
+                assert np.all(np.diff(seg) > 0)                   # leaves: ascending original index
+            pts = x[seg].astype(np.float64)
+            assert np.array_equal(t.lo[node], pts.min(0)) and np.array_equal(t.hi[node], pts.max(0))
+            assert t.W[node] == pytest.approx(math.fsum(w[seg].astype(np.float64)), rel=1e-13)
+            if k < t.depth:
+                s = t.split_dim[node]
+                ext = pts.max(0) - pts.min(0)
+                assert s == int(np.argmax(ext))
+                mid = ((2 * i + 1) * n) // (2 << k)
+                left, right = t.perm[b[i]:mid], t.perm[mid:b[i + 1]]
+                kl = max((x[j, s], j) for j in left)
+                kr = min((x[j, s], j) for j in right)
+                assert kl < kr                                    # median split by (coord, index)
+    return t
+
+
+@pytest.mark.parametrize("n,D,L", [(1000, 2, 32), (777, 3, 16), (300, 5, 8), (64, 1, 2), (33, 4, 32)])
+def test_tree_invariants(n, D, L):
+    x, _, w = synth.small_random(n + D, n, D)
+    _check_tree(x, w, L)
+
+
+def test_tree_fp64_and_ties():
+    rng = np.random.default_rng(3)
+    x = np.round(rng.uniform(0, 1, (500, 2)), 2)                 # many equal coordinates
+    w = rng.uniform(0.5, 1.5, 500).astype(np.float32)
+    _check_tree(x, w, 8)
+
+
+def test_tree_1d_is_the_sorted_order():
+    rng = np.random.default_rng(4)
+    x = np.round(rng.uniform(0, 1, (513, 1)), 3).astype(np.float32)
+    w = np.ones(513, np.float32)
+    t = T.build_tree(x, w, 4)
+    want = np.lexsort((np.arange(513), x[:, 0]))
+    for i in range(1 << t.depth):
+        b = T.level_bounds(513, t.depth)
+        assert set(t.perm[b[i]:b[i + 1]]) == set(want[b[i]:b[i + 1]])
+
+
+def _problem(seed, n, D, m=None):
+    q, r, w = synth.small_random(seed, n, D, m=m)
+    mono = m is None
+    return q, r, w, mono
+
+
+def _trees(q, r, w, mono, L):
+    rt = T.build_tree(r, w, L)
+    qt = rt if mono else T.build_tree(q, np.ones(q.shape[0], np.float32), L)
+    return qt, rt
+
+
+def _coverage(qt, rt, trav, nh):
+    cov = np.zeros((qt.n, rt.n, nh), dtype=np.int32)
+    for it in trav.iters:
+        for q, r, j, m in zip(it["q"], it["r"], it["j"], it["method"]):
+            if m != T.SPLIT:
+                cov[qt.begin[q]:qt.end[q], rt.begin[r]:rt.end[r], j] += 1
+    return cov
+
+
+@pytest.mark.parametrize("selector", [T.SEL_RULE, T.SEL_FD_ONLY, T.SEL_EXHAUSTIVE])
+def test_traversal_covers_every_triple_exactly_once(selector):
+    q, r, w, mono = _problem(21, 600, 2)
+    qt, rt = _trees(q, r, w, mono, 16)
+    h = np.array([0.005, 0.05, 0.5])
+    trav = T.traverse(qt, rt, mono, h, 1e-2, selector=selector, w_max=float(w.max()))
+    assert np.all(_coverage(qt, rt, trav, h.size) == 1)
+
+
+@pytest.mark.parametrize("D,n,m,eps,tokens", [(2, 1500, None, 1e-2, True), (3, 1200, None, 1e-3, True),
+                                              (3, 1000, 700, 1e-2, True), (2, 1200, None, 1e-2, False),
+                                              (5, 800, None, 1e-2, True)])
+def test_estimate_within_eps_and_theorem2_invariant(D, n, m, eps, tokens):
+    q, r, w, mono = _problem(30 + D, n, D, m)
+    qt, rt = _trees(q, r, w, mono, 16)
+    h = synth.log_bandwidths(synth.bbox_diagonal(r), 6, 1e-3, 1.0)
+    trav = T.traverse(qt, rt, mono, h, eps, tokens=tokens, w_max=float(w.max()))
+    got, charged = T.estimate(qt, rt, q, r, w, h, trav)
+    want = oracle_ex.gauss_sum(q, r, w, h)
+    floor = 2.0 ** -40 * float(np.sum(w.astype(np.float64)))
+    den = np.maximum(want, floor)
+    assert np.all(charged <= trav.eps_t * den * (1 + 1e-9))          # Theorem 2 with tokens
+    assert np.max(np.abs(got - want) / den) <= trav.eps_t * (1 + 1e-6)
+    methods = np.concatenate([it["method"] for it in trav.iters])
+    assert (methods == T.FD).any() and (methods == T.BASE).any()
+
+
+def test_series_methods_are_used_in_low_dimension():
+    q, r, w, mono = _problem(40, 3000, 2)
+    qt, rt = _trees(q, r, w, mono, 16)
+    h = np.array([0.1, 0.3])
+    trav = T.traverse(qt, rt, mono, h, 1e-3, w_max=float(w.max()))
+    methods = np.concatenate([it["method"] for it in trav.iters])
+    assert np.isin([T.DH, T.DL, T.H2L], methods).any()
+    got, _ = T.estimate(qt, rt, q, r, w, h, trav)
+    want = oracle_ex.gauss_sum(q, r, w, h)
+    assert np.max(np.abs(got - want) / want) <= 1e-3
