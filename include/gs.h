@@ -143,6 +143,27 @@ int gs_sum(const void *queries, int64_t M, const void *refs, const float *weight
            const gs_opts *opts, void *stream, gs_stats *stats);
 
 /*
+ * gs_sum_trace -- gs_sum (eps > 0 only) that also records how the traversal
+ * treated every node pair, for verification against a reference traversal.
+ *   trace      device, 4 x trace_cap int32; record i = (query node, reference
+ *              node, bandwidth index, action | order << 8 | iteration << 16)
+ *              in processing order (iterations ascending; inside one,
+ *              groups (bandwidth, query node) ascending, reference nodes
+ *              ascending).  Nodes are heap-numbered (root 0, children of k at
+ *              2k+1, 2k+2).  Actions: 0 FD, 1 DH, 2 DL, 3 H2L, 4 base case,
+ *              5 split.  Records past trace_cap are dropped.
+ *   trace_len  host, written with the total number of records (may exceed
+ *              trace_cap)
+ *   qperm      device, M int32 or NULL: sorted position -> query index
+ *   rperm      device, N int32 or NULL: sorted position -> reference index
+ * Errors as gs_sum; GS_ERR_ARG when eps == 0.
+ */
+int gs_sum_trace(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+                 int D, int dtype, const double *h, int nh, double eps, double *out,
+                 const gs_opts *opts, void *stream, gs_stats *stats, int32_t *trace, int64_t trace_cap,
+                 int64_t *trace_len, int32_t *qperm, int32_t *rperm);
+
+/*
  * gs_sum_host -- gs_sum for callers whose data lives in HOST memory: every
  * array argument (queries, refs, weights, out) is host memory.  The call
  * copies the inputs to device scratch, runs gs_sum on `stream`, copies out

@@ -245,7 +245,9 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
     rho = fp32_rho(D, rt.n, w_max, W, floor_log2)
     eps_t = eps - rho
     F, BT = bound_factor_table(D, P)
-    Dpow = [float(D) ** k for k in range(2 * P + 2)]
+    Dpow = [1.0]
+    for _ in range(2 * P + 1):
+        Dpow.append(Dpow[-1] * float(D))
     two_h2 = (2.0 * h) * h
     inv_2h2 = 1.0 / two_h2
     inv_4h2 = 1.0 / ((4.0 * h) * h)

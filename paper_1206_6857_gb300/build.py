@@ -24,6 +24,11 @@ def _nvcc():
     raise RuntimeError("nvcc not found")
 
 
+# translation units whose FP64 arithmetic must not be contracted into FMAs
+# (decisions there are reproduced bit for bit by a CPU evaluation)
+NO_FMA = {"gs_frontier.cu", "gs_tree.cu"}
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -45,7 +50,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_mtime):
-            jobs.append([nvcc] + ARCH + NVCC_FLAGS + ["-c", s, "-o", o])
+            extra = ["-fmad=false"] if os.path.basename(s) in NO_FMA else []
+            jobs.append([nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

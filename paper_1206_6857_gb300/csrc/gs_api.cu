@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "gs_internal.h"
@@ -21,6 +22,23 @@ void set_error(const char *fmt, ...) {
 int cuda_fail(cudaError_t e, const char *what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
+}
+
+bool CallCtx::debug_sync_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("GS_DEBUG_SYNC");
+        v = (e && e[0] && e[0] != '0') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+int CallCtx::check(const char *what) {
+    if (!debug) return GS_OK;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return GS_OK;
 }
 
 static int check_common(const void *queries, int64_t M, const void *refs, const float *weights,
@@ -75,6 +93,10 @@ static int status_to_code(unsigned st) {
         set_error("a bounded device wait gave up");
         return GS_ERR_TIMEOUT;
     }
+    if (st & ST_EPS) {
+        set_error("eps is too small: the FP32 base-case error bound takes more than half of it");
+        return GS_ERR_ARG;
+    }
     if (st & ST_INTERNAL) {
         set_error("internal consistency check failed on the device");
         return GS_ERR_CUDA;
@@ -104,9 +126,9 @@ int gs_opts_default(gs_opts *o) {
     return GS_OK;
 }
 
-int gs_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
-           int D, int dtype, const double *h, int nh, double eps, double *out,
-           const gs_opts *opts, void *stream, gs_stats *stats) {
+static int sum_impl(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
+                    int dtype, const double *h, int nh, double eps, double *out, const gs_opts *opts, void *stream,
+                    gs_stats *stats, TraceOut *trace) {
     g_err[0] = 0;
     int rc = check_common(queries, M, refs, weights, N, D, dtype, h, nh, eps, out);
     if (rc) return rc;
@@ -117,13 +139,17 @@ int gs_sum(const void *queries, int64_t M, const void *refs, const float *weight
         if (o.leaf_size == 0) o.leaf_size = 32;
         if (o.floor_log2 == 0) o.floor_log2 = -40;
     }
+    if (o.selector < GS_SEL_RULE || o.selector > GS_SEL_EXHAUSTIVE) {
+        set_error("unknown selector %d", o.selector);
+        return GS_ERR_ARG;
+    }
+    if (o.floor_log2 < -1000 || o.floor_log2 > -1) {
+        set_error("floor_log2=%d outside [-1000, -1]", o.floor_log2);
+        return GS_ERR_ARG;
+    }
     if (stats) memset(stats, 0, sizeof(*stats));
     cudaStream_t st = (cudaStream_t)stream;
-    const bool exhaustive = eps == 0.0 || o.selector == GS_SEL_EXHAUSTIVE;
-    if (!exhaustive) {
-        set_error("the dual-tree path is not built into this library yet");
-        return GS_ERR_UNSUPPORTED;
-    }
+    const bool exhaustive = eps == 0.0;
 
     CallCtx cx;
     cx.st = st;
@@ -136,21 +162,49 @@ int gs_sum(const void *queries, int64_t M, const void *refs, const float *weight
         cudaFreeAsync(ing, st);
         return cuda_fail(e, "ingest launch");
     }
-    rc = exhaustive_sum(queries, M, refs, weights, N, D, dtype, h, nh, ing, out, cx);
-    Ingest hing;
-    if (rc == GS_OK) {
-        e = cudaMemcpyAsync(&hing, ing, sizeof(Ingest), cudaMemcpyDeviceToHost, st);
-        cx.end();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(e, "gs_sum");
+    unsigned status = 0;
+    if (exhaustive) {
+        rc = exhaustive_sum(queries, M, refs, weights, N, D, dtype, h, nh, ing, out, cx);
+        Ingest hing;
+        if (rc == GS_OK) {
+            e = cudaMemcpyAsync(&hing, ing, sizeof(Ingest), cudaMemcpyDeviceToHost, st);
+            cx.end();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "gs_sum");
+            status = hing.status;
+        }
+        if (rc == GS_OK && stats) stats->point_pairs_base = M * N * nh;
+    } else {
+        rc = dualtree_sum(queries, M, refs, weights, N, D, dtype, h, nh, eps, out, o, cx, ing, trace, &status);
     }
     cudaFreeAsync(ing, st);
-    if (rc == GS_OK) rc = status_to_code(hing.status);
-    if (rc == GS_OK && stats) {
-        cx.finish();
-        stats->point_pairs_base = M * N * nh;
-    }
+    if (rc == GS_OK) rc = status_to_code(status);
+    if (rc == GS_OK && stats) cx.finish();
     return rc;
+}
+
+int gs_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+           int D, int dtype, const double *h, int nh, double eps, double *out,
+           const gs_opts *opts, void *stream, gs_stats *stats) {
+    return sum_impl(queries, M, refs, weights, N, D, dtype, h, nh, eps, out, opts, stream, stats, nullptr);
+}
+
+int gs_sum_trace(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+                 int D, int dtype, const double *h, int nh, double eps, double *out,
+                 const gs_opts *opts, void *stream, gs_stats *stats, int32_t *trace, int64_t trace_cap,
+                 int64_t *trace_len, int32_t *qperm, int32_t *rperm) {
+    if (eps == 0.0) {
+        set_error("gs_sum_trace needs eps > 0 (the exhaustive path has no traversal)");
+        return GS_ERR_ARG;
+    }
+    TraceOut t;
+    t.trace = trace;
+    t.cap = trace ? trace_cap : 0;
+    t.len = trace_len;
+    t.qperm = qperm;
+    t.rperm = rperm;
+    if (trace_len) *trace_len = 0;
+    return sum_impl(queries, M, refs, weights, N, D, dtype, h, nh, eps, out, opts, stream, stats, &t);
 }
 
 int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,

@@ -1,0 +1,601 @@
+// Breadth-first node-pair frontier: the dual-tree recursion of Fig. 1 / Fig. 7
+// (DITO) restated level-synchronously so that every pair of an iteration is
+// processed in parallel.
+//
+// Iteration t holds pairs (Q, R, j) with Q at depth min(t, dQ) and R at
+// depth min(t, dR), grouped by (j, Q) with R ascending.  One warp handles one
+// group:
+//   pass 1  delta_min / delta_max from the bounding boxes (Section 5), the
+//           group's lower bound G^min = (finished lower bounds of Q and its
+//           ancestors) + sum of W_R K(delta_max) over the group's pairs,
+//           raised to w_min(Q) (monochromatic) and to the floor 2^f W;
+//   pass 2  per pair: its token share W_T * W_R / sum W_R, the FD test with
+//           tokens (Fig. 7), then bestMethod (Fig. 6) over DH / DL / H2L with
+//           the Lemma 4-6 bounds against the Theorem 2 budget, else a
+//           leaf-leaf base case (banks W_R, DITOBase) or a split.
+// The group's token, finished lower bound and FD estimate are then reduced
+// in a fixed order (32 lane-strided partial sums and an xor butterfly) and
+// inherited by the child groups.  A column scan over groups gives every
+// group its output offsets, and a second warp-per-group pass writes the
+// child frontier (still grouped and sorted), the base-case pairs and the
+// series actions.
+//
+// Everything that decides an action is FP64 with no FMA contraction (this
+// file is compiled with -fmad=false) and an exp written for this purpose
+// (Cody-Waite reduction + degree-13 Taylor polynomial), so the pair lists are
+// reproducible bit for bit by a plain CPU evaluation of the same formulas.
+#include <math.h>
+
+#include "gs_frontier.cuh"
+#include "gs_internal.h"
+#include "gs_tree.cuh"
+
+namespace gs {
+
+__constant__ double c_taylor[14];
+
+static const double kInvLn2 = 1.4426950408889634;
+static const double kLn2Hi = 0x1.62e42fee00000p-1;
+static const double kLn2Lo = 1.9082149292705877e-10;
+static const double kSqrt2 = 1.4142135623730951;
+
+// exp(x) for x <= 0: x = k ln2 + r (Cody & Waite), e^r by Horner on the
+// degree-13 Taylor polynomial, times 2^k built exactly; 0 below -708.
+__device__ __forceinline__ double exp_neg(double x) {
+    if (x < -708.0) return 0.0;
+    const double k = rint(x * kInvLn2);
+    const double r = (x - k * kLn2Hi) - k * kLn2Lo;
+    double p = c_taylor[13];
+#pragma unroll
+    for (int n = 12; n >= 0; --n) p = p * r + c_taylor[n];
+    const long long e = (long long)((int)k + 1023) << 52;
+    return p * __longlong_as_double(e);
+}
+
+__device__ __forceinline__ double rpow(double r, int p) {
+    double o = 1.0;
+    for (int i = 0; i < p; ++i) o = o * r;
+    return o;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v = v + __shfl_xor_sync(0xffffffffu, v, m);
+    return v;
+}
+
+struct FrontierParams {
+    int D, nh, P, selector, tokens, mono;
+    int t, q_depth, r_depth, q_leaf, r_leaf;
+    int floor_log2;
+    int64_t qn, rn;
+    const double *qlo, *qhi, *qrad;
+    const float *qwmin;
+    const double *rlo, *rhi, *rrad, *rW;
+    const double *inv_2h2, *inv_4h2, *inv_h;
+    double *fin, *tok, *est;
+    double F[17], BT[17], Dpow[34];
+};
+
+__device__ __forceinline__ double node_count(int64_t n, int depth, int64_t node) {
+    const int64_t i = node - ((1ll << depth) - 1);
+    return (double)(level_begin(n, depth, i + 1) - level_begin(n, depth, i));
+}
+
+struct PairGeom {
+    double dmin2, dmax2;
+};
+
+__device__ __forceinline__ PairGeom pair_geom(const FrontierParams &fp, int64_t q, int64_t r) {
+    PairGeom g;
+    g.dmin2 = 0.0;
+    g.dmax2 = 0.0;
+    for (int d = 0; d < fp.D; ++d) {
+        const double ql = fp.qlo[q * fp.D + d], qh = fp.qhi[q * fp.D + d];
+        const double rl = fp.rlo[r * fp.D + d], rh = fp.rhi[r * fp.D + d];
+        const double gap = fmax(0.0, fmax(rl - qh, ql - rh));
+        const double far = fmax(qh - rl, rh - ql);
+        g.dmin2 = g.dmin2 + gap * gap;
+        g.dmax2 = g.dmax2 + far * far;
+    }
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// K1: decisions
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ groups,
+               const int32_t *__restrict__ pr, uint8_t *__restrict__ dec, int32_t *__restrict__ cnt,
+               int4 *__restrict__ trace, int64_t trace_cap) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ng = fs->ngroups[fp.t];
+    const double Wtot = fs->Wtot, floorW = fs->floorW, eps_t = fs->eps_t;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t trace_base = fs->trace_count;
+    for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += warps) {
+        const Group G = groups[g];
+        const int64_t q = G.q;
+        const int j = G.j;
+        const double inv2 = fp.inv_2h2[j], inv4 = fp.inv_4h2[j], invh = fp.inv_h[j];
+        // pass 1: lower bound over the group's pairs
+        double s_dl = 0.0, s_W = 0.0;
+        for (int k = lane; k < G.cnt; k += 32) {
+            const int64_t r = pr[G.off + k];
+            const PairGeom pg = pair_geom(fp, q, r);
+            const double kmax = exp_neg(-(pg.dmax2 * inv2));
+            const double WR = fp.rW[r];
+            s_dl = s_dl + WR * kmax;
+            s_W = s_W + WR;
+        }
+        const double front = warp_sum(s_dl), Wg = warp_sum(s_W);
+        const int64_t qj = q * fp.nh + j;
+        const double fin0 = fp.fin[qj], tok0 = fp.tok[qj];
+        double Gb = fin0 + front;
+        if (fp.mono) Gb = fmax(Gb, (double)fp.qwmin[q]);
+        Gb = fmax(Gb, floorW);
+        const double cq = node_count(fp.qn, fp.q_depth, q);
+        const double rQ = fp.qrad[q] * invh;
+        // pass 2: decisions
+        double s_left = 0.0, s_fin = 0.0, s_est = 0.0;
+        int n_split = 0, n_base = 0, n_ser = 0;
+        int n_m[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = lane; k < G.cnt; k += 32) {
+            const int64_t r = pr[G.off + k];
+            const PairGeom pg = pair_geom(fp, q, r);
+            const double kmax = exp_neg(-(pg.dmax2 * inv2));
+            const double kmin = exp_neg(-(pg.dmin2 * inv2));
+            const double WR = fp.rW[r];
+            const double dl = WR * kmax;
+            const double allot = fp.tokens ? (tok0 * WR) / Wg : 0.0;
+            int method = (fp.q_leaf && fp.r_leaf) ? M_BASE : M_SPLIT;
+            int pord = 0;
+            double leftover = 0.0;
+            bool decided = false;
+            if (fp.selector != GS_SEL_EXHAUSTIVE) {
+                const double e_fd = (WR * (kmin - kmax)) * 0.5;
+                const double n_fd = (Wtot * e_fd) / (eps_t * Gb) - WR;
+                if (n_fd <= allot) {
+                    method = M_FD;
+                    leftover = allot - n_fd;
+                    decided = true;
+                    s_est = s_est + (WR * (kmin + kmax)) * 0.5;
+                }
+            }
+            if (!decided && (fp.selector == GS_SEL_RULE || fp.selector == GS_SEL_MLP) && fp.P >= 1) {
+                const double e4 = exp_neg(-(pg.dmin2 * inv4));
+                const double base = WR * e4;
+                const double rR = fp.rrad[r] * invh;
+                const double x2 = kSqrt2 * rQ;
+                const double sr = kSqrt2 * rR;
+                const double cr = node_count(fp.rn, fp.r_depth, r);
+                double best_c = INFINITY, best_need = 0.0;
+                int best_m = -1, best_p = 0;
+                for (int m = M_DH; m <= M_H2L; ++m) {
+                    int pm = 0;
+                    double needm = 0.0;
+                    for (int p = 1; p <= fp.P; ++p) {
+                        double Ep;
+                        if (m == M_DH) {
+                            Ep = (base * fp.F[p]) * rpow(rR, p);
+                        } else if (m == M_DL) {
+                            Ep = (base * fp.F[p]) * rpow(rQ, p);
+                        } else {
+                            const double tail = (x2 <= 1.0) ? 1.0 : rpow(x2, p - 1);
+                            Ep = (base * fp.F[p]) * (rpow(rQ, p) + (rpow(sr, p) * fp.BT[p]) * tail);
+                        }
+                        const double np_ = (Wtot * Ep) / (eps_t * Gb) - WR;
+                        if (np_ <= allot) {
+                            pm = p;
+                            needm = np_;
+                            break;
+                        }
+                    }
+                    if (pm == 0) continue;
+                    double c;
+                    if (m == M_DH)
+                        c = cq * fp.Dpow[pm + 1];
+                    else if (m == M_DL)
+                        c = cr * fp.Dpow[pm + 1];
+                    else
+                        c = fp.Dpow[2 * pm + 1];
+                    if (c < best_c) {
+                        best_c = c;
+                        best_m = m;
+                        best_p = pm;
+                        best_need = needm;
+                    }
+                }
+                const double c_ex = ((double)fp.D * cq) * cr;
+                if (best_m >= 0 && best_c <= c_ex) {
+                    method = best_m;
+                    pord = best_p;
+                    leftover = allot - best_need;
+                    decided = true;
+                }
+            }
+            if (!decided) {
+                if (fp.tokens) leftover = method == M_BASE ? allot + WR : allot;
+            }
+            if (!fp.tokens) leftover = 0.0;
+            s_left = s_left + leftover;
+            if (method != M_SPLIT) s_fin = s_fin + dl;
+            n_split += method == M_SPLIT;
+            n_base += method == M_BASE;
+            n_ser += (method >= M_DH && method <= M_H2L);
+            n_m[method]++;
+            dec[G.off + k] = (uint8_t)(method | (pord << 3));
+            if (trace) {
+                const int64_t ti = trace_base + G.off + k;
+                if (ti < trace_cap)
+                    trace[ti] = make_int4((int)q, (int)r, j, method | (pord << 8) | (fp.t << 16));
+            }
+        }
+        const double tok_new = warp_sum(s_left), fin_add = warp_sum(s_fin), est_add = warp_sum(s_est);
+        n_split = __reduce_add_sync(0xffffffffu, n_split);
+        n_base = __reduce_add_sync(0xffffffffu, n_base);
+        n_ser = __reduce_add_sync(0xffffffffu, n_ser);
+#pragma unroll
+        for (int m = 0; m < 6; ++m) n_m[m] = __reduce_add_sync(0xffffffffu, n_m[m]);
+        if (lane == 0) {
+            const double fin_new = fin0 + fin_add;
+            fp.fin[qj] = fin_new;
+            fp.tok[qj] = tok_new;
+            fp.est[qj] = fp.est[qj] + est_add;
+            if (!fp.q_leaf) {
+                for (int c = 1; c <= 2; ++c) {
+                    fp.fin[(2 * q + c) * fp.nh + j] = fin_new;
+                    fp.tok[(2 * q + c) * fp.nh + j] = tok_new;
+                }
+            }
+            int child_pairs, child_groups;
+            if (fp.q_leaf) {
+                child_pairs = 2 * n_split;
+                child_groups = n_split > 0;
+            } else if (fp.r_leaf) {
+                child_pairs = 2 * n_split;
+                child_groups = n_split > 0 ? 2 : 0;
+            } else {
+                child_pairs = 4 * n_split;
+                child_groups = n_split > 0 ? 2 : 0;
+            }
+            int32_t *c = cnt + g * kCols;
+            c[0] = child_pairs;
+            c[1] = child_groups;
+            c[2] = n_base;
+            c[3] = n_ser;
+            c[4] = n_base > 0;
+            for (int m = 0; m < 6; ++m)
+                if (n_m[m]) atomicAdd(&fs->method_count[m], (unsigned long long)n_m[m]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// column scan over groups (3 phases, fixed grid)
+// ---------------------------------------------------------------------------
+constexpr int kColGrid = 256;
+constexpr int kColTB = 256;
+
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long *tot) {
+    __shared__ long long wsum[kColTB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        long long s = lane < kColTB / 32 ? wsum[lane] : 0;
+        long long si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long u = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += u;
+        }
+        if (lane < kColTB / 32) wsum[lane] = si - s;
+        if (lane == kColTB / 32 - 1) *tot = si;
+    }
+    __syncthreads();
+    const long long r = wsum[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kColTB)
+k_cols_partial(const FrontierState *fs, int t, const int32_t *__restrict__ cnt, long long *partial) {
+    __shared__ long long tot;
+    const int64_t ng = fs->ngroups[t];
+    const int64_t chunk = (ng + gridDim.x - 1) / gridDim.x;
+    const int64_t g0 = blockIdx.x * chunk, g1 = min(g0 + chunk, ng);
+    for (int c = 0; c < kCols; ++c) {
+        long long s = 0;
+        for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) s += cnt[g * kCols + c];
+        block_excl_scan_ll(s, &tot);
+        if (threadIdx.x == 0) partial[c * kColGrid + blockIdx.x] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kColTB) k_cols_scan_partials(FrontierState *fs, long long *partial) {
+    __shared__ long long tot;
+    for (int c = 0; c < kCols; ++c) {
+        const long long v = partial[c * kColGrid + threadIdx.x];
+        const long long e = block_excl_scan_ll(v, &tot);
+        partial[c * kColGrid + threadIdx.x] = e;
+        if (threadIdx.x == 0) fs->totals[c] = tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kColTB)
+k_cols_offsets(const FrontierState *fs, int t, const int32_t *__restrict__ cnt, const long long *__restrict__ partial,
+               long long *off) {
+    __shared__ long long tot;
+    const int64_t ng = fs->ngroups[t];
+    const int64_t chunk = (ng + gridDim.x - 1) / gridDim.x;
+    const int64_t g0 = blockIdx.x * chunk, g1 = min(g0 + chunk, ng);
+    for (int c = 0; c < kCols; ++c) {
+        long long carry = partial[c * kColGrid + blockIdx.x];
+        for (int64_t t0 = g0; t0 < g1; t0 += blockDim.x) {
+            const int64_t g = t0 + threadIdx.x;
+            const long long v = g < g1 ? cnt[g * kCols + c] : 0;
+            const long long e = block_excl_scan_ll(v, &tot);
+            if (g < g1) off[g * kCols + c] = carry + e;
+            carry += tot;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: write the child frontier, base pairs and series actions
+// ---------------------------------------------------------------------------
+struct Caps {
+    int64_t pairs, groups, base, base_groups, series;
+};
+
+__global__ void __launch_bounds__(256)
+k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, Caps caps, const Group *__restrict__ groups,
+             const int32_t *__restrict__ pr, const uint8_t *__restrict__ dec, const int32_t *__restrict__ cnt,
+             const long long *__restrict__ off, Group *__restrict__ groups_next, int32_t *__restrict__ pr_next,
+             Group *__restrict__ base_groups, int32_t *__restrict__ base_r, SeriesEntry *__restrict__ series) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ng = fs->ngroups[t];
+    const int64_t base0 = fs->base_count, bg0 = fs->base_groups, ser0 = fs->series_count;
+    if (fs->totals[0] > caps.pairs || fs->totals[1] > caps.groups || base0 + fs->totals[2] > caps.base ||
+        bg0 + fs->totals[4] > caps.base_groups || ser0 + fs->totals[3] > caps.series) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) fs->overflow = 1;
+        return;
+    }
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += warps) {
+        const Group G = groups[g];
+        const int32_t *c = cnt + g * kCols;
+        const long long *o = off + g * kCols;
+        const int64_t o_pairs = o[0], o_groups = o[1], o_base = base0 + o[2], o_ser = ser0 + o[3];
+        const int64_t o_bg = bg0 + o[4];
+        const int n_split = q_leaf ? c[0] / 2 : (r_leaf ? c[0] / 2 : c[0] / 4);
+        const int per_child = r_leaf ? n_split : 2 * n_split;
+        int run_s = 0, run_b = 0, run_x = 0;
+        for (int k0 = 0; k0 < G.cnt; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < G.cnt;
+            const int d = valid ? dec[G.off + k] : 0xff;
+            const int m = d & 7;
+            const bool isS = valid && m == M_SPLIT, isB = valid && m == M_BASE;
+            const bool isX = valid && m >= M_DH && m <= M_H2L;
+            const unsigned bS = __ballot_sync(0xffffffffu, isS), bB = __ballot_sync(0xffffffffu, isB);
+            const unsigned bX = __ballot_sync(0xffffffffu, isX);
+            const int32_t r = valid ? pr[G.off + k] : 0;
+            if (isS) {
+                const int rank = run_s + __popc(bS & lt_mask);
+                if (!q_leaf && !r_leaf) {
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int64_t p = o_pairs + (int64_t)cc * per_child + 2 * rank;
+                        pr_next[p] = 2 * r + 1;
+                        pr_next[p + 1] = 2 * r + 2;
+                    }
+                } else if (q_leaf) {
+                    const int64_t p = o_pairs + 2 * rank;
+                    pr_next[p] = 2 * r + 1;
+                    pr_next[p + 1] = 2 * r + 2;
+                } else {
+                    for (int cc = 0; cc < 2; ++cc) pr_next[o_pairs + (int64_t)cc * per_child + rank] = r;
+                }
+            }
+            if (isB) base_r[o_base + run_b + __popc(bB & lt_mask)] = r;
+            if (isX) {
+                SeriesEntry e;
+                e.q = G.q;
+                e.r = r;
+                e.j = (int16_t)G.j;
+                e.p = (int8_t)(d >> 3);
+                e.method = (int8_t)m;
+                e.pad = 0;
+                series[o_ser + run_x + __popc(bX & lt_mask)] = e;
+            }
+            run_s += __popc(bS);
+            run_b += __popc(bB);
+            run_x += __popc(bX);
+        }
+        if (lane == 0) {
+            if (n_split > 0) {
+                if (q_leaf) {
+                    Group ng_;
+                    ng_.q = G.q; ng_.j = G.j; ng_.off = o_pairs; ng_.cnt = 2 * n_split; ng_.pad = 0;
+                    groups_next[o_groups] = ng_;
+                } else {
+                    for (int cc = 0; cc < 2; ++cc) {
+                        Group ng_;
+                        ng_.q = 2 * G.q + 1 + cc; ng_.j = G.j; ng_.off = o_pairs + (int64_t)cc * per_child;
+                        ng_.cnt = per_child; ng_.pad = 0;
+                        groups_next[o_groups + cc] = ng_;
+                    }
+                }
+            }
+            if (c[2] > 0) {
+                Group bg;
+                bg.q = G.q; bg.j = G.j; bg.off = o_base; bg.cnt = c[2]; bg.pad = 0;
+                base_groups[o_bg] = bg;
+            }
+        }
+    }
+}
+
+__global__ void k_front_advance(FrontierState *fs, int t) {
+    const int64_t npairs = fs->npairs[t];
+    fs->trace_count += npairs;
+    if (fs->overflow) {
+        fs->ngroups[t + 1] = 0;
+        fs->npairs[t + 1] = 0;
+        return;
+    }
+    fs->ngroups[t + 1] = fs->totals[1];
+    fs->npairs[t + 1] = fs->totals[0];
+    fs->base_count += fs->totals[2];
+    fs->series_count += fs->totals[3];
+    fs->base_groups += fs->totals[4];
+}
+
+// initial frontier: one group (root, j) with the single pair (root, root) per
+// bandwidth; eps for the traversal after the FP32 base-case charge.
+__global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int nh, const double *rW,
+                             const Ingest *ing, int64_t N, int D, int floor_log2, double eps) {
+    const int j = threadIdx.x;
+    if (j < nh) {
+        Group g;
+        g.q = 0; g.j = j; g.off = j; g.cnt = 1; g.pad = 0;
+        groups[j] = g;
+        pr[j] = 0;
+    }
+    if (j == 0) {
+        const double W = rW[0];
+        const double wmax = (double)__uint_as_float(ing->wmax_bits);
+        const double u = 5.9604644775390625e-08;   // 2^-24
+        double rho = 0.6931471805599453 * 64.0 * (double)(D + 4) * u;
+        rho = rho + 4.76837158203125e-07;          // 2^-21
+        rho = rho + 64.0 * u;
+        rho = rho + ldexp(1.0, -63 - floor_log2) * (((double)N * wmax) / W);
+        fs->rho = rho;
+        fs->eps_t = eps - rho;
+        fs->Wtot = W;
+        fs->floorW = W * ldexp(1.0, floor_log2);
+        fs->ngroups[0] = nh;
+        fs->npairs[0] = nh;
+        if (!(fs->eps_t > 0.5 * eps)) atomicOr(&((Ingest *)ing)->status, ST_EPS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+static bool g_taylor_ready[64] = {false};
+
+static int ensure_taylor() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && g_taylor_ready[dev]) return GS_OK;
+    double c[14];
+    double f = 1.0;
+    for (int n = 0; n < 14; ++n) {
+        if (n > 1) f = f * (double)n;
+        c[n] = 1.0 / f;
+    }
+    GS_CUDA_TRY(cudaMemcpyToSymbol(c_taylor, c, sizeof(c)));
+    if (dev >= 0 && dev < 64) g_taylor_ready[dev] = true;
+    return GS_OK;
+}
+
+static unsigned long long binom_u64(int a, int b) {
+    unsigned long long r = 1;
+    for (int i = 1; i <= b; ++i) r = r * (unsigned long long)(a - b + i) / (unsigned long long)i;
+    return r;
+}
+
+static double factd(int m) {
+    double f = 1.0;
+    for (int q = 2; q <= m; ++q) f = f * (double)q;
+    return f;
+}
+
+int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
+    cudaStream_t st = cx.st;
+    int rc = cx.check("before frontier");
+    if (rc) return rc;
+    rc = ensure_taylor();
+    if (rc) return rc;
+    FrontierParams fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.D = in.D;
+    fp.nh = in.nh;
+    fp.P = in.P;
+    fp.selector = in.selector;
+    fp.tokens = in.tokens;
+    fp.mono = in.mono;
+    fp.floor_log2 = in.floor_log2;
+    fp.qn = in.qt->n;
+    fp.rn = in.rt->n;
+    fp.qlo = in.qt->lo; fp.qhi = in.qt->hi; fp.qrad = in.qt->rad; fp.qwmin = in.qt->wmin;
+    fp.rlo = in.rt->lo; fp.rhi = in.rt->hi; fp.rrad = in.rt->rad; fp.rW = in.rt->W;
+    fp.inv_2h2 = fb.inv_2h2; fp.inv_4h2 = fb.inv_4h2; fp.inv_h = fb.inv_h;
+    fp.fin = fb.fin; fp.tok = fb.tok; fp.est = fb.est;
+    const int D = in.D;
+    // Lemma 4-6 factor C(D+p-1, D-1) / sqrt((floor(p/D)!)^(D-p') (ceil(p/D)!)^p'),
+    // C(D+p-1, D), and D^k, all from exact integers
+    for (int p = 1; p <= 16 && p <= in.P; ++p) {
+        const int pp = p % D;
+        double prod = 1.0;
+        for (int i = 0; i < D - pp; ++i) prod = prod * factd(p / D);
+        for (int i = 0; i < pp; ++i) prod = prod * factd((p + D - 1) / D);
+        fp.F[p] = (double)binom_u64(D + p - 1, D - 1) / sqrt(prod);
+        fp.BT[p] = (double)binom_u64(D + p - 1, D);
+    }
+    fp.Dpow[0] = 1.0;
+    for (int k = 1; k < 34; ++k) fp.Dpow[k] = fp.Dpow[k - 1] * (double)D;
+
+    k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, in.ing, in.rt->n, in.D,
+                                   in.floor_log2, in.eps);
+    cx.launches += 1;
+    if ((rc = cx.check("k_front_init"))) return rc;
+    const int T = in.qt->depth > in.rt->depth ? in.qt->depth : in.rt->depth;
+    Caps caps;
+    caps.pairs = fb.cap_pairs;
+    caps.groups = fb.cap_groups;
+    caps.base = fb.cap_base;
+    caps.base_groups = fb.cap_base_groups;
+    caps.series = fb.cap_series;
+    int cur = 0;
+    const int grid = fb.grid_warps / 8;
+    for (int t = 0; t <= T; ++t) {
+        fp.t = t;
+        fp.q_depth = t < in.qt->depth ? t : in.qt->depth;
+        fp.r_depth = t < in.rt->depth ? t : in.rt->depth;
+        fp.q_leaf = t >= in.qt->depth;
+        fp.r_leaf = t >= in.rt->depth;
+        k_front_decide<<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
+                                             fb.trace_cap);
+        if ((rc = cx.check("k_front_decide"))) return rc;
+        k_cols_partial<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial);
+        if ((rc = cx.check("k_cols_partial"))) return rc;
+        k_cols_scan_partials<<<1, kColTB, 0, st>>>(fb.fs, fb.partial);
+        if ((rc = cx.check("k_cols_scan_partials"))) return rc;
+        k_cols_offsets<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial, fb.off);
+        if ((rc = cx.check("k_cols_offsets"))) return rc;
+        k_front_emit<<<grid, 256, 0, st>>>(fb.fs, t, fp.q_leaf, fp.r_leaf, caps, fb.groups[cur], fb.pr[cur], fb.dec,
+                                           fb.cnt, fb.off, fb.groups[cur ^ 1], fb.pr[cur ^ 1], fb.base_groups,
+                                           fb.base_r, fb.series);
+        if ((rc = cx.check("k_front_emit"))) return rc;
+        k_front_advance<<<1, 1, 0, st>>>(fb.fs, t);
+        if ((rc = cx.check("k_front_advance"))) return rc;
+        cx.launches += 6;
+        cur ^= 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "frontier launch");
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include "../../include/gs.h"
+#include "gs_frontier.cuh"
+#include "gs_tree.cuh"
 
 namespace gs {
 
@@ -16,6 +18,7 @@ enum : unsigned {
     ST_CAPACITY = 1u << 2,
     ST_TIMEOUT = 1u << 3,
     ST_INTERNAL = 1u << 4,
+    ST_EPS = 1u << 5,        // eps too small for the FP32 base-case error charge
 };
 
 // Summary of the inputs, produced on the device by the ingest kernels.
@@ -38,6 +41,11 @@ struct CallCtx {
     int ev_phase[kMaxMarks];
     int nev = 0;
     int open_phase = -1;
+    // GS_DEBUG_SYNC=1 in the environment: synchronise and check after every
+    // launch site that calls check(), naming the kernel in the error.
+    bool debug = debug_sync_enabled();
+    static bool debug_sync_enabled();
+    int check(const char *what);
 
     // Start timing `phase` (closing any open one).  No-op without stats.
     void phase(int ph) {
@@ -91,6 +99,63 @@ cudaError_t launch_ingest(Ingest *ing, const void *queries, int64_t M, const voi
 int exhaustive_sum(const void *queries, int64_t M, const void *refs, const float *weights,
                    int64_t N, int D, int dtype, const double *h, int nh, const Ingest *ing,
                    double *out, CallCtx &cx);
+
+// ---- dual-tree path -------------------------------------------------------
+struct TraversalIn {
+    const TreeDev *qt = nullptr, *rt = nullptr;
+    const Ingest *ing = nullptr;
+    const float *weights = nullptr;
+    const double *h = nullptr;   // host
+    int D = 0, nh = 0, P = 0, selector = 0, tokens = 1, mono = 0, floor_log2 = -40;
+    double eps = 0.0;
+};
+
+struct FrontierBufs {
+    FrontierState *fs = nullptr;
+    Group *groups[2] = {nullptr, nullptr};
+    int32_t *pr[2] = {nullptr, nullptr};
+    uint8_t *dec = nullptr;
+    int32_t *cnt = nullptr;
+    long long *off = nullptr, *partial = nullptr;
+    Group *base_groups = nullptr;
+    int32_t *base_r = nullptr;
+    SeriesEntry *series = nullptr;
+    double *fin = nullptr, *tok = nullptr, *est = nullptr;
+    double *inv_2h2 = nullptr, *inv_4h2 = nullptr, *inv_h = nullptr, *inv_s = nullptr;
+    unsigned long long *evals = nullptr;
+    int4 *trace = nullptr;
+    int64_t trace_cap = 0;
+    int64_t cap_pairs = 0, cap_groups = 0, cap_base = 0, cap_base_groups = 0, cap_series = 0;
+    int grid_warps = 0;
+};
+
+int build_tree(const void *x, const float *w, int64_t n, int D, int dtype, int L, const Ingest *ing, int DP,
+               int rec_stride, bool with_weights, CallCtx &cx, TreeDev *out);
+int build_moments(TreeDev &t, const float *w, const SeriesTables &tb, CallCtx &cx);
+void free_tree(TreeDev &t, cudaStream_t st);
+int build_series_tables(int D, int P, SeriesTables *tb, cudaStream_t st);
+void free_series_tables(SeriesTables *tb, cudaStream_t st);
+int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx);
+int run_basecase(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, CallCtx &cx);
+int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTables *tb, double *Gq,
+                         double *B, int32_t *pL, double *out, CallCtx &cx);
+
+// Padded dimension used by the FP32 record layouts (1..8, 12, 16, 24, 32).
+int dp_for(int D);
+int plimit_for(int D);
+
+// Optional outputs of a dual-tree call used by tests and tools.
+struct TraceOut {
+    int32_t *trace = nullptr;     // device, 4 x cap int32
+    int64_t cap = 0;
+    int64_t *len = nullptr;       // host
+    int32_t *qperm = nullptr;     // device, M (may be NULL)
+    int32_t *rperm = nullptr;     // device, N (may be NULL)
+};
+
+int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
+                 int dtype, const double *h, int nh, double eps, double *out, const gs_opts &o, CallCtx &cx,
+                 Ingest *ing, TraceOut *trace, unsigned *status_out);
 
 // Instruction-rate probe (see gs_probe_rates).
 int probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, cudaStream_t st);

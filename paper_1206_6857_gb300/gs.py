@@ -82,6 +82,7 @@ SIGNATURES = {
     "gs_sum": (ctypes.c_int, _SUM_ARGS),
     "gs_sum_host": (ctypes.c_int, _SUM_ARGS),
     "gs_probe_rates": (ctypes.c_int, [_VP, _VP, _VP]),
+    "gs_sum_trace": (ctypes.c_int, _SUM_ARGS + [_VP, _I64, _VP, _VP, _VP]),
 }
 
 
@@ -164,6 +165,31 @@ def gs_sum(queries, refs, weights, h, eps, out=None, opts: gs_opts | None = None
         _check(rc)
         return out
     return rc, out
+
+
+def gs_sum_trace(queries, refs, weights, h, eps, opts: gs_opts | None = None, stream=None,
+                 trace_cap: int = 1 << 22, stats: gs_stats | None = None):
+    """gs_sum (eps > 0) plus the traversal record: returns (out, trace, qperm,
+    rperm) with trace an (n, 4) int32 CUDA tensor of (query node, reference
+    node, bandwidth, action | order << 8 | iteration << 16)."""
+    import torch
+    M, D = queries.shape
+    N = refs.shape[0]
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    dev = queries.device
+    out = torch.empty((M, hh.size), dtype=torch.float64, device=dev)
+    tr = torch.empty((trace_cap, 4), dtype=torch.int32, device=dev)
+    qperm = torch.empty(M, dtype=torch.int32, device=dev)
+    rperm = torch.empty(N, dtype=torch.int32, device=dev)
+    n = ctypes.c_int64()
+    _check(load().gs_sum_trace(_VP(queries.data_ptr()), M, _VP(refs.data_ptr()), _VP(weights.data_ptr()), N, D,
+                               _dtype_code(queries), hh.ctypes.data, hh.size, float(eps), _VP(out.data_ptr()),
+                               ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream),
+                               ctypes.byref(stats) if stats is not None else None, _VP(tr.data_ptr()), trace_cap,
+                               ctypes.byref(n), _VP(qperm.data_ptr()), _VP(rperm.data_ptr())))
+    if n.value > trace_cap:
+        raise GSError(GS_ERR_CAPACITY, "trace of %d records exceeds trace_cap=%d" % (n.value, trace_cap))
+    return out, tr[:n.value], qperm, rperm
 
 
 def gs_sum_host(queries: np.ndarray, refs: np.ndarray, weights: np.ndarray, h, eps,

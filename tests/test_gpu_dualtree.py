@@ -1,0 +1,170 @@
+"""GPU dual-tree path against the CPU references.
+
+* tree partitions and the full traversal record (every pair of every
+  iteration, with the action and series order taken) are bit-exact against
+  oracle.dualtree on the same seeded inputs;
+* every result is within eps of the FP64 exhaustive oracle,
+  |G~ - G| <= eps * max(G, 2^-40 W), query by query.
+"""
+import numpy as np
+import pytest
+
+from helpers import rel_err
+from oracle import dualtree as T
+from oracle import exhaustive as oracle_ex
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+    from paper_1206_6857_gb300 import build, gs as _gs
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    _gs.load()
+    return _gs
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _opts(gs, leaf=32, selector=0, tokens=True, plimit=0):
+    o = gs.gs_opts_default()
+    o.leaf_size = leaf
+    o.selector = selector
+    o.no_tokens = 0 if tokens else 1
+    o.plimit = plimit
+    return o
+
+
+def _cpu_trace(q, r, w, mono, h, eps, leaf, selector, tokens, plimit):
+    rt = T.build_tree(r, w, leaf)
+    qt = rt if mono else T.build_tree(q, np.ones(q.shape[0], np.float32), leaf)
+    trav = T.traverse(qt, rt, mono, h, eps, plimit=plimit or None, selector=selector, tokens=tokens,
+                      w_max=float(w.max()))
+    rec = []
+    for t, it in enumerate(trav.iters):
+        code = it["method"] | (it["p"] << 8) | (t << 16)
+        rec.append(np.stack([it["q"], it["r"], it["j"], code], axis=1))
+    return qt, rt, np.concatenate(rec).astype(np.int64), trav
+
+
+CASES = [
+    # seed, n, D, m (None: monochromatic), eps, leaf, selector, tokens, plimit, h
+    (1, 3000, 2, None, 1e-2, 32, 0, True, 0, [0.003, 0.03, 0.3]),
+    (2, 2500, 3, None, 1e-3, 16, 0, True, 0, [0.01, 0.05, 0.2, 0.8]),
+    (3, 2000, 3, 1500, 1e-2, 32, 0, True, 0, [0.02, 0.2]),
+    (4, 1800, 5, None, 1e-2, 16, 0, True, 0, [0.05, 0.3, 1.0]),
+    (5, 2200, 2, None, 1e-2, 8, 2, True, 0, [0.01, 0.1]),
+    (6, 2200, 2, None, 1e-2, 32, 0, False, 0, [0.01, 0.1]),
+    (7, 1500, 4, None, 1e-2, 32, 3, True, 0, [0.1]),
+    (8, 1200, 7, 900, 1e-2, 16, 0, True, 0, [0.1, 0.5]),
+    (9, 2000, 2, None, 1e-3, 32, 0, True, 3, [0.05, 0.2]),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_n%d_d%d" % (c[0], c[1], c[2]))
+def test_traversal_bit_exact_and_within_eps(gs, case):
+    seed, n, D, m, eps, leaf, sel, tok, plim, h = case
+    q, r, w = synth.small_random(seed, n, D, m=m)
+    mono = m is None
+    h = np.asarray(h, np.float64)
+    tq = _dev(q)
+    tr = tq if mono else _dev(r)
+    out, trace, qperm, rperm = gs.gs_sum_trace(tq, tr, _dev(w), h, eps, opts=_opts(gs, leaf, sel, tok, plim))
+    qt, rt, want, trav = _cpu_trace(q, r, w, mono, h, eps, leaf, sel, tok, plim)
+    assert np.array_equal(rperm.cpu().numpy(), rt.perm)
+    assert np.array_equal(qperm.cpu().numpy(), qt.perm)
+    got = trace.cpu().numpy().astype(np.int64)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    bad = np.flatnonzero(np.any(got != want, axis=1))
+    assert bad.size == 0, "first mismatch at record %d: gpu %s cpu %s" % (bad[0], got[bad[0]], want[bad[0]])
+    exact = oracle_ex.gauss_sum(q, r, w, h)
+    err = rel_err(out.cpu().numpy(), exact, float(w.astype(np.float64).sum()))
+    assert err.max() <= eps, err.max()
+
+
+def _check_eps(gs, wl, eps=None, opts=None, sample=None):
+    eps = wl.eps if eps is None else eps
+    tq = _dev(wl.queries)
+    tr = tq if wl.mono else _dev(wl.refs)
+    st = gs.gs_stats()
+    out = gs.gs_sum(tq, tr, _dev(wl.weights), wl.h, eps, opts=opts, stats=st).cpu().numpy()
+    qs, o = wl.queries, out
+    if sample is not None:
+        idx = np.sort(np.random.default_rng(0).choice(wl.M, sample, replace=False))
+        qs, o = wl.queries[idx], out[idx]
+    exact = oracle_ex.gauss_sum(qs, wl.refs, wl.weights, wl.h)
+    err = rel_err(o, exact, float(wl.weights.astype(np.float64).sum()))
+    assert err.max() <= eps, (err.max(), st.as_dict())
+    return st
+
+
+def test_config1_full_size_every_query(gs):
+    st = _check_eps(gs, synth.config1())
+    assert st.pairs_fd + st.pairs_dh + st.pairs_dl + st.pairs_h2l > 0
+
+
+def test_config2_scaled_sweep(gs):
+    _check_eps(gs, synth.config2(0.02))
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_config3_scaled_series_regime(gs, eps):
+    _check_eps(gs, synth.config3(0.02, eps=eps), eps=eps)
+
+
+def test_config4_scaled_bichromatic_d16(gs):
+    _check_eps(gs, synth.config4(0.005))
+
+
+def test_config5_some_batched_problems(gs):
+    for i in range(6):
+        _check_eps(gs, synth.config5_problem(i, scale=0.1))
+
+
+def test_config2_full_size_sampled(gs):
+    st = _check_eps(gs, synth.config2(), sample=48)
+    assert st.point_pairs_base < 1e12 * 16      # the tree pruned something
+
+
+@pytest.mark.parametrize("n,m,D", [(1, 1, 2), (5, 3, 1), (40, 1, 3), (1, 50, 2), (64, 64, 32)])
+def test_degenerate_sizes(gs, n, m, D):
+    q, r, w = synth.small_random(n * 31 + m, n, D, m=m)
+    h = np.array([0.01, 0.2, 3.0])
+    out = gs.gs_sum(_dev(q), _dev(r), _dev(w), h, 1e-2, opts=_opts(gs, leaf=2)).cpu().numpy()
+    exact = oracle_ex.gauss_sum(q, r, w, h)
+    assert rel_err(out, exact, float(w.astype(np.float64).sum())).max() <= 1e-2
+
+
+def test_coincident_points(gs):
+    x = np.tile(np.array([[0.3, 0.7]], np.float32), (500, 1))
+    w = np.full(500, 0.002, np.float32)
+    out = gs.gs_sum(_dev(x), _dev(x), _dev(w), [1e-3, 1.0], 1e-2).cpu().numpy()
+    assert np.allclose(out, 1.0, rtol=1e-2)
+
+
+@pytest.mark.parametrize("leaf", [2, 5, 64, 128])
+def test_leaf_sizes(gs, leaf):
+    q, r, w = synth.small_random(77, 3000, 3)
+    h = np.array([0.02, 0.2])
+    out = gs.gs_sum(_dev(q), _dev(q), _dev(w), h, 1e-2, opts=_opts(gs, leaf=leaf)).cpu().numpy()
+    exact = oracle_ex.gauss_sum(q, r, w, h)
+    assert rel_err(out, exact).max() <= 1e-2
+
+
+def test_capacity_retry(gs):
+    q, r, w = synth.small_random(78, 4000, 2)
+    h = np.array([0.05])
+    o = _opts(gs)
+    o.pair_capacity = 2000
+    st = gs.gs_stats()
+    out = gs.gs_sum(_dev(q), _dev(q), _dev(w), h, 1e-2, opts=o, stats=st).cpu().numpy()
+    assert st.retries >= 1
+    exact = oracle_ex.gauss_sum(q, r, w, h)
+    assert rel_err(out, exact).max() <= 1e-2
