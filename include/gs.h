@@ -70,9 +70,20 @@ typedef struct gs_opts {
                                |G~ - G| <= eps * max(G, 2^floor_log2 * W), W = sum w;
                                0 -> -40                                                 */
     int32_t reserved0;
-    int64_t pair_capacity;  /* frontier / work-list capacity in pairs; 0 -> automatic  */
+    int64_t pair_capacity;  /* initial work-list capacity in pairs; 0 -> automatic     */
+    double  cost_weight[4]; /* multipliers of the Fig. 6 costs c_DH, c_DL, c_H2L and
+                               c_Direct; all 0 -> GS_COST_* defaults below (calibrated
+                               to GB300 unit costs); all 1 -> the paper's cost model   */
     int64_t reserved[4];
 } gs_opts;
+
+/* Default cost weights: a series action runs in FP64 on the GPU while a
+ * direct (base-case) term is an FP32 exponential, so on GB300 one unit of
+ * series cost is weighted 32 units of direct cost. */
+#define GS_COST_DH      32.0
+#define GS_COST_DL      32.0
+#define GS_COST_H2L     32.0
+#define GS_COST_DIRECT   1.0
 
 /* Phases timed into gs_stats.ms_phase (CUDA events on the call's stream). */
 #define GS_PH_INGEST    0   /* input checks and packing                              */

@@ -230,12 +230,20 @@ class Traversal:
     W: float = 0.0
 
 
+COST_WEIGHTS = (32.0, 32.0, 32.0, 1.0)
+
+
 def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None = None,
              selector: int = SEL_RULE, tokens: bool = True, floor_log2: int = -40,
-             w_max: float = None):
+             w_max: float = None, cost_weight=COST_WEIGHTS):
     """Run the level-synchronous traversal; returns a Traversal whose iters[t]
     holds the frontier (q, r, j) and the decision (method, p, E) of every
-    pair in the exact order the GPU processes them."""
+    pair in the exact order the GPU processes them.
+
+    bestMethod (Fig. 6) compares the paper's costs c_DH = N_Q D^{p+1},
+    c_DL = N_R D^{p+1}, c_H2L = D^{2p+1} and c_Direct = D N_Q N_R, each
+    multiplied by its weight in cost_weight (all ones: the paper's model)."""
+    kw = [float(v) for v in cost_weight]
     h = np.asarray(h, np.float64)
     nh = h.size
     D = qt.D
@@ -345,18 +353,18 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
                     Em[ok] = Ep[ok]
                 found = pm > 0
                 if m == DH:
-                    c = cnt_q[pq] * np.array([Dpow[p + 1] for p in pm])
+                    c = (cnt_q[pq] * np.array([Dpow[p + 1] for p in pm])) * kw[0]
                 elif m == DL:
-                    c = cnt_r[pr] * np.array([Dpow[p + 1] for p in pm])
+                    c = (cnt_r[pr] * np.array([Dpow[p + 1] for p in pm])) * kw[1]
                 else:
-                    c = np.array([Dpow[2 * p + 1] for p in pm])
+                    c = np.array([Dpow[2 * p + 1] for p in pm]) * kw[2]
                 better = found & (c < best_c)
                 best_c[better] = c[better]
                 best_m[better] = m
                 best_p[better] = pm[better]
                 best_need[better] = needm[better]
                 best_E[better] = Em[better]
-            c_ex = (float(D) * cnt_q[pq]) * cnt_r[pr]
+            c_ex = ((float(D) * cnt_q[pq]) * cnt_r[pr]) * kw[3]
             series = (~use_fd) & (best_m >= 0) & (best_c <= c_ex)   # ties favour the series method (Fig. 6)
             method[series] = best_m[series]
             porder[series] = best_p[series]

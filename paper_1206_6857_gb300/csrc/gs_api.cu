@@ -123,6 +123,10 @@ int gs_opts_default(gs_opts *o) {
     o->leaf_size = 32;
     o->floor_log2 = -40;
     o->selector = GS_SEL_RULE;
+    o->cost_weight[0] = GS_COST_DH;
+    o->cost_weight[1] = GS_COST_DL;
+    o->cost_weight[2] = GS_COST_H2L;
+    o->cost_weight[3] = GS_COST_DIRECT;
     return GS_OK;
 }
 
@@ -138,7 +142,18 @@ static int sum_impl(const void *queries, int64_t M, const void *refs, const floa
         o = *opts;
         if (o.leaf_size == 0) o.leaf_size = 32;
         if (o.floor_log2 == 0) o.floor_log2 = -40;
+        if (o.cost_weight[0] == 0 && o.cost_weight[1] == 0 && o.cost_weight[2] == 0 && o.cost_weight[3] == 0) {
+            o.cost_weight[0] = GS_COST_DH;
+            o.cost_weight[1] = GS_COST_DL;
+            o.cost_weight[2] = GS_COST_H2L;
+            o.cost_weight[3] = GS_COST_DIRECT;
+        }
     }
+    for (int k = 0; k < 4; ++k)
+        if (!(o.cost_weight[k] > 0.0) || !isfinite(o.cost_weight[k])) {
+            set_error("cost_weight[%d]=%g must be finite and positive", k, o.cost_weight[k]);
+            return GS_ERR_ARG;
+        }
     if (o.selector < GS_SEL_RULE || o.selector > GS_SEL_EXHAUSTIVE) {
         set_error("unknown selector %d", o.selector);
         return GS_ERR_ARG;

@@ -23,6 +23,8 @@
 
 namespace gs {
 
+constexpr int kLeavesPerRun = 4;
+
 struct BaseParams {
     const float *qrec, *rrec;
     int64_t qn, rn;
@@ -60,9 +62,17 @@ k_basecase(BaseParams bp, const FrontierState *__restrict__ fs, const Group *__r
 #pragma unroll
             for (int d = 0; d < DP; ++d) xq[s][d] = bp.qrec[pos * NT + d];
         }
+        // three-level summation: FP32 over one reference leaf, FP32 over up to
+        // kLeavesPerRun leaves, FP64 across runs (keeps the FP64 pipe off the
+        // critical path while bounding the FP32 sums to a few hundred terms)
         double acc[QPL];
+        float run[QPL];
 #pragma unroll
-        for (int s = 0; s < QPL; ++s) acc[s] = 0.0;
+        for (int s = 0; s < QPL; ++s) {
+            acc[s] = 0.0;
+            run[s] = 0.f;
+        }
+        int in_run = 0;
         unsigned long long grp_refs = 0;
         for (int k = 0; k < G.cnt; ++k) {
             const int64_t rnode = base_r[G.off + k];
@@ -100,9 +110,19 @@ k_basecase(BaseParams bp, const FrontierState *__restrict__ fs, const Group *__r
                 }
             }
 #pragma unroll
-            for (int s = 0; s < QPL; ++s) acc[s] += (double)part[s];
+            for (int s = 0; s < QPL; ++s) run[s] += part[s];
+            if (++in_run == kLeavesPerRun) {
+#pragma unroll
+                for (int s = 0; s < QPL; ++s) {
+                    acc[s] += (double)run[s];
+                    run[s] = 0.f;
+                }
+                in_run = 0;
+            }
             grp_refs += (unsigned long long)(re - rb);
         }
+#pragma unroll
+        for (int s = 0; s < QPL; ++s) acc[s] += (double)run[s];
 #pragma unroll
         for (int s = 0; s < QPL; ++s) {
             const int qq = lane + 32 * s;

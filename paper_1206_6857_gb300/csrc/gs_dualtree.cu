@@ -41,35 +41,55 @@ static int sm_count() {
 
 static void free_bufs(FrontierBufs &fb, cudaStream_t st) {
     // inv_4h2, inv_h and inv_s live inside the inv_2h2 allocation
-    void *ptrs[] = {fb.fs, fb.groups[0], fb.groups[1], fb.pr[0], fb.pr[1], fb.dec, fb.cnt, fb.off, fb.partial,
-                    fb.base_groups, fb.base_r, fb.series, fb.fin, fb.tok, fb.est, fb.inv_2h2, fb.evals};
+    void *ptrs[] = {fb.fs, fb.groups[0], fb.groups[1], fb.pr[0], fb.pr[1], fb.dec, fb.geo, fb.cnt, fb.off,
+                    fb.partial, fb.base_groups, fb.base_r, fb.series[0], fb.series[1], fb.series[2], fb.fin,
+                    fb.tok, fb.est, fb.inv_2h2, fb.evals};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, st);
-    int4 *tr = fb.trace;
-    int64_t tc = fb.trace_cap;
-    const int gw = fb.grid_warps;
-    fb = FrontierBufs();
-    fb.trace = tr;
-    fb.trace_cap = tc;
-    fb.grid_warps = gw;
+    FrontierBufs keep;
+    keep.trace = fb.trace;
+    keep.trace_cap = fb.trace_cap;
+    keep.grid_warps = fb.grid_warps;
+    keep.host_totals = fb.host_totals;
+    fb = keep;
 }
 
 #define GS_ALLOC(ptr, bytes) GS_CUDA_TRY(cudaMallocAsync((void **)&(ptr), (size_t)(bytes), st))
 
-static int alloc_bufs(FrontierBufs &fb, int64_t nodesQ, int nh, const double *h, cudaStream_t st) {
+// pinned host scratch for the per-iteration totals (one per host thread)
+static int64_t *host_scratch() {
+    static thread_local int64_t *p = nullptr;
+    if (!p && cudaMallocHost((void **)&p, 64 * sizeof(int64_t)) != cudaSuccess) p = nullptr;
+    return p;
+}
+
+static int alloc_bufs(FrontierBufs &fb, int64_t nodesQ, int nh, const double *h, int64_t initial, cudaStream_t st) {
+    fb.host_totals = host_scratch();
+    if (!fb.host_totals) {
+        set_error("pinned host allocation failed");
+        return GS_ERR_OOM;
+    }
     GS_ALLOC(fb.fs, sizeof(FrontierState));
     GS_CUDA_TRY(cudaMemsetAsync(fb.fs, 0, sizeof(FrontierState), st));
     for (int b = 0; b < 2; ++b) {
         GS_ALLOC(fb.groups[b], fb.cap_groups * sizeof(Group));
-        GS_ALLOC(fb.pr[b], fb.cap_pairs * sizeof(int32_t));
+        fb.cap_pr[b] = initial;
+        GS_ALLOC(fb.pr[b], initial * sizeof(int32_t));
     }
-    GS_ALLOC(fb.dec, fb.cap_pairs);
+    fb.cap_pairs = initial;
+    GS_ALLOC(fb.dec, initial);
+    fb.cap_geo = 3 * initial;
+    GS_ALLOC(fb.geo, 3 * initial * sizeof(double));
     GS_ALLOC(fb.cnt, fb.cap_groups * kCols * sizeof(int32_t));
     GS_ALLOC(fb.off, fb.cap_groups * kCols * sizeof(long long));
     GS_ALLOC(fb.partial, kCols * 256 * sizeof(long long));
     GS_ALLOC(fb.base_groups, fb.cap_base_groups * sizeof(Group));
-    GS_ALLOC(fb.base_r, fb.cap_base * sizeof(int32_t));
-    GS_ALLOC(fb.series, fb.cap_series * sizeof(SeriesEntry));
+    fb.cap_base = initial;
+    GS_ALLOC(fb.base_r, initial * sizeof(int32_t));
+    for (int m = 0; m < 3; ++m) {
+        fb.cap_series[m] = initial / 4 > 1024 ? initial / 4 : 1024;
+        GS_ALLOC(fb.series[m], fb.cap_series[m] * sizeof(SeriesEntry));
+    }
     const size_t ns = (size_t)nodesQ * nh * sizeof(double);
     GS_ALLOC(fb.fin, ns);
     GS_ALLOC(fb.tok, ns);
@@ -159,91 +179,69 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
     in.floor_log2 = o.floor_log2;
     in.eps = eps;
 
-    const int64_t lq = 1ll << qt.depth, lr = 1ll << rt.depth;
-    const int64_t all_pairs = (int64_t)nh * lq * lr;
-    auto clampcap = [&](int64_t want) { return want < all_pairs ? want : all_pairs; };
+    for (int k = 0; k < 4; ++k) in.cost_w[k] = o.cost_weight[k];
+    const int64_t lq = 1ll << qt.depth;
     FrontierBufs fb;
     fb.grid_warps = sm_count() * 64;
     if (trace && trace->trace) {
         fb.trace = (int4 *)trace->trace;
         fb.trace_cap = trace->cap;
     }
-    int64_t mult = 1;
     double *Gq = nullptr, *B = nullptr;
     int32_t *pL = nullptr;
     FrontierState hfs;
     Ingest hing;
-    int attempt = 0;
-    for (;; ++attempt) {
-        if (o.pair_capacity > 0) {
-            fb.cap_pairs = fb.cap_base = fb.cap_series = o.pair_capacity << (2 * attempt);
-        } else {
-            fb.cap_pairs = clampcap((int64_t)64 * nh * lq * mult > (1 << 20) ? (int64_t)64 * nh * lq * mult : (1 << 20));
-            fb.cap_base = clampcap((int64_t)256 * nh * lq * mult > (1 << 20) ? (int64_t)256 * nh * lq * mult : (1 << 20));
-            fb.cap_series = clampcap((int64_t)16 * nh * lq * mult > (1 << 20) ? (int64_t)16 * nh * lq * mult : (1 << 20));
+    fb.cap_groups = (int64_t)nh * lq;
+    fb.cap_base_groups = (int64_t)nh * lq;
+    const int64_t initial = o.pair_capacity > 0 ? o.pair_capacity : ((int64_t)16 * nh * lq > (1 << 16) ? (int64_t)16 * nh * lq : (1 << 16));
+    rc = alloc_bufs(fb, qt.nodes, nh, h, initial, st);
+    if (!rc) {
+        cx.phase(GS_PH_FRONTIER);
+        rc = run_frontier(in, fb, cx);
+    }
+    if (!rc) {
+        GS_ALLOC(Gq, (size_t)qt.n * nh * sizeof(double));
+        GS_CUDA_TRY(cudaMemsetAsync(Gq, 0, (size_t)qt.n * nh * sizeof(double), st));
+        if (series) {
+            GS_ALLOC(B, (size_t)qt.nodes * nh * tb.T * sizeof(double));
+            GS_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)qt.nodes * nh * tb.T * sizeof(double), st));
+            GS_ALLOC(pL, (size_t)qt.nodes * nh * sizeof(int32_t));
+            GS_CUDA_TRY(cudaMemsetAsync(pL, 0, (size_t)qt.nodes * nh * sizeof(int32_t), st));
         }
-        fb.cap_groups = (int64_t)nh * lq;
-        fb.cap_base_groups = (int64_t)nh * lq;
-        rc = alloc_bufs(fb, qt.nodes, nh, h, st);
-        if (!rc) {
-            cx.phase(GS_PH_FRONTIER);
-            rc = run_frontier(in, fb, cx);
-        }
-        if (!rc) {
-            GS_ALLOC(Gq, (size_t)qt.n * nh * sizeof(double));
-            GS_CUDA_TRY(cudaMemsetAsync(Gq, 0, (size_t)qt.n * nh * sizeof(double), st));
-            if (series) {
-                GS_ALLOC(B, (size_t)qt.nodes * nh * tb.T * sizeof(double));
-                GS_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)qt.nodes * nh * tb.T * sizeof(double), st));
-                GS_ALLOC(pL, (size_t)qt.nodes * nh * sizeof(int32_t));
-                GS_CUDA_TRY(cudaMemsetAsync(pL, 0, (size_t)qt.nodes * nh * sizeof(int32_t), st));
-            }
-            rc = run_basecase(in, fb, Gq, DP, cx);
-        }
-        if (!rc) rc = run_series_and_final(in, fb, series ? &tb : nullptr, Gq, B, pL, out, cx);
-        if (!rc && trace && trace->qperm) {
-            cudaError_t e = cudaMemcpyAsync(trace->qperm, qt.perm, qt.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) rc = cuda_fail(e, "trace query permutation");
-        }
-        if (!rc && trace && trace->rperm) {
-            cudaError_t e = cudaMemcpyAsync(trace->rperm, rt.perm, rt.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) rc = cuda_fail(e, "trace reference permutation");
-        }
-        if (!rc) {
-            cudaError_t e = cudaMemcpyAsync(&hfs, fb.fs, sizeof(hfs), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&hing, ing, sizeof(hing), cudaMemcpyDeviceToHost, st);
-            unsigned long long hev = 0;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&hev, fb.evals, sizeof(hev), cudaMemcpyDeviceToHost, st);
-            cx.end();
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) rc = cuda_fail(e, "dual-tree");
-            if (!rc && cx.stats) {
-                gs_stats *s = cx.stats;
-                s->pairs_fd = (int64_t)hfs.method_count[M_FD];
-                s->pairs_dh = (int64_t)hfs.method_count[M_DH];
-                s->pairs_dl = (int64_t)hfs.method_count[M_DL];
-                s->pairs_h2l = (int64_t)hfs.method_count[M_H2L];
-                s->pairs_base = (int64_t)hfs.method_count[M_BASE];
-                s->pairs_split = (int64_t)hfs.method_count[M_SPLIT];
-                s->point_pairs_base = (int64_t)hev;
-                s->levels = (qt.depth > rt.depth ? qt.depth : rt.depth) + 1;
-                s->retries = attempt;
-                s->fp32_rel_bound = hfs.rho;
-                s->eps_traversal = hfs.eps_t;
-            }
+        rc = run_basecase(in, fb, Gq, DP, cx);
+    }
+    if (!rc) rc = run_series_and_final(in, fb, series ? &tb : nullptr, Gq, B, pL, out, cx);
+    if (!rc && trace && trace->qperm) {
+        cudaError_t e = cudaMemcpyAsync(trace->qperm, qt.perm, qt.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "trace query permutation");
+    }
+    if (!rc && trace && trace->rperm) {
+        cudaError_t e = cudaMemcpyAsync(trace->rperm, rt.perm, rt.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "trace reference permutation");
+    }
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(&hfs, fb.fs, sizeof(hfs), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hing, ing, sizeof(hing), cudaMemcpyDeviceToHost, st);
+        unsigned long long hev = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hev, fb.evals, sizeof(hev), cudaMemcpyDeviceToHost, st);
+        cx.end();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "dual-tree");
+        if (!rc && cx.stats) {
+            gs_stats *s = cx.stats;
+            s->pairs_fd = (int64_t)hfs.method_count[M_FD];
+            s->pairs_dh = (int64_t)hfs.method_count[M_DH];
+            s->pairs_dl = (int64_t)hfs.method_count[M_DL];
+            s->pairs_h2l = (int64_t)hfs.method_count[M_H2L];
+            s->pairs_base = (int64_t)hfs.method_count[M_BASE];
+            s->pairs_split = (int64_t)hfs.method_count[M_SPLIT];
+            s->point_pairs_base = (int64_t)hev;
+            s->levels = (qt.depth > rt.depth ? qt.depth : rt.depth) + 1;
+            s->retries = 0;
+            s->fp32_rel_bound = hfs.rho;
+            s->eps_traversal = hfs.eps_t;
         }
         if (!rc && trace && trace->len) *trace->len = hfs.trace_count;
-        if (rc || !hfs.overflow || attempt >= 3) break;
-        // capacity overflow: grow and re-run the traversal on the same trees
-        cudaFreeAsync(Gq, st);
-        Gq = nullptr;
-        if (B) cudaFreeAsync(B, st);
-        if (pL) cudaFreeAsync(pL, st);
-        B = nullptr;
-        pL = nullptr;
-        free_bufs(fb, st);
-        mult *= 4;
-        cx.phase(GS_PH_OTHER);
     }
     if (Gq) cudaFreeAsync(Gq, st);
     if (B) cudaFreeAsync(B, st);
@@ -253,10 +251,6 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
     free_tree(rt, st);
     if (!mono) free_tree(qt, st);
     if (rc) return rc;
-    if (hfs.overflow) {
-        set_error("a device work list exceeded its capacity after %d retries", attempt);
-        return GS_ERR_CAPACITY;
-    }
     *status_out = hing.status;
     return GS_OK;
 }

@@ -74,7 +74,9 @@ struct FrontierParams {
     const double *rlo, *rhi, *rrad, *rW;
     const double *inv_2h2, *inv_4h2, *inv_h;
     double *fin, *tok, *est;
+    double *geo;          // per pair cache: K(delta_max), K(delta_min), delta_min^2
     double F[17], BT[17], Dpow[34];
+    double cw[4];         // cost weights of c_DH, c_DL, c_H2L, c_Direct
 };
 
 __device__ __forceinline__ double node_count(int64_t n, int depth, int64_t node) {
@@ -118,12 +120,17 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const int64_t q = G.q;
         const int j = G.j;
         const double inv2 = fp.inv_2h2[j], inv4 = fp.inv_4h2[j], invh = fp.inv_h[j];
-        // pass 1: lower bound over the group's pairs
+        // pass 1: bounding-box distances, kernel bounds, lower bound over the group
         double s_dl = 0.0, s_W = 0.0;
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
             const PairGeom pg = pair_geom(fp, q, r);
             const double kmax = exp_neg(-(pg.dmax2 * inv2));
+            const double kmin = exp_neg(-(pg.dmin2 * inv2));
+            double *gc = fp.geo + 3 * (G.off + k);
+            gc[0] = kmax;
+            gc[1] = kmin;
+            gc[2] = pg.dmin2;
             const double WR = fp.rW[r];
             s_dl = s_dl + WR * kmax;
             s_W = s_W + WR;
@@ -138,13 +145,11 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const double rQ = fp.qrad[q] * invh;
         // pass 2: decisions
         double s_left = 0.0, s_fin = 0.0, s_est = 0.0;
-        int n_split = 0, n_base = 0, n_ser = 0;
         int n_m[6] = {0, 0, 0, 0, 0, 0};
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
-            const PairGeom pg = pair_geom(fp, q, r);
-            const double kmax = exp_neg(-(pg.dmax2 * inv2));
-            const double kmin = exp_neg(-(pg.dmin2 * inv2));
+            const double *gc = fp.geo + 3 * (G.off + k);
+            const double kmax = gc[0], kmin = gc[1], dmin2 = gc[2];
             const double WR = fp.rW[r];
             const double dl = WR * kmax;
             const double allot = fp.tokens ? (tok0 * WR) / Wg : 0.0;
@@ -163,18 +168,32 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                 }
             }
             if (!decided && (fp.selector == GS_SEL_RULE || fp.selector == GS_SEL_MLP) && fp.P >= 1) {
-                const double e4 = exp_neg(-(pg.dmin2 * inv4));
-                const double base = WR * e4;
+                // bestMethod (Fig. 6).  Costs grow with p, so a method whose
+                // cost already reaches the best so far (or exceeds c_Direct)
+                // cannot be chosen and its remaining bounds are skipped; the
+                // choice is the same as evaluating every bound.
+                const double cr = node_count(fp.rn, fp.r_depth, r);
+                const double c_ex = (((double)fp.D * cq) * cr) * fp.cw[3];
+                double best_c = INFINITY, best_need = 0.0;
+                int best_m = -1, best_p = 0;
+                double e4 = -1.0, base = 0.0;
                 const double rR = fp.rrad[r] * invh;
                 const double x2 = kSqrt2 * rQ;
                 const double sr = kSqrt2 * rR;
-                const double cr = node_count(fp.rn, fp.r_depth, r);
-                double best_c = INFINITY, best_need = 0.0;
-                int best_m = -1, best_p = 0;
                 for (int m = M_DH; m <= M_H2L; ++m) {
-                    int pm = 0;
-                    double needm = 0.0;
                     for (int p = 1; p <= fp.P; ++p) {
+                        double c;
+                        if (m == M_DH)
+                            c = (cq * fp.Dpow[p + 1]) * fp.cw[0];
+                        else if (m == M_DL)
+                            c = (cr * fp.Dpow[p + 1]) * fp.cw[1];
+                        else
+                            c = fp.Dpow[2 * p + 1] * fp.cw[2];
+                        if (c >= best_c || c > c_ex) break;
+                        if (e4 < 0.0) {
+                            e4 = exp_neg(-(dmin2 * inv4));
+                            base = WR * e4;
+                        }
                         double Ep;
                         if (m == M_DH) {
                             Ep = (base * fp.F[p]) * rpow(rR, p);
@@ -186,28 +205,15 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                         }
                         const double np_ = (Wtot * Ep) / (eps_t * Gb) - WR;
                         if (np_ <= allot) {
-                            pm = p;
-                            needm = np_;
+                            best_c = c;
+                            best_m = m;
+                            best_p = p;
+                            best_need = np_;
                             break;
                         }
                     }
-                    if (pm == 0) continue;
-                    double c;
-                    if (m == M_DH)
-                        c = cq * fp.Dpow[pm + 1];
-                    else if (m == M_DL)
-                        c = cr * fp.Dpow[pm + 1];
-                    else
-                        c = fp.Dpow[2 * pm + 1];
-                    if (c < best_c) {
-                        best_c = c;
-                        best_m = m;
-                        best_p = pm;
-                        best_need = needm;
-                    }
                 }
-                const double c_ex = ((double)fp.D * cq) * cr;
-                if (best_m >= 0 && best_c <= c_ex) {
+                if (best_m >= 0) {
                     method = best_m;
                     pord = best_p;
                     leftover = allot - best_need;
@@ -220,9 +226,6 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             if (!fp.tokens) leftover = 0.0;
             s_left = s_left + leftover;
             if (method != M_SPLIT) s_fin = s_fin + dl;
-            n_split += method == M_SPLIT;
-            n_base += method == M_BASE;
-            n_ser += (method >= M_DH && method <= M_H2L);
             n_m[method]++;
             dec[G.off + k] = (uint8_t)(method | (pord << 3));
             if (trace) {
@@ -232,9 +235,6 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             }
         }
         const double tok_new = warp_sum(s_left), fin_add = warp_sum(s_fin), est_add = warp_sum(s_est);
-        n_split = __reduce_add_sync(0xffffffffu, n_split);
-        n_base = __reduce_add_sync(0xffffffffu, n_base);
-        n_ser = __reduce_add_sync(0xffffffffu, n_ser);
 #pragma unroll
         for (int m = 0; m < 6; ++m) n_m[m] = __reduce_add_sync(0xffffffffu, n_m[m]);
         if (lane == 0) {
@@ -248,6 +248,7 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     fp.tok[(2 * q + c) * fp.nh + j] = tok_new;
                 }
             }
+            const int n_split = n_m[M_SPLIT];
             int child_pairs, child_groups;
             if (fp.q_leaf) {
                 child_pairs = 2 * n_split;
@@ -260,11 +261,13 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                 child_groups = n_split > 0 ? 2 : 0;
             }
             int32_t *c = cnt + g * kCols;
-            c[0] = child_pairs;
-            c[1] = child_groups;
-            c[2] = n_base;
-            c[3] = n_ser;
-            c[4] = n_base > 0;
+            c[C_PAIRS] = child_pairs;
+            c[C_GROUPS] = child_groups;
+            c[C_BASE] = n_m[M_BASE];
+            c[C_DH] = n_m[M_DH];
+            c[C_DL] = n_m[M_DL];
+            c[C_H2L] = n_m[M_H2L];
+            c[C_BGROUPS] = n_m[M_BASE] > 0;
             for (int m = 0; m < 6; ++m)
                 if (n_m[m]) atomicAdd(&fs->method_count[m], (unsigned long long)n_m[m]);
         }
@@ -352,62 +355,64 @@ k_cols_offsets(const FrontierState *fs, int t, const int32_t *__restrict__ cnt, 
 // ---------------------------------------------------------------------------
 // K2: write the child frontier, base pairs and series actions
 // ---------------------------------------------------------------------------
-struct Caps {
-    int64_t pairs, groups, base, base_groups, series;
+struct EmitOut {
+    Group *groups_next;
+    int32_t *pr_next;
+    Group *base_groups;
+    int32_t *base_r;
+    SeriesEntry *series[3];
 };
 
 __global__ void __launch_bounds__(256)
-k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, Caps caps, const Group *__restrict__ groups,
+k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, const Group *__restrict__ groups,
              const int32_t *__restrict__ pr, const uint8_t *__restrict__ dec, const int32_t *__restrict__ cnt,
-             const long long *__restrict__ off, Group *__restrict__ groups_next, int32_t *__restrict__ pr_next,
-             Group *__restrict__ base_groups, int32_t *__restrict__ base_r, SeriesEntry *__restrict__ series) {
+             const long long *__restrict__ off, EmitOut eo) {
     const int lane = threadIdx.x & 31;
     const int64_t ng = fs->ngroups[t];
-    const int64_t base0 = fs->base_count, bg0 = fs->base_groups, ser0 = fs->series_count;
-    if (fs->totals[0] > caps.pairs || fs->totals[1] > caps.groups || base0 + fs->totals[2] > caps.base ||
-        bg0 + fs->totals[4] > caps.base_groups || ser0 + fs->totals[3] > caps.series) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) fs->overflow = 1;
-        return;
-    }
+    const int64_t base0 = fs->base_count, bg0 = fs->base_groups;
+    const int64_t ser0[3] = {fs->series_count[0], fs->series_count[1], fs->series_count[2]};
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += warps) {
         const Group G = groups[g];
         const int32_t *c = cnt + g * kCols;
         const long long *o = off + g * kCols;
-        const int64_t o_pairs = o[0], o_groups = o[1], o_base = base0 + o[2], o_ser = ser0 + o[3];
-        const int64_t o_bg = bg0 + o[4];
-        const int n_split = q_leaf ? c[0] / 2 : (r_leaf ? c[0] / 2 : c[0] / 4);
+        const int64_t o_pairs = o[C_PAIRS], o_groups = o[C_GROUPS], o_base = base0 + o[C_BASE];
+        const int64_t o_bg = bg0 + o[C_BGROUPS];
+        int64_t o_ser[3];
+        for (int m = 0; m < 3; ++m) o_ser[m] = ser0[m] + o[C_DH + m];
+        const int n_split = q_leaf ? c[C_PAIRS] / 2 : (r_leaf ? c[C_PAIRS] / 2 : c[C_PAIRS] / 4);
         const int per_child = r_leaf ? n_split : 2 * n_split;
-        int run_s = 0, run_b = 0, run_x = 0;
+        int run_s = 0, run_b = 0, run_x[3] = {0, 0, 0};
         for (int k0 = 0; k0 < G.cnt; k0 += 32) {
             const int k = k0 + lane;
             const bool valid = k < G.cnt;
             const int d = valid ? dec[G.off + k] : 0xff;
             const int m = d & 7;
             const bool isS = valid && m == M_SPLIT, isB = valid && m == M_BASE;
-            const bool isX = valid && m >= M_DH && m <= M_H2L;
             const unsigned bS = __ballot_sync(0xffffffffu, isS), bB = __ballot_sync(0xffffffffu, isB);
-            const unsigned bX = __ballot_sync(0xffffffffu, isX);
+            unsigned bX[3];
+            for (int x = 0; x < 3; ++x) bX[x] = __ballot_sync(0xffffffffu, valid && m == M_DH + x);
             const int32_t r = valid ? pr[G.off + k] : 0;
             if (isS) {
                 const int rank = run_s + __popc(bS & lt_mask);
                 if (!q_leaf && !r_leaf) {
                     for (int cc = 0; cc < 2; ++cc) {
                         const int64_t p = o_pairs + (int64_t)cc * per_child + 2 * rank;
-                        pr_next[p] = 2 * r + 1;
-                        pr_next[p + 1] = 2 * r + 2;
+                        eo.pr_next[p] = 2 * r + 1;
+                        eo.pr_next[p + 1] = 2 * r + 2;
                     }
                 } else if (q_leaf) {
                     const int64_t p = o_pairs + 2 * rank;
-                    pr_next[p] = 2 * r + 1;
-                    pr_next[p + 1] = 2 * r + 2;
+                    eo.pr_next[p] = 2 * r + 1;
+                    eo.pr_next[p + 1] = 2 * r + 2;
                 } else {
-                    for (int cc = 0; cc < 2; ++cc) pr_next[o_pairs + (int64_t)cc * per_child + rank] = r;
+                    for (int cc = 0; cc < 2; ++cc) eo.pr_next[o_pairs + (int64_t)cc * per_child + rank] = r;
                 }
             }
-            if (isB) base_r[o_base + run_b + __popc(bB & lt_mask)] = r;
-            if (isX) {
+            if (isB) eo.base_r[o_base + run_b + __popc(bB & lt_mask)] = r;
+            if (valid && m >= M_DH && m <= M_H2L) {
+                const int x = m - M_DH;
                 SeriesEntry e;
                 e.q = G.q;
                 e.r = r;
@@ -415,55 +420,49 @@ k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, Caps caps, const 
                 e.p = (int8_t)(d >> 3);
                 e.method = (int8_t)m;
                 e.pad = 0;
-                series[o_ser + run_x + __popc(bX & lt_mask)] = e;
+                eo.series[x][o_ser[x] + run_x[x] + __popc(bX[x] & lt_mask)] = e;
             }
             run_s += __popc(bS);
             run_b += __popc(bB);
-            run_x += __popc(bX);
+            for (int x = 0; x < 3; ++x) run_x[x] += __popc(bX[x]);
         }
         if (lane == 0) {
             if (n_split > 0) {
                 if (q_leaf) {
                     Group ng_;
                     ng_.q = G.q; ng_.j = G.j; ng_.off = o_pairs; ng_.cnt = 2 * n_split; ng_.pad = 0;
-                    groups_next[o_groups] = ng_;
+                    eo.groups_next[o_groups] = ng_;
                 } else {
                     for (int cc = 0; cc < 2; ++cc) {
                         Group ng_;
                         ng_.q = 2 * G.q + 1 + cc; ng_.j = G.j; ng_.off = o_pairs + (int64_t)cc * per_child;
                         ng_.cnt = per_child; ng_.pad = 0;
-                        groups_next[o_groups + cc] = ng_;
+                        eo.groups_next[o_groups + cc] = ng_;
                     }
                 }
             }
-            if (c[2] > 0) {
+            if (c[C_BASE] > 0) {
                 Group bg;
-                bg.q = G.q; bg.j = G.j; bg.off = o_base; bg.cnt = c[2]; bg.pad = 0;
-                base_groups[o_bg] = bg;
+                bg.q = G.q; bg.j = G.j; bg.off = o_base; bg.cnt = c[C_BASE]; bg.pad = 0;
+                eo.base_groups[o_bg] = bg;
             }
         }
     }
 }
 
 __global__ void k_front_advance(FrontierState *fs, int t) {
-    const int64_t npairs = fs->npairs[t];
-    fs->trace_count += npairs;
-    if (fs->overflow) {
-        fs->ngroups[t + 1] = 0;
-        fs->npairs[t + 1] = 0;
-        return;
-    }
-    fs->ngroups[t + 1] = fs->totals[1];
-    fs->npairs[t + 1] = fs->totals[0];
-    fs->base_count += fs->totals[2];
-    fs->series_count += fs->totals[3];
-    fs->base_groups += fs->totals[4];
+    fs->trace_count += fs->npairs[t];
+    fs->ngroups[t + 1] = fs->totals[C_GROUPS];
+    fs->npairs[t + 1] = fs->totals[C_PAIRS];
+    fs->base_count += fs->totals[C_BASE];
+    for (int m = 0; m < 3; ++m) fs->series_count[m] += fs->totals[C_DH + m];
+    fs->base_groups += fs->totals[C_BGROUPS];
 }
 
 // initial frontier: one group (root, j) with the single pair (root, root) per
 // bandwidth; eps for the traversal after the FP32 base-case charge.
 __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int nh, const double *rW,
-                             const Ingest *ing, int64_t N, int D, int floor_log2, double eps) {
+                             Ingest *ing, int64_t N, int D, int floor_log2, double eps) {
     const int j = threadIdx.x;
     if (j < nh) {
         Group g;
@@ -485,7 +484,7 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
         fs->floorW = W * ldexp(1.0, floor_log2);
         fs->ngroups[0] = nh;
         fs->npairs[0] = nh;
-        if (!(fs->eps_t > 0.5 * eps)) atomicOr(&((Ingest *)ing)->status, ST_EPS);
+        if (!(fs->eps_t > 0.5 * eps)) atomicOr(&ing->status, ST_EPS);
     }
 }
 
@@ -521,6 +520,22 @@ static double factd(int m) {
     return f;
 }
 
+// Grow a device array to hold at least `need` elements, keeping the first
+// `keep` elements.
+template <typename E>
+static int grow(E **ptr, int64_t *cap, int64_t need, int64_t keep, cudaStream_t st) {
+    if (need <= *cap) return GS_OK;
+    int64_t nc = *cap * 2;
+    if (nc < need + need / 2) nc = need + need / 2;
+    E *np = nullptr;
+    GS_CUDA_TRY(cudaMallocAsync((void **)&np, (size_t)nc * sizeof(E), st));
+    if (keep > 0 && *ptr) GS_CUDA_TRY(cudaMemcpyAsync(np, *ptr, (size_t)keep * sizeof(E), cudaMemcpyDeviceToDevice, st));
+    if (*ptr) cudaFreeAsync(*ptr, st);
+    *ptr = np;
+    *cap = nc;
+    return GS_OK;
+}
+
 int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     cudaStream_t st = cx.st;
     int rc = cx.check("before frontier");
@@ -542,6 +557,7 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.rlo = in.rt->lo; fp.rhi = in.rt->hi; fp.rrad = in.rt->rad; fp.rW = in.rt->W;
     fp.inv_2h2 = fb.inv_2h2; fp.inv_4h2 = fb.inv_4h2; fp.inv_h = fb.inv_h;
     fp.fin = fb.fin; fp.tok = fb.tok; fp.est = fb.est;
+    for (int k = 0; k < 4; ++k) fp.cw[k] = in.cost_w[k];
     const int D = in.D;
     // Lemma 4-6 factor C(D+p-1, D-1) / sqrt((floor(p/D)!)^(D-p') (ceil(p/D)!)^p'),
     // C(D+p-1, D), and D^k, all from exact integers
@@ -556,43 +572,69 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.Dpow[0] = 1.0;
     for (int k = 1; k < 34; ++k) fp.Dpow[k] = fp.Dpow[k - 1] * (double)D;
 
-    k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, in.ing, in.rt->n, in.D,
-                                   in.floor_log2, in.eps);
+    k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, (Ingest *)in.ing, in.rt->n,
+                                   in.D, in.floor_log2, in.eps);
     cx.launches += 1;
     if ((rc = cx.check("k_front_init"))) return rc;
     const int T = in.qt->depth > in.rt->depth ? in.qt->depth : in.rt->depth;
-    Caps caps;
-    caps.pairs = fb.cap_pairs;
-    caps.groups = fb.cap_groups;
-    caps.base = fb.cap_base;
-    caps.base_groups = fb.cap_base_groups;
-    caps.series = fb.cap_series;
     int cur = 0;
-    const int grid = fb.grid_warps / 8;
-    for (int t = 0; t <= T; ++t) {
+    int64_t ng = in.nh, npairs = in.nh;
+    int64_t base_count = 0, bgroups = 0, ser_count[3] = {0, 0, 0};
+    const int max_grid = fb.grid_warps / 8;
+    for (int t = 0; t <= T && ng > 0; ++t) {
         fp.t = t;
         fp.q_depth = t < in.qt->depth ? t : in.qt->depth;
         fp.r_depth = t < in.rt->depth ? t : in.rt->depth;
         fp.q_leaf = t >= in.qt->depth;
         fp.r_leaf = t >= in.rt->depth;
+        // this iteration's per-pair arrays
+        if ((rc = grow(&fb.dec, &fb.cap_pairs, npairs, 0, st))) return rc;
+        if ((rc = grow(&fb.geo, &fb.cap_geo, 3 * npairs, 0, st))) return rc;
+        fp.geo = fb.geo;
+        const int grid = (int)((ng + 7) / 8 < max_grid ? (ng + 7) / 8 : max_grid);
         k_front_decide<<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
                                              fb.trace_cap);
         if ((rc = cx.check("k_front_decide"))) return rc;
         k_cols_partial<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial);
-        if ((rc = cx.check("k_cols_partial"))) return rc;
         k_cols_scan_partials<<<1, kColTB, 0, st>>>(fb.fs, fb.partial);
-        if ((rc = cx.check("k_cols_scan_partials"))) return rc;
         k_cols_offsets<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial, fb.off);
-        if ((rc = cx.check("k_cols_offsets"))) return rc;
-        k_front_emit<<<grid, 256, 0, st>>>(fb.fs, t, fp.q_leaf, fp.r_leaf, caps, fb.groups[cur], fb.pr[cur], fb.dec,
-                                           fb.cnt, fb.off, fb.groups[cur ^ 1], fb.pr[cur ^ 1], fb.base_groups,
-                                           fb.base_r, fb.series);
-        if ((rc = cx.check("k_front_emit"))) return rc;
+        cx.launches += 4;
+        if ((rc = cx.check("k_cols_*"))) return rc;
+        // read this iteration's totals and make room for what it will write
+        GS_CUDA_TRY(cudaMemcpyAsync(fb.host_totals, &fb.fs->totals[0], kCols * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st));
+        GS_CUDA_TRY(cudaStreamSynchronize(st));
+        int64_t tot[kCols];
+        for (int c = 0; c < kCols; ++c) tot[c] = fb.host_totals[c];
+        if (tot[C_GROUPS] > fb.cap_groups || bgroups + tot[C_BGROUPS] > fb.cap_base_groups) {
+            set_error("internal: group count above its bound");
+            return GS_ERR_CUDA;
+        }
+        if ((rc = grow(&fb.pr[cur ^ 1], &fb.cap_pr[cur ^ 1], tot[C_PAIRS], 0, st))) return rc;
+        if ((rc = grow(&fb.base_r, &fb.cap_base, base_count + tot[C_BASE], base_count, st))) return rc;
+        for (int m = 0; m < 3; ++m)
+            if ((rc = grow(&fb.series[m], &fb.cap_series[m], ser_count[m] + tot[C_DH + m], ser_count[m], st)))
+                return rc;
+        EmitOut eo;
+        eo.groups_next = fb.groups[cur ^ 1];
+        eo.pr_next = fb.pr[cur ^ 1];
+        eo.base_groups = fb.base_groups;
+        eo.base_r = fb.base_r;
+        for (int m = 0; m < 3; ++m) eo.series[m] = fb.series[m];
+        k_front_emit<<<grid, 256, 0, st>>>(fb.fs, t, fp.q_leaf, fp.r_leaf, fb.groups[cur], fb.pr[cur], fb.dec,
+                                           fb.cnt, fb.off, eo);
         k_front_advance<<<1, 1, 0, st>>>(fb.fs, t);
-        if ((rc = cx.check("k_front_advance"))) return rc;
-        cx.launches += 6;
+        cx.launches += 3;
+        if ((rc = cx.check("k_front_emit"))) return rc;
+        ng = tot[C_GROUPS];
+        npairs = tot[C_PAIRS];
+        base_count += tot[C_BASE];
+        bgroups += tot[C_BGROUPS];
+        for (int m = 0; m < 3; ++m) ser_count[m] += tot[C_DH + m];
         cur ^= 1;
     }
+    for (int m = 0; m < 3; ++m) fb.n_series[m] = ser_count[m];
+    fb.n_base_groups = bgroups;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "frontier launch");
     return GS_OK;

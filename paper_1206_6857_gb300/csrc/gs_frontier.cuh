@@ -25,13 +25,16 @@ struct SeriesEntry {
     int32_t pad;
 };
 
-constexpr int kCols = 5;   // per-group counts: child pairs, child groups, base pairs, series, base groups
+// per-group counts: child pairs, child groups, base pairs, DH, DL, H2L actions, base groups
+constexpr int kCols = 7;
+enum : int { C_PAIRS = 0, C_GROUPS = 1, C_BASE = 2, C_DH = 3, C_DL = 4, C_H2L = 5, C_BGROUPS = 6 };
 
 // Device-resident traversal bookkeeping (one instance per call).
 struct FrontierState {
     int64_t ngroups[72];        // groups in iteration t
     int64_t npairs[72];         // pairs in iteration t
-    int64_t base_count, base_groups, series_count, trace_count;
+    int64_t base_count, base_groups, trace_count;
+    int64_t series_count[3];    // DH, DL, H2L actions so far
     int64_t totals[kCols];      // column totals of the last scan
     unsigned long long method_count[6];
     double eps_t, rho, Wtot, floorW;

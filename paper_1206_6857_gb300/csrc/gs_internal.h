@@ -108,6 +108,7 @@ struct TraversalIn {
     const double *h = nullptr;   // host
     int D = 0, nh = 0, P = 0, selector = 0, tokens = 1, mono = 0, floor_log2 = -40;
     double eps = 0.0;
+    double cost_w[4] = {GS_COST_DH, GS_COST_DL, GS_COST_H2L, GS_COST_DIRECT};
 };
 
 struct FrontierBufs {
@@ -119,14 +120,20 @@ struct FrontierBufs {
     long long *off = nullptr, *partial = nullptr;
     Group *base_groups = nullptr;
     int32_t *base_r = nullptr;
-    SeriesEntry *series = nullptr;
+    SeriesEntry *series[3] = {nullptr, nullptr, nullptr};   // DH, DL, H2L action lists
+    double *geo = nullptr;          // per pair: K(delta_max), K(delta_min), delta_min^2
     double *fin = nullptr, *tok = nullptr, *est = nullptr;
     double *inv_2h2 = nullptr, *inv_4h2 = nullptr, *inv_h = nullptr, *inv_s = nullptr;
     unsigned long long *evals = nullptr;
     int4 *trace = nullptr;
     int64_t trace_cap = 0;
-    int64_t cap_pairs = 0, cap_groups = 0, cap_base = 0, cap_base_groups = 0, cap_series = 0;
+    int64_t cap_pairs = 0, cap_groups = 0, cap_base = 0, cap_base_groups = 0, cap_series[3] = {0, 0, 0};
+    int64_t cap_pr[2] = {0, 0};     // capacity of each pair buffer
+    int64_t cap_geo = 0;
+    int64_t n_series[3] = {0, 0, 0};// actions per list after the traversal (host copy)
+    int64_t n_base_groups = 0;
     int grid_warps = 0;
+    int64_t *host_totals = nullptr; // pinned host scratch (kCols + 8 int64)
 };
 
 int build_tree(const void *x, const float *w, int64_t n, int D, int dtype, int L, const Ingest *ing, int DP,

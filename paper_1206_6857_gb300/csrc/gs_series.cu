@@ -56,169 +56,147 @@ __device__ __forceinline__ void hermite_polys(double t, int n, double *h) {
     for (int k = 1; k + 1 < n; ++k) h[k + 1] = 2.0 * t * h[k] - 2.0 * k * h[k - 1];
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    __syncthreads();
-    return s;
+    return v;
 }
 
 // ---------------------------------------------------------------------------
-// DH: block per entry; warps over the queries of Q, lanes over multi-indices
+// DH: one warp per action, lanes over the queries of Q
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSerTB)
+__global__ void __launch_bounds__(256)
 k_series_dh(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
-    __shared__ double A[kMaxT];
-    __shared__ double Hs[kSerTB / 32][kMaxDP];
-    const int64_t ne = fs->series_count;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    const int64_t ne = fs->series_count[0];
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int D = sp.D;
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < ne; e += warps) {
         const SeriesEntry E = ent[e];
-        if (E.method != M_DH) continue;
-        const int p = E.p, D = sp.D, Tp = sp.tb.Tp[p];
+        const int p = E.p, Tp = sp.tb.Tp[p];
         const double is = sp.inv_s[E.j];
-        __syncthreads();
-        for (int a = threadIdx.x; a < Tp; a += blockDim.x) {
-            double v = sp.rmom[(int64_t)E.r * sp.T + a];
-            for (int k = 0; k < sp.tb.deg[a]; ++k) v *= is;
-            A[a] = v;
-        }
-        __syncthreads();
+        double ispow[16];
+        ispow[0] = 1.0;
+        for (int k = 1; k < p; ++k) ispow[k] = ispow[k - 1] * is;
+        const double *mom = sp.rmom + (int64_t)E.r * sp.T;
+        const double *cR = sp.rcenter + (int64_t)E.r * D;
         const int qd = node_depth(E.q);
         const int64_t qi = E.q - ((1ll << qd) - 1);
         const int64_t b = level_begin(sp.qn, qd, qi), en = level_begin(sp.qn, qd, qi + 1);
-        for (int64_t pos = b + w; pos < en; pos += blockDim.x >> 5) {
+        for (int64_t pos = b + lane; pos < en; pos += 32) {
+            double H[kMaxDP];
             double t2 = 0.0;
-            for (int d = lane; d < D; d += 32) {
-                const double t = (coord(sp.qxs, sp.dtype, pos, D, d) - sp.rcenter[(int64_t)E.r * D + d]) * is;
-                hermite_polys(t, p, &Hs[w][d * p]);
+            for (int d = 0; d < D; ++d) {
+                const double t = (coord(sp.qxs, sp.dtype, pos, D, d) - cR[d]) * is;
+                hermite_polys(t, p, &H[d * p]);
                 t2 += t * t;
             }
-            for (int o = 16; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-            __syncwarp();
             double s = 0.0;
-            for (int a = lane; a < Tp; a += 32) {
+            for (int a = 0; a < Tp; ++a) {
                 const uint8_t *al = sp.tb.alpha + a * D;
-                double pr = A[a];
-                for (int d = 0; d < D; ++d) pr *= Hs[w][d * p + al[d]];
+                double pr = mom[a] * ispow[sp.tb.deg[a]];
+                for (int d = 0; d < D; ++d) pr *= H[d * p + al[d]];
                 s += pr;
             }
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) atomicAdd(&sp.Gq[pos * sp.nh + E.j], s * exp(-t2));
-            __syncwarp();
+            atomicAdd(&sp.Gq[pos * sp.nh + E.j], s * exp(-t2));
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// DL: block per entry; references of R in chunks of 32, threads over b
+// DL: one warp per action, lanes over the references of R; each coefficient
+// is reduced across the warp and banked by lane (b mod 32)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSerTB)
+__global__ void __launch_bounds__(256)
 k_series_dl(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
-    __shared__ double Hr[32][kMaxDP];
-    __shared__ double we[32];
-    const int64_t ne = fs->series_count;
-    for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    const int64_t ne = fs->series_count[1];
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int D = sp.D;
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < ne; e += warps) {
         const SeriesEntry E = ent[e];
-        if (E.method != M_DL) continue;
-        const int p = E.p, D = sp.D, Tp = sp.tb.Tp[p];
+        const int p = E.p, Tp = sp.tb.Tp[p];
         const double is = sp.inv_s[E.j];
+        const double *cQ = sp.qcenter + (int64_t)E.q * D;
         const int rd = node_depth(E.r);
         const int64_t ri = E.r - ((1ll << rd) - 1);
         const int64_t rb = level_begin(sp.rn, rd, ri), re = level_begin(sp.rn, rd, ri + 1);
-        double acc[kMaxT / kSerTB];
-#pragma unroll
-        for (int i = 0; i < kMaxT / kSerTB; ++i) acc[i] = 0.0;
+        double acc[kMaxT / 32];
+        for (int i = 0; i < (Tp + 31) / 32; ++i) acc[i] = 0.0;
         for (int64_t c0 = rb; c0 < re; c0 += 32) {
-            const int nc = (int)min((int64_t)32, re - c0);
-            __syncthreads();
-            if (threadIdx.x < nc) {
-                const int64_t pos = c0 + threadIdx.x;
+            const int64_t pos = c0 + lane;
+            const bool valid = pos < re;
+            double H[kMaxDP];
+            double we = 0.0;
+            if (valid) {
                 double v2 = 0.0;
                 for (int d = 0; d < D; ++d) {
-                    const double v = (coord(sp.rxs, sp.dtype, pos, D, d) - sp.qcenter[(int64_t)E.q * D + d]) * is;
-                    hermite_polys(v, p, &Hr[threadIdx.x][d * p]);
+                    const double v = (coord(sp.rxs, sp.dtype, pos, D, d) - cQ[d]) * is;
+                    hermite_polys(v, p, &H[d * p]);
                     v2 += v * v;
                 }
-                we[threadIdx.x] = (double)sp.w[sp.rperm[pos]] * exp(-v2);
+                we = (double)sp.w[sp.rperm[pos]] * exp(-v2);
+            } else {
+                for (int i = 0; i < D * p; ++i) H[i] = 0.0;
             }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < kMaxT / kSerTB; ++i) {
-                const int bt = threadIdx.x + i * kSerTB;
-                if (bt >= Tp) break;
-                const uint8_t *be = sp.tb.alpha + bt * D;
-                double s = 0.0;
-                for (int r = 0; r < nc; ++r) {
-                    double pr = we[r];
-                    for (int d = 0; d < D; ++d) pr *= Hr[r][d * p + be[d]];
-                    s += pr;
-                }
-                acc[i] += s;
+            for (int a = 0; a < Tp; ++a) {
+                const uint8_t *be = sp.tb.alpha + a * D;
+                double pr = we;
+                for (int d = 0; d < D; ++d) pr *= H[d * p + be[d]];
+                pr = warp_sum_d(pr);
+                if ((a & 31) == lane) acc[a >> 5] += pr;
             }
         }
         double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * sp.T;
-#pragma unroll
-        for (int i = 0; i < kMaxT / kSerTB; ++i) {
-            const int bt = threadIdx.x + i * kSerTB;
-            if (bt >= Tp) break;
-            atomicAdd(&Bq[bt], acc[i] * sp.tb.inv_fact[bt]);
-        }
-        if (threadIdx.x == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
+        for (int a = lane; a < Tp; a += 32) atomicAdd(&Bq[a], acc[a >> 5] * sp.tb.inv_fact[a]);
+        if (lane == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
     }
 }
 
 // ---------------------------------------------------------------------------
-// H2L: block per entry; threads over b, loop over a
+// H2L: one warp per action, lanes over b, loop over a; the 1-D Hermite
+// polynomials of tau = (x_Q - x_R)/s up to order 2p-2 sit in shared memory
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSerTB)
+__global__ void __launch_bounds__(256)
 k_series_h2l(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
-    __shared__ double A[kMaxT];
-    __shared__ double Hs[2 * kMaxDP];
-    __shared__ double red[kSerTB / 32];
-    const int64_t ne = fs->series_count;
-    for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    __shared__ double Hs[8][2 * kMaxDP];
+    const int64_t ne = fs->series_count[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int D = sp.D;
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; e < ne; e += warps) {
         const SeriesEntry E = ent[e];
-        if (E.method != M_H2L) continue;
-        const int p = E.p, D = sp.D, Tp = sp.tb.Tp[p];
+        const int p = E.p, Tp = sp.tb.Tp[p];
         const int nH = 2 * p - 1;   // orders 0 .. 2p-2
         const double is = sp.inv_s[E.j];
-        __syncthreads();
-        for (int a = threadIdx.x; a < Tp; a += blockDim.x) {
-            double v = sp.rmom[(int64_t)E.r * sp.T + a];
-            for (int k = 0; k < sp.tb.deg[a]; ++k) v *= is;
-            A[a] = v;
-        }
+        double ispow[16];
+        ispow[0] = 1.0;
+        for (int k = 1; k < p; ++k) ispow[k] = ispow[k - 1] * is;
+        const double *mom = sp.rmom + (int64_t)E.r * sp.T;
+        __syncwarp();
         double t2 = 0.0;
-        if (threadIdx.x < D) {
-            const int d = threadIdx.x;
-            const double tau = (sp.qcenter[(int64_t)E.q * D + d] - sp.rcenter[(int64_t)E.r * D + d]) * is;
-            hermite_polys(tau, nH, &Hs[d * nH]);
+        if (lane < D) {
+            const double tau = (sp.qcenter[(int64_t)E.q * D + lane] - sp.rcenter[(int64_t)E.r * D + lane]) * is;
+            hermite_polys(tau, nH, &Hs[w][lane * nH]);
             t2 = tau * tau;
         }
-        t2 = block_sum(t2, red);
-        __shared__ double et;
-        if (threadIdx.x == 0) et = exp(-t2);
-        __syncthreads();
+        t2 = warp_sum_d(t2);
+        __syncwarp();
+        const double et = exp(-t2);
         double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * sp.T;
-        for (int bt = threadIdx.x; bt < Tp; bt += blockDim.x) {
+        for (int bt = lane; bt < Tp; bt += 32) {
             const uint8_t *be = sp.tb.alpha + bt * D;
             double s = 0.0;
             for (int a = 0; a < Tp; ++a) {
                 const uint8_t *al = sp.tb.alpha + a * D;
-                double pr = A[a];
-                for (int d = 0; d < D; ++d) pr *= Hs[d * nH + al[d] + be[d]];
+                double pr = mom[a] * ispow[sp.tb.deg[a]];
+                for (int d = 0; d < D; ++d) pr *= Hs[w][d * nH + al[d] + be[d]];
                 s += pr;
             }
             const double sign = (sp.tb.deg[bt] & 1) ? -1.0 : 1.0;
             atomicAdd(&Bq[bt], sign * sp.tb.inv_fact[bt] * et * s);
         }
-        if (threadIdx.x == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
+        if (lane == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
     }
 }
 
@@ -354,13 +332,26 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         }
         cx.phase(GS_PH_SERIES);
         int rc;
-        k_series_dh<<<fb.grid_warps / 4, kSerTB, 0, st>>>(sp, fb.fs, fb.series);
-        if ((rc = cx.check("k_series_dh"))) return rc;
-        k_series_dl<<<fb.grid_warps / 4, kSerTB, 0, st>>>(sp, fb.fs, fb.series);
-        if ((rc = cx.check("k_series_dl"))) return rc;
-        k_series_h2l<<<fb.grid_warps / 4, kSerTB, 0, st>>>(sp, fb.fs, fb.series);
-        if ((rc = cx.check("k_series_h2l"))) return rc;
-        cx.launches += 3;
+        auto grid_for = [&](int64_t n) {
+            int64_t g = (n + 7) / 8;
+            const int64_t mx = fb.grid_warps / 8;
+            return (unsigned)(g < 1 ? 1 : (g > mx ? mx : g));
+        };
+        if (fb.n_series[0] > 0) {
+            k_series_dh<<<grid_for(fb.n_series[0]), 256, 0, st>>>(sp, fb.fs, fb.series[0]);
+            cx.launches += 1;
+            if ((rc = cx.check("k_series_dh"))) return rc;
+        }
+        if (fb.n_series[1] > 0) {
+            k_series_dl<<<grid_for(fb.n_series[1]), 256, 0, st>>>(sp, fb.fs, fb.series[1]);
+            cx.launches += 1;
+            if ((rc = cx.check("k_series_dl"))) return rc;
+        }
+        if (fb.n_series[2] > 0) {
+            k_series_h2l<<<grid_for(fb.n_series[2]), 256, 0, st>>>(sp, fb.fs, fb.series[2]);
+            cx.launches += 1;
+            if ((rc = cx.check("k_series_h2l"))) return rc;
+        }
         cx.phase(GS_PH_DOWN);
         for (int k = 0; k < in.qt->depth; ++k) {
             const int64_t items = (1ll << k) * in.nh;

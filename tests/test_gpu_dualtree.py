@@ -33,20 +33,26 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _opts(gs, leaf=32, selector=0, tokens=True, plimit=0):
+PAPER = (1.0, 1.0, 1.0, 1.0)          # the paper's unit cost weights
+
+
+def _opts(gs, leaf=32, selector=0, tokens=True, plimit=0, cw=None):
     o = gs.gs_opts_default()
     o.leaf_size = leaf
     o.selector = selector
     o.no_tokens = 0 if tokens else 1
     o.plimit = plimit
+    if cw is not None:
+        for k in range(4):
+            o.cost_weight[k] = cw[k]
     return o
 
 
-def _cpu_trace(q, r, w, mono, h, eps, leaf, selector, tokens, plimit):
+def _cpu_trace(q, r, w, mono, h, eps, leaf, selector, tokens, plimit, cw):
     rt = T.build_tree(r, w, leaf)
     qt = rt if mono else T.build_tree(q, np.ones(q.shape[0], np.float32), leaf)
     trav = T.traverse(qt, rt, mono, h, eps, plimit=plimit or None, selector=selector, tokens=tokens,
-                      w_max=float(w.max()))
+                      w_max=float(w.max()), cost_weight=cw)
     rec = []
     for t, it in enumerate(trav.iters):
         code = it["method"] | (it["p"] << 8) | (t << 16)
@@ -54,30 +60,33 @@ def _cpu_trace(q, r, w, mono, h, eps, leaf, selector, tokens, plimit):
     return qt, rt, np.concatenate(rec).astype(np.int64), trav
 
 
+DEF = T.COST_WEIGHTS
 CASES = [
-    # seed, n, D, m (None: monochromatic), eps, leaf, selector, tokens, plimit, h
-    (1, 3000, 2, None, 1e-2, 32, 0, True, 0, [0.003, 0.03, 0.3]),
-    (2, 2500, 3, None, 1e-3, 16, 0, True, 0, [0.01, 0.05, 0.2, 0.8]),
-    (3, 2000, 3, 1500, 1e-2, 32, 0, True, 0, [0.02, 0.2]),
-    (4, 1800, 5, None, 1e-2, 16, 0, True, 0, [0.05, 0.3, 1.0]),
-    (5, 2200, 2, None, 1e-2, 8, 2, True, 0, [0.01, 0.1]),
-    (6, 2200, 2, None, 1e-2, 32, 0, False, 0, [0.01, 0.1]),
-    (7, 1500, 4, None, 1e-2, 32, 3, True, 0, [0.1]),
-    (8, 1200, 7, 900, 1e-2, 16, 0, True, 0, [0.1, 0.5]),
-    (9, 2000, 2, None, 1e-3, 32, 0, True, 3, [0.05, 0.2]),
+    # seed, n, D, m (None: monochromatic), eps, leaf, selector, tokens, plimit, h, cost weights
+    (1, 3000, 2, None, 1e-2, 32, 0, True, 0, [0.003, 0.03, 0.3], PAPER),
+    (2, 2500, 3, None, 1e-3, 16, 0, True, 0, [0.01, 0.05, 0.2, 0.8], PAPER),
+    (3, 2000, 3, 1500, 1e-2, 32, 0, True, 0, [0.02, 0.2], DEF),
+    (4, 1800, 5, None, 1e-2, 16, 0, True, 0, [0.05, 0.3, 1.0], PAPER),
+    (5, 2200, 2, None, 1e-2, 8, 2, True, 0, [0.01, 0.1], DEF),
+    (6, 2200, 2, None, 1e-2, 32, 0, False, 0, [0.01, 0.1], PAPER),
+    (7, 1500, 4, None, 1e-2, 32, 3, True, 0, [0.1], DEF),
+    (8, 1200, 7, 900, 1e-2, 16, 0, True, 0, [0.1, 0.5], DEF),
+    (9, 2000, 2, None, 1e-3, 32, 0, True, 3, [0.05, 0.2], PAPER),
+    (10, 6000, 2, None, 1e-2, 32, 0, True, 0, [0.02, 0.1, 0.4], DEF),
+    (11, 4000, 3, None, 1e-4, 32, 0, True, 0, [0.05, 0.3], DEF),
 ]
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_n%d_d%d" % (c[0], c[1], c[2]))
 def test_traversal_bit_exact_and_within_eps(gs, case):
-    seed, n, D, m, eps, leaf, sel, tok, plim, h = case
+    seed, n, D, m, eps, leaf, sel, tok, plim, h, cw = case
     q, r, w = synth.small_random(seed, n, D, m=m)
     mono = m is None
     h = np.asarray(h, np.float64)
     tq = _dev(q)
     tr = tq if mono else _dev(r)
-    out, trace, qperm, rperm = gs.gs_sum_trace(tq, tr, _dev(w), h, eps, opts=_opts(gs, leaf, sel, tok, plim))
-    qt, rt, want, trav = _cpu_trace(q, r, w, mono, h, eps, leaf, sel, tok, plim)
+    out, trace, qperm, rperm = gs.gs_sum_trace(tq, tr, _dev(w), h, eps, opts=_opts(gs, leaf, sel, tok, plim, cw))
+    qt, rt, want, trav = _cpu_trace(q, r, w, mono, h, eps, leaf, sel, tok, plim, cw)
     assert np.array_equal(rperm.cpu().numpy(), rt.perm)
     assert np.array_equal(qperm.cpu().numpy(), qt.perm)
     got = trace.cpu().numpy().astype(np.int64)
@@ -158,13 +167,25 @@ def test_leaf_sizes(gs, leaf):
     assert rel_err(out, exact).max() <= 1e-2
 
 
-def test_capacity_retry(gs):
+def test_small_initial_capacity_grows(gs):
+    """Work lists start tiny and must grow between iterations."""
     q, r, w = synth.small_random(78, 4000, 2)
-    h = np.array([0.05])
-    o = _opts(gs)
-    o.pair_capacity = 2000
-    st = gs.gs_stats()
-    out = gs.gs_sum(_dev(q), _dev(q), _dev(w), h, 1e-2, opts=o, stats=st).cpu().numpy()
-    assert st.retries >= 1
+    h = np.array([0.05, 0.5])
+    o = _opts(gs, cw=PAPER)
+    o.pair_capacity = 64
+    out = gs.gs_sum(_dev(q), _dev(q), _dev(w), h, 1e-3, opts=o).cpu().numpy()
     exact = oracle_ex.gauss_sum(q, r, w, h)
-    assert rel_err(out, exact).max() <= 1e-2
+    assert rel_err(out, exact).max() <= 1e-3
+
+
+@pytest.mark.parametrize("D", [2, 3, 5])
+def test_paper_cost_model_within_eps(gs, D):
+    """Series-heavy runs (the paper's unit cost weights) stay within eps."""
+    q, r, w = synth.small_random(90 + D, 8000, D)
+    h = synth.log_bandwidths(synth.bbox_diagonal(r), 6, 1e-2, 1.0)
+    for eps in (1e-2, 1e-4):
+        st = gs.gs_stats()
+        out = gs.gs_sum(_dev(q), _dev(q), _dev(w), h, eps, opts=_opts(gs, cw=PAPER), stats=st).cpu().numpy()
+        exact = oracle_ex.gauss_sum(q, r, w, h)
+        assert rel_err(out, exact).max() <= eps
+        assert st.pairs_dh + st.pairs_dl + st.pairs_h2l > 0

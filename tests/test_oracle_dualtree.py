@@ -146,7 +146,8 @@ def test_series_methods_are_used_in_low_dimension():
     q, r, w, mono = _problem(40, 3000, 2)
     qt, rt = _trees(q, r, w, mono, 16)
     h = np.array([0.1, 0.3])
-    trav = T.traverse(qt, rt, mono, h, 1e-3, w_max=float(w.max()))
+    # the paper's unit cost weights favour series actions in 2-D
+    trav = T.traverse(qt, rt, mono, h, 1e-3, w_max=float(w.max()), cost_weight=(1, 1, 1, 1))
     methods = np.concatenate([it["method"] for it in trav.iters])
     assert np.isin([T.DH, T.DL, T.H2L], methods).any()
     got, _ = T.estimate(qt, rt, q, r, w, h, trav)
