@@ -6,10 +6,12 @@ uniform background, 16 log-spaced bandwidths from 1e-3 to 1 times the data
 diameter, eps = 1e-2).
 
 One step = one pass of the whole path over the workload, inputs resident in
-HBM: `--mode sum` (default) runs gs_sum with eps=1e-2 (tree build, frontier,
-series, base case, downward pass); `--mode exhaustive` runs the exhaustive
-sum (eps=0) instead.  The L2 cache is flushed before every timed step (inputs
-are 12 MB, smaller than L2).
+HBM: `--mode lscv` (default) runs gs_lscv -- the dual-tree sums for all 16
+bandwidths h and their sqrt(2) h companions (32 Gaussian sums: tree build,
+frontier, series, base case, downward pass) and the LSCV reduction;
+`--mode sum` runs gs_sum over the 16 bandwidths only; `--eps 0` selects the
+exhaustive sums instead of the dual tree.  The L2 cache is flushed before
+every timed step (inputs are 12 MB, smaller than L2).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded query sample of the same workload instead.
@@ -38,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
-    ap.add_argument("--mode", default="exhaustive", choices=["sum", "exhaustive"])
+    ap.add_argument("--mode", default="lscv", choices=["lscv", "sum"])
+    ap.add_argument("--eps", type=float, default=None, help="override eps (0 = exhaustive)")
     ap.add_argument("--scale", type=float, default=1.0, help="workload size factor (1 = full)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -50,9 +53,16 @@ def workload(scale):
     return synth.config2(scale)
 
 
+def sum_bandwidths(wl, mode):
+    """Bandwidths one step sums over: the sweep, plus sqrt(2) h for LSCV."""
+    from workloads import synth
+    return synth.lscv_bandwidths(wl.h) if mode == "lscv" else wl.h
+
+
 def wl_config(wl, mode, eps):
     return {"workload": "kde_sweep_d3_n%d_mono_16h" % wl.N, "M": wl.M, "N": wl.N, "D": wl.D,
-            "nh": int(wl.h.size), "eps": eps, "mode": mode, "leaf_size": wl.leaf_size,
+            "nh": int(wl.h.size), "gaussian_sums": int(sum_bandwidths(wl, mode).size), "eps": eps,
+            "mode": mode, "leaf_size": wl.leaf_size,
             "h_range_x_diameter": [1e-3, 1.0], "diameter": round(wl.diameter, 6),
             "input_dtype": "f32", "l2": "flushed before every timed step (256 MB write)",
             "parallelism": "replicas"}
@@ -116,14 +126,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(wl, nq, seed=0):
+def oracle_sample_rate(wl, nq, hs, seed=0):
     from oracle import exhaustive as oracle_ex
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(wl.M, nq, replace=False))
     t0 = time.perf_counter()
-    oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, wl.h)
+    oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, hs)
     dt = time.perf_counter() - t0
-    return nq * wl.N * wl.h.size / dt, dt, oracle_ex.num_threads()
+    return nq * wl.N * hs.size / dt, dt, oracle_ex.num_threads()
 
 
 def run_reference(args):
@@ -133,16 +143,17 @@ def run_reference(args):
     wl = workload(args.scale)
     from oracle import build as ob
     ob.build()
-    nq = max(1, int(200 * min(1.0, 1.0 / args.scale)))   # ~3e9 evals per step at full size
+    hs = sum_bandwidths(wl, args.mode)
+    nq = max(1, int(100 * min(1.0, 1.0 / args.scale)))   # ~3e9 evals per step at full size
     for _ in range(args.warmup):
-        oracle_sample_rate(wl, max(1, nq // 8), seed=99)
+        oracle_sample_rate(wl, max(1, nq // 8), hs, seed=99)
     rates, secs = [], []
     for k in range(args.steps):
-        r, dt, cores = oracle_sample_rate(wl, nq, seed=k)
+        r, dt, cores = oracle_sample_rate(wl, nq, hs, seed=k)
         rates.append(r)
         secs.append(dt)
     value = float(np.mean(rates))
-    sample = "%d seeded queries x all %d refs x %d bandwidths per step" % (nq, wl.N, wl.h.size)
+    sample = "%d seeded queries x all %d refs x %d bandwidths per step" % (nq, wl.N, hs.size)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
@@ -198,16 +209,21 @@ def run_gs(args):
     gs.load()
 
     wl = workload(args.scale)
-    eps = 0.0 if args.mode == "exhaustive" else wl.eps
+    eps = wl.eps if args.eps is None else args.eps
+    hs = sum_bandwidths(wl, args.mode)
     dev = torch.device("cuda", local)
     tq = torch.from_numpy(wl.queries).to(dev)
     tw = torch.from_numpy(wl.weights).to(dev)
     out = torch.empty((wl.M, wl.h.size), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    scores = {}
 
     def step(stats=None):
-        gs.gs_sum(tq, tq, tw, wl.h, eps, out=out, stream=stream, stats=stats)
+        if args.mode == "lscv":
+            scores["lscv"] = gs.gs_lscv(tq, tw, wl.h, eps, stream=stream, stats=stats)
+        else:
+            gs.gs_sum(tq, tq, tw, wl.h, eps, out=out, stream=stream, stats=stats)
 
     for _ in range(args.warmup):
         step()
@@ -243,7 +259,7 @@ def run_gs(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
-    units = float(wl.M) * wl.N * wl.h.size          # kernel evaluations one step stands for
+    units = float(wl.M) * wl.N * hs.size            # kernel evaluations one step stands for
     value = units * world / (ms / 1e3)
     base_ms = float(np.mean([s.ms_phase[gs.GS_PH_BASE] / max(1, s.launches_base) for s in stats_list]))
     evals_base = float(np.mean([s.point_pairs_base / max(1, s.launches_base) for s in stats_list]))
@@ -255,7 +271,7 @@ def run_gs(args):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = ex2_rate * props.multi_processor_count * sm_mhz * 1e6 / 1e12
     achieved = evals_base / (base_ms / 1e3) / 1e12
-    kname = "k_exhaustive" if args.mode == "exhaustive" else "k_basecase"
+    kname = "k_exhaustive" if eps == 0.0 else "k_basecase"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
             "frac": achieved / peak if peak else None,
             "traffic": load_traffic(kname, source_sha()),
@@ -263,30 +279,43 @@ def run_gs(args):
             % (ex2_rate, props.multi_processor_count, sm_mhz),
             "ffma_lanes_per_sm_clk": ffma_rate, "kernel_ms_per_launch": base_ms}
 
-    # end to end: host (pinned) buffers through the C-ABI host entry point
+    # end to end: inputs start in pinned host memory and the step's result
+    # comes back to the host, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        hq = torch.from_numpy(wl.queries).pin_memory().numpy()
-        hw = torch.from_numpy(wl.weights).pin_memory().numpy()
-        hout = torch.empty((wl.M, wl.h.size), dtype=torch.float64).pin_memory().numpy()
-        gs.gs_sum_host(hq, hq, hw, wl.h, eps, out=hout)
-        torch.cuda.synchronize()
+        hq = torch.from_numpy(wl.queries).pin_memory()
+        hw = torch.from_numpy(wl.weights).pin_memory()
         n_e2e = max(1, min(args.steps, 3))
+        if args.mode == "lscv":
+            def e2e_step():
+                dq = hq.to(dev, non_blocking=True)
+                dw = hw.to(dev, non_blocking=True)
+                return gs.gs_lscv(dq, dw, wl.h, eps, stream=stream)   # returns host arrays
+            d2h = 2 * 8 * wl.h.size
+        else:
+            hout = torch.empty((wl.M, wl.h.size), dtype=torch.float64).pin_memory().numpy()
+
+            def e2e_step():
+                gs.gs_sum_host(hq.numpy(), hq.numpy(), hw.numpy(), wl.h, eps, out=hout)
+            d2h = int(hout.nbytes)
+        e2e_step()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            gs.gs_sum_host(hq, hq, hw, wl.h, eps, out=hout)
+            e2e_step()
+        torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / n_e2e
-        e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": int(hq.nbytes + hw.nbytes),
-               "d2h_bytes_per_step": int(hout.nbytes), "ms_per_step": dt * 1e3}
+        e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": int(hq.numel() * 4 + hw.numel() * 4),
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import build as ob
         ob.build()
-        nq = max(1, int(400 * min(1.0, 1.0 / args.scale)))
-        r, dt, cores = oracle_sample_rate(wl, nq)
+        nq = max(1, int(200 * min(1.0, 1.0 / args.scale)))
+        r, dt, cores = oracle_sample_rate(wl, nq, hs)
         cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
-               "sample": "%d seeded queries x all %d refs x %d bandwidths (%.1f s)" % (nq, wl.N, wl.h.size, dt)}
+               "sample": "%d seeded queries x all %d refs x %d bandwidths (%.1f s)" % (nq, wl.N, hs.size, dt)}
 
     if rank == 0:
         s0 = stats_list[-1]
@@ -296,6 +325,10 @@ def run_gs(args):
                 "config": wl_config(wl, args.mode, eps), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches * args.steps,
                 "stats": {k: v for k, v in s0.as_dict().items()}}
+        if "lscv" in scores:
+            sc, er = scores["lscv"]
+            line["lscv"] = {"h": [float(v) for v in wl.h], "score": [float(v) for v in sc],
+                            "err_bound": [float(v) for v in er], "argmin_h": float(wl.h[int(np.argmin(sc))])}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

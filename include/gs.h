@@ -175,6 +175,30 @@ int gs_sum_trace(const void *queries, int64_t M, const void *refs, const float *
                  int64_t *trace_len, int32_t *qperm, int32_t *rperm);
 
 /*
+ * gs_lscv -- least-squares cross-validation scores of a weighted Gaussian
+ * kernel density estimate over a bandwidth sweep (Section 7: the bandwidth
+ * range "according to the standard least-squares cross-validation scores").
+ * With normalised weights wbar_i = w_i / W and phi_h the normalised Gaussian,
+ *   LSCV(h) = int f^2 - 2 sum_i wbar_i f_{-i}(x_i)
+ *           = (4 pi h^2)^{-D/2} sum_i wbar_i G_{sqrt2 h}(x_i) / W
+ *             - 2 (2 pi h^2)^{-D/2} sum_i wbar_i (G_h(x_i) - w_i) / (W - w_i),
+ * so one monochromatic dual-tree pass over the 2 nh bandwidths
+ * {h_j} u {sqrt2 h_j} gives every score.
+ *   pts        device, N x D, dtype (queries = references)
+ *   weights    device, N floats > 0
+ *   h          HOST, nh bandwidths, 1 <= nh <= 32
+ *   eps        relative error of every Gaussian sum (0 = exhaustive)
+ *   score      HOST, nh doubles: LSCV(h_j)
+ *   score_err  HOST, nh doubles or NULL: a-posteriori bound on |score error|
+ *              implied by eps, eps * [(4 pi h^2)^{-D/2} sum wbar G_{sqrt2 h}/W
+ *              + 2 (2 pi h^2)^{-D/2} sum wbar G_h / (W - w_i)]
+ * stats, if given, describe the underlying gs_sum call.  Errors as gs_sum;
+ * GS_ERR_ARG when N < 2.
+ */
+int gs_lscv(const void *pts, int64_t N, int D, int dtype, const float *weights, const double *h, int nh,
+            double eps, double *score, double *score_err, const gs_opts *opts, void *stream, gs_stats *stats);
+
+/*
  * gs_sum_host -- gs_sum for callers whose data lives in HOST memory: every
  * array argument (queries, refs, weights, out) is host memory.  The call
  * copies the inputs to device scratch, runs gs_sum on `stream`, copies out

@@ -104,6 +104,29 @@ static int status_to_code(unsigned st) {
     return GS_OK;
 }
 
+// LSCV partial sums per bandwidth j (atomics across blocks):
+//   acc[3j]   += wbar_i G_{sqrt2 h}(x_i)
+//   acc[3j+1] += wbar_i (G_h(x_i) - w_i) / (W - w_i)
+//   acc[3j+2] += wbar_i G_h(x_i) / (W - w_i)
+__global__ void k_lscv_sums(const double *__restrict__ G, const float *__restrict__ w, int64_t N, int nh,
+                            const Ingest *__restrict__ ing, double *acc) {
+    __shared__ double sh[3 * 32];
+    for (int i = threadIdx.x; i < 3 * nh; i += blockDim.x) sh[i] = 0.0;
+    __syncthreads();
+    const double W = ing->wsum;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = (double)w[i], wb = wi / W, den = W - wi;
+        for (int j = 0; j < nh; ++j) {
+            const double gh = G[i * 2 * nh + j], g2 = G[i * 2 * nh + nh + j];
+            atomicAdd(&sh[3 * j], wb * g2);
+            atomicAdd(&sh[3 * j + 1], wb * (gh - wi) / den);
+            atomicAdd(&sh[3 * j + 2], wb * gh / den);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * nh; i += blockDim.x) atomicAdd(&acc[i], sh[i]);
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -220,6 +243,69 @@ int gs_sum_trace(const void *queries, int64_t M, const void *refs, const float *
     t.rperm = rperm;
     if (trace_len) *trace_len = 0;
     return sum_impl(queries, M, refs, weights, N, D, dtype, h, nh, eps, out, opts, stream, stats, &t);
+}
+
+int gs_lscv(const void *pts, int64_t N, int D, int dtype, const float *weights, const double *h, int nh,
+            double eps, double *score, double *score_err, const gs_opts *opts, void *stream, gs_stats *stats) {
+    g_err[0] = 0;
+    if (!score) {
+        set_error("gs_lscv: NULL score");
+        return GS_ERR_ARG;
+    }
+    if (N < 2) {
+        set_error("gs_lscv needs N >= 2");
+        return GS_ERR_ARG;
+    }
+    if (nh < 1 || nh > 32 || !h) {
+        set_error("gs_lscv: nh=%d outside [1, 32]", nh);
+        return GS_ERR_ARG;
+    }
+    double hh[64];
+    for (int j = 0; j < nh; ++j) {
+        hh[j] = h[j];
+        hh[nh + j] = h[j] * 1.4142135623730951;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double *G = nullptr, *acc = nullptr;
+    Ingest *ing = nullptr;
+    GS_CUDA_TRY(cudaMallocAsync((void **)&G, (size_t)N * 2 * nh * sizeof(double), st));
+    int rc = sum_impl(pts, N, pts, weights, N, D, dtype, hh, 2 * nh, eps, G, opts, stream, stats, nullptr);
+    if (rc == GS_OK) {
+        // total weight (the library's own ingest reduction) and the sums
+        cudaError_t e = cudaMallocAsync((void **)&ing, sizeof(Ingest), st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&acc, 3 * 32 * sizeof(double), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * 32 * sizeof(double), st);
+        CallCtx cx;
+        cx.st = st;
+        if (e == cudaSuccess) e = launch_ingest(ing, pts, N, pts, weights, N, D, dtype, cx);
+        if (e == cudaSuccess) {
+            int64_t blocks = (N + 255) / 256;
+            if (blocks > 1024) blocks = 1024;
+            k_lscv_sums<<<(unsigned)blocks, 256, 0, st>>>(G, weights, N, nh, ing, acc);
+            e = cudaGetLastError();
+        }
+        double hacc[3 * 32];
+        Ingest hing;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hing, ing, sizeof(hing), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "gs_lscv");
+        } else {
+            const double W = hing.wsum;
+            const double pi = 3.141592653589793;
+            for (int j = 0; j < nh; ++j) {
+                const double c2 = pow(4.0 * pi * h[j] * h[j], -0.5 * D);
+                const double c1 = pow(2.0 * pi * h[j] * h[j], -0.5 * D);
+                score[j] = c2 * hacc[3 * j] / W - 2.0 * c1 * hacc[3 * j + 1];
+                if (score_err) score_err[j] = eps * (c2 * hacc[3 * j] / W + 2.0 * c1 * hacc[3 * j + 2]);
+            }
+        }
+    }
+    cudaFreeAsync(G, st);
+    if (acc) cudaFreeAsync(acc, st);
+    if (ing) cudaFreeAsync(ing, st);
+    return rc;
 }
 
 int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,

@@ -37,106 +37,113 @@ struct BaseParams {
     unsigned long long *evals;         // point-pair evaluations (statistics)
 };
 
+constexpr int kBaseWarps = 4;
+
+// One CTA per base group; its warps take the group's reference leaves
+// round-robin and their per-query sums are combined in shared memory before
+// a single FP64 atomic per query.
 template <int DP, int QPL, bool ANCH>
-__global__ void __launch_bounds__(256)
-k_basecase(BaseParams bp, const FrontierState *__restrict__ fs, const Group *__restrict__ bgroups,
-           const int32_t *__restrict__ base_r) {
+__global__ void __launch_bounds__(32 * kBaseWarps)
+k_basecase(BaseParams bp, const Group *__restrict__ bgroups, const int32_t *__restrict__ base_r) {
     constexpr int NT = RefRec<float, DP>::NT;
-    const int lane = threadIdx.x & 31;
-    const int64_t ng = fs->base_groups;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    __shared__ double red[kBaseWarps][QPL * 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float wmax = __uint_as_float(bp.ing->wmax_bits);
     const int64_t qleaf0 = (1ll << bp.q_depth) - 1, rleaf0 = (1ll << bp.r_depth) - 1;
-    unsigned long long my_evals = 0;
-    for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += warps) {
-        const Group G = bgroups[g];
-        const int64_t qi = G.q - qleaf0;
-        const int64_t qb = level_begin(bp.qn, bp.q_depth, qi), qe = level_begin(bp.qn, bp.q_depth, qi + 1);
-        const int nq = (int)(qe - qb);
-        const float c = bp.negc[G.j];
-        float xq[QPL][DP];
+    const Group G = bgroups[blockIdx.x];
+    const int64_t qi = G.q - qleaf0;
+    const int64_t qb = level_begin(bp.qn, bp.q_depth, qi), qe = level_begin(bp.qn, bp.q_depth, qi + 1);
+    const int nq = (int)(qe - qb);
+    const float c = bp.negc[G.j];
+    float xq[QPL][DP];
 #pragma unroll
-        for (int s = 0; s < QPL; ++s) {
-            const int qq = lane + 32 * s;
-            const int64_t pos = qb + (qq < nq ? qq : 0);
+    for (int s = 0; s < QPL; ++s) {
+        const int qq = lane + 32 * s;
+        const int64_t pos = qb + (qq < nq ? qq : 0);
 #pragma unroll
-            for (int d = 0; d < DP; ++d) xq[s][d] = bp.qrec[pos * NT + d];
-        }
-        // three-level summation: FP32 over one reference leaf, FP32 over up to
-        // kLeavesPerRun leaves, FP64 across runs (keeps the FP64 pipe off the
-        // critical path while bounding the FP32 sums to a few hundred terms)
-        double acc[QPL];
-        float run[QPL];
-#pragma unroll
-        for (int s = 0; s < QPL; ++s) {
-            acc[s] = 0.0;
-            run[s] = 0.f;
-        }
-        int in_run = 0;
-        unsigned long long grp_refs = 0;
-        for (int k = 0; k < G.cnt; ++k) {
-            const int64_t rnode = base_r[G.off + k];
-            const int64_t ri = rnode - rleaf0;
-            const int64_t rb = level_begin(bp.rn, bp.r_depth, ri), re = level_begin(bp.rn, bp.r_depth, ri + 1);
-            float dc[DP];
-#pragma unroll
-            for (int d = 0; d < DP; ++d) dc[d] = 0.f;
-            if (ANCH) {
-                for (int d = 0; d < bp.D; ++d)
-                    dc[d] = (float)(bp.qcenter[G.q * bp.D + d] - bp.rcenter[rnode * bp.D + d]);
-            }
-            float part[QPL];
-#pragma unroll
-            for (int s = 0; s < QPL; ++s) part[s] = 0.f;
-            const float4 *rp = reinterpret_cast<const float4 *>(bp.rrec + rb * NT);
-#pragma unroll 2
-            for (int64_t p = rb; p < re; ++p, rp += NT / 4) {
-                float rv[NT];
-#pragma unroll
-                for (int v = 0; v < NT / 4; ++v) {
-                    const float4 f = __ldg(rp + v);
-                    rv[4 * v] = f.x; rv[4 * v + 1] = f.y; rv[4 * v + 2] = f.z; rv[4 * v + 3] = f.w;
-                }
-                const float l = rv[DP];
-#pragma unroll
-                for (int s = 0; s < QPL; ++s) {
-                    float d2 = 0.f;
-#pragma unroll
-                    for (int d = 0; d < DP; ++d) {
-                        const float df = ANCH ? (xq[s][d] - rv[d]) + dc[d] : xq[s][d] - rv[d];
-                        d2 = fmaf(df, df, d2);
-                    }
-                    part[s] += ex2_approx(fmaf(d2, c, l));
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < QPL; ++s) run[s] += part[s];
-            if (++in_run == kLeavesPerRun) {
-#pragma unroll
-                for (int s = 0; s < QPL; ++s) {
-                    acc[s] += (double)run[s];
-                    run[s] = 0.f;
-                }
-                in_run = 0;
-            }
-            grp_refs += (unsigned long long)(re - rb);
-        }
-#pragma unroll
-        for (int s = 0; s < QPL; ++s) acc[s] += (double)run[s];
-#pragma unroll
-        for (int s = 0; s < QPL; ++s) {
-            const int qq = lane + 32 * s;
-            if (qq < nq) atomicAdd(&bp.Gq[(qb + qq) * bp.nh + G.j], acc[s] * (double)wmax);
-        }
-        if (lane == 0) my_evals += grp_refs * (unsigned long long)nq;
+        for (int d = 0; d < DP; ++d) xq[s][d] = bp.qrec[pos * NT + d];
     }
-    if (bp.evals && my_evals) atomicAdd(bp.evals, my_evals);
+    // three-level summation: FP32 over one reference leaf, FP32 over up to
+    // kLeavesPerRun leaves, FP64 across runs (keeps the FP64 pipe off the
+    // critical path while bounding each FP32 sum to a few hundred terms)
+    double acc[QPL];
+    float run[QPL];
+#pragma unroll
+    for (int s = 0; s < QPL; ++s) {
+        acc[s] = 0.0;
+        run[s] = 0.f;
+    }
+    int in_run = 0;
+    unsigned long long grp_refs = 0;
+    for (int k = w; k < G.cnt; k += kBaseWarps) {
+        const int64_t rnode = base_r[G.off + k];
+        const int64_t ri = rnode - rleaf0;
+        const int64_t rb = level_begin(bp.rn, bp.r_depth, ri), re = level_begin(bp.rn, bp.r_depth, ri + 1);
+        float dc[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) dc[d] = 0.f;
+        if (ANCH) {
+            for (int d = 0; d < bp.D; ++d)
+                dc[d] = (float)(bp.qcenter[G.q * bp.D + d] - bp.rcenter[rnode * bp.D + d]);
+        }
+        float part[QPL];
+#pragma unroll
+        for (int s = 0; s < QPL; ++s) part[s] = 0.f;
+        const float4 *rp = reinterpret_cast<const float4 *>(bp.rrec + rb * NT);
+        const int nr = (int)(re - rb);
+#pragma unroll 4
+        for (int i = 0; i < nr; ++i) {
+            float rv[NT];
+#pragma unroll
+            for (int v = 0; v < NT / 4; ++v) {
+                const float4 f = __ldg(rp + i * (NT / 4) + v);
+                rv[4 * v] = f.x; rv[4 * v + 1] = f.y; rv[4 * v + 2] = f.z; rv[4 * v + 3] = f.w;
+            }
+            const float l = rv[DP];
+#pragma unroll
+            for (int s = 0; s < QPL; ++s) {
+                float d2 = 0.f;
+#pragma unroll
+                for (int d = 0; d < DP; ++d) {
+                    const float df = ANCH ? (xq[s][d] - rv[d]) + dc[d] : xq[s][d] - rv[d];
+                    d2 = fmaf(df, df, d2);
+                }
+                part[s] += ex2_approx(fmaf(d2, c, l));
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < QPL; ++s) run[s] += part[s];
+        if (++in_run == kLeavesPerRun) {
+#pragma unroll
+            for (int s = 0; s < QPL; ++s) {
+                acc[s] += (double)run[s];
+                run[s] = 0.f;
+            }
+            in_run = 0;
+        }
+        grp_refs += (unsigned long long)nr;
+    }
+#pragma unroll
+    for (int s = 0; s < QPL; ++s) red[w][s * 32 + lane] = acc[s] + (double)run[s];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int s = 0; s < QPL; ++s) {
+            const int qq = lane + 32 * s;
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < kBaseWarps; ++k) v += red[k][s * 32 + lane];
+            if (qq < nq) atomicAdd(&bp.Gq[(qb + qq) * bp.nh + G.j], v * (double)wmax);
+        }
+    }
+    if (bp.evals && lane == 0 && grp_refs) atomicAdd(bp.evals, grp_refs * (unsigned long long)nq);
 }
 
 template <int DP>
 static void launch_dp(int qpl, bool anch, const BaseParams &bp, const FrontierState *fs, const Group *bg,
-                      const int32_t *br, int grid, cudaStream_t st) {
-#define GS_L(Q, A) k_basecase<DP, Q, A><<<grid, 256, 0, st>>>(bp, fs, bg, br)
+                      const int32_t *br, int64_t grid, cudaStream_t st) {
+    (void)fs;
+#define GS_L(Q, A) k_basecase<DP, Q, A><<<(unsigned)grid, 32 * kBaseWarps, 0, st>>>(bp, bg, br)
     if (anch) {
         if (qpl <= 1) GS_L(1, true); else if (qpl <= 2) GS_L(2, true); else GS_L(4, true);
     } else {
@@ -169,8 +176,12 @@ int run_basecase(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, Ca
         return GS_ERR_ARG;
     }
     const bool anch = in.qt->dtype == GS_F64;
-    const int grid = fb.grid_warps / 8;
+    const int64_t grid = fb.n_base_groups;
     cx.phase(GS_PH_BASE);
+    if (grid == 0) {
+        cx.phase(GS_PH_OTHER);
+        return GS_OK;
+    }
     switch (DP) {
         case 1: launch_dp<1>(qpl, anch, bp, fb.fs, fb.base_groups, fb.base_r, grid, cx.st); break;
         case 2: launch_dp<2>(qpl, anch, bp, fb.fs, fb.base_groups, fb.base_r, grid, cx.st); break;

@@ -62,40 +62,68 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Shared-memory layout of the series kernels: the multi-index exponent
+// table (T x D bytes) and degrees (T bytes) of the whole order-P set, then
+// one region per warp.
+__device__ __forceinline__ void load_tables(const SeriesTables &tb, int D, uint8_t *al_s, uint8_t *dg_s) {
+    for (int i = threadIdx.x; i < tb.T * D; i += blockDim.x) al_s[i] = tb.alpha[i];
+    for (int i = threadIdx.x; i < tb.T; i += blockDim.x) dg_s[i] = tb.deg[i];
+    __syncthreads();
+}
+
+__host__ __device__ inline int table_bytes(int T, int D) { return ((T * D + 7) / 8 + (T + 7) / 8) * 8; }
+
 // ---------------------------------------------------------------------------
-// DH: one warp per action, lanes over the queries of Q
+// DH: one warp per action, lanes over the queries of Q; per-lane Hermite
+// polynomial tables in shared memory (lane-minor, conflict-free)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_series_dh(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+__global__ void k_series_dh(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+    extern __shared__ double smem_d[];
+    const int D = sp.D, T = sp.T, P = sp.P;
+    uint8_t *al_s = (uint8_t *)smem_d;
+    uint8_t *dg_s = al_s + ((T * D + 7) / 8) * 8;
+    load_tables(sp.tb, D, al_s, dg_s);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double *A = smem_d + table_bytes(T, D) / 8 + (size_t)w * (T + D * P * 32);
+    double *Hs = A + T;
     const int64_t ne = fs->series_count[0];
-    const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int D = sp.D;
-    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < ne; e += warps) {
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; e < ne; e += warps) {
         const SeriesEntry E = ent[e];
         const int p = E.p, Tp = sp.tb.Tp[p];
         const double is = sp.inv_s[E.j];
-        double ispow[16];
-        ispow[0] = 1.0;
-        for (int k = 1; k < p; ++k) ispow[k] = ispow[k - 1] * is;
-        const double *mom = sp.rmom + (int64_t)E.r * sp.T;
+        const double *mom = sp.rmom + (int64_t)E.r * T;
+        __syncwarp();
+        for (int a = lane; a < Tp; a += 32) {
+            double v = mom[a];
+            for (int k = 0; k < dg_s[a]; ++k) v *= is;
+            A[a] = v;
+        }
+        __syncwarp();
         const double *cR = sp.rcenter + (int64_t)E.r * D;
         const int qd = node_depth(E.q);
         const int64_t qi = E.q - ((1ll << qd) - 1);
         const int64_t b = level_begin(sp.qn, qd, qi), en = level_begin(sp.qn, qd, qi + 1);
         for (int64_t pos = b + lane; pos < en; pos += 32) {
-            double H[kMaxDP];
             double t2 = 0.0;
             for (int d = 0; d < D; ++d) {
                 const double t = (coord(sp.qxs, sp.dtype, pos, D, d) - cR[d]) * is;
-                hermite_polys(t, p, &H[d * p]);
+                double h0 = 1.0, h1 = 2.0 * t;
+                Hs[(d * p) * 32 + lane] = h0;
+                if (p > 1) Hs[(d * p + 1) * 32 + lane] = h1;
+                for (int k = 1; k + 1 < p; ++k) {
+                    const double h2 = 2.0 * t * h1 - 2.0 * k * h0;
+                    Hs[(d * p + k + 1) * 32 + lane] = h2;
+                    h0 = h1;
+                    h1 = h2;
+                }
                 t2 += t * t;
             }
             double s = 0.0;
             for (int a = 0; a < Tp; ++a) {
-                const uint8_t *al = sp.tb.alpha + a * D;
-                double pr = mom[a] * ispow[sp.tb.deg[a]];
-                for (int d = 0; d < D; ++d) pr *= H[d * p + al[d]];
+                const uint8_t *al = al_s + a * D;
+                double pr = A[a];
+                for (int d = 0; d < D; ++d) pr *= Hs[(d * p + al[d]) * 32 + lane];
                 s += pr;
             }
             atomicAdd(&sp.Gq[pos * sp.nh + E.j], s * exp(-t2));
@@ -104,16 +132,23 @@ k_series_dh(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesE
 }
 
 // ---------------------------------------------------------------------------
-// DL: one warp per action, lanes over the references of R; each coefficient
-// is reduced across the warp and banked by lane (b mod 32)
+// DL: one warp per action, lanes over the coefficients b; references of R
+// in chunks of 32 whose Hermite tables are built cooperatively in shared
+// memory
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_series_dl(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+__global__ void k_series_dl(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+    extern __shared__ double smem_d[];
+    const int D = sp.D, T = sp.T, P = sp.P;
+    uint8_t *al_s = (uint8_t *)smem_d;
+    uint8_t *dg_s = al_s + ((T * D + 7) / 8) * 8;
+    load_tables(sp.tb, D, al_s, dg_s);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int DPp = D * P;
+    double *Hr = smem_d + table_bytes(T, D) / 8 + (size_t)w * (32 * DPp + 32);
+    double *we = Hr + 32 * DPp;
     const int64_t ne = fs->series_count[1];
-    const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int D = sp.D;
-    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < ne; e += warps) {
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; e < ne; e += warps) {
         const SeriesEntry E = ent[e];
         const int p = E.p, Tp = sp.tb.Tp[p];
         const double is = sp.inv_s[E.j];
@@ -121,79 +156,90 @@ k_series_dl(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesE
         const int rd = node_depth(E.r);
         const int64_t ri = E.r - ((1ll << rd) - 1);
         const int64_t rb = level_begin(sp.rn, rd, ri), re = level_begin(sp.rn, rd, ri + 1);
-        double acc[kMaxT / 32];
-        for (int i = 0; i < (Tp + 31) / 32; ++i) acc[i] = 0.0;
-        for (int64_t c0 = rb; c0 < re; c0 += 32) {
-            const int64_t pos = c0 + lane;
-            const bool valid = pos < re;
-            double H[kMaxDP];
-            double we = 0.0;
-            if (valid) {
-                double v2 = 0.0;
-                for (int d = 0; d < D; ++d) {
-                    const double v = (coord(sp.rxs, sp.dtype, pos, D, d) - cQ[d]) * is;
-                    hermite_polys(v, p, &H[d * p]);
-                    v2 += v * v;
+        double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * T;
+        for (int b0 = 0; b0 < Tp; b0 += 32) {
+            const int bt = b0 + lane;
+            const uint8_t *be = al_s + (bt < Tp ? bt : 0) * D;
+            double acc = 0.0;
+            for (int64_t c0 = rb; c0 < re; c0 += 32) {
+                const int nc = (int)min((int64_t)32, re - c0);
+                __syncwarp();
+                if (lane < nc) {
+                    const int64_t pos = c0 + lane;
+                    double v2 = 0.0;
+                    double *H = Hr + lane * DPp;
+                    for (int d = 0; d < D; ++d) {
+                        const double v = (coord(sp.rxs, sp.dtype, pos, D, d) - cQ[d]) * is;
+                        hermite_polys(v, p, &H[d * p]);
+                        v2 += v * v;
+                    }
+                    we[lane] = (double)sp.w[sp.rperm[pos]] * exp(-v2);
                 }
-                we = (double)sp.w[sp.rperm[pos]] * exp(-v2);
-            } else {
-                for (int i = 0; i < D * p; ++i) H[i] = 0.0;
+                __syncwarp();
+                if (bt < Tp) {
+                    for (int r = 0; r < nc; ++r) {
+                        const double *H = Hr + r * DPp;
+                        double pr = we[r];
+                        for (int d = 0; d < D; ++d) pr *= H[d * p + be[d]];
+                        acc += pr;
+                    }
+                }
             }
-            for (int a = 0; a < Tp; ++a) {
-                const uint8_t *be = sp.tb.alpha + a * D;
-                double pr = we;
-                for (int d = 0; d < D; ++d) pr *= H[d * p + be[d]];
-                pr = warp_sum_d(pr);
-                if ((a & 31) == lane) acc[a >> 5] += pr;
-            }
+            if (bt < Tp) atomicAdd(&Bq[bt], acc * sp.tb.inv_fact[bt]);
         }
-        double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * sp.T;
-        for (int a = lane; a < Tp; a += 32) atomicAdd(&Bq[a], acc[a >> 5] * sp.tb.inv_fact[a]);
         if (lane == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
     }
 }
 
 // ---------------------------------------------------------------------------
-// H2L: one warp per action, lanes over b, loop over a; the 1-D Hermite
-// polynomials of tau = (x_Q - x_R)/s up to order 2p-2 sit in shared memory
+// H2L: one warp per action, lanes over b, loop over a; A_a and the 1-D
+// Hermite polynomials of tau = (x_Q - x_R)/s (orders 0 .. 2p-2) in shared
+// memory
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_series_h2l(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
-    __shared__ double Hs[8][2 * kMaxDP];
-    const int64_t ne = fs->series_count[2];
+__global__ void k_series_h2l(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+    extern __shared__ double smem_d[];
+    const int D = sp.D, T = sp.T, P = sp.P;
+    uint8_t *al_s = (uint8_t *)smem_d;
+    uint8_t *dg_s = al_s + ((T * D + 7) / 8) * 8;
+    load_tables(sp.tb, D, al_s, dg_s);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nHmax = 2 * P - 1;
+    double *A = smem_d + table_bytes(T, D) / 8 + (size_t)w * (T + D * nHmax);
+    double *Hs = A + T;
+    const int64_t ne = fs->series_count[2];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int D = sp.D;
     for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; e < ne; e += warps) {
         const SeriesEntry E = ent[e];
         const int p = E.p, Tp = sp.tb.Tp[p];
-        const int nH = 2 * p - 1;   // orders 0 .. 2p-2
+        const int nH = 2 * p - 1;
         const double is = sp.inv_s[E.j];
-        double ispow[16];
-        ispow[0] = 1.0;
-        for (int k = 1; k < p; ++k) ispow[k] = ispow[k - 1] * is;
-        const double *mom = sp.rmom + (int64_t)E.r * sp.T;
+        const double *mom = sp.rmom + (int64_t)E.r * T;
         __syncwarp();
+        for (int a = lane; a < Tp; a += 32) {
+            double v = mom[a];
+            for (int k = 0; k < dg_s[a]; ++k) v *= is;
+            A[a] = v;
+        }
         double t2 = 0.0;
         if (lane < D) {
             const double tau = (sp.qcenter[(int64_t)E.q * D + lane] - sp.rcenter[(int64_t)E.r * D + lane]) * is;
-            hermite_polys(tau, nH, &Hs[w][lane * nH]);
+            hermite_polys(tau, nH, &Hs[lane * nH]);
             t2 = tau * tau;
         }
         t2 = warp_sum_d(t2);
         __syncwarp();
         const double et = exp(-t2);
-        double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * sp.T;
+        double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * T;
         for (int bt = lane; bt < Tp; bt += 32) {
-            const uint8_t *be = sp.tb.alpha + bt * D;
+            const uint8_t *be = al_s + bt * D;
             double s = 0.0;
             for (int a = 0; a < Tp; ++a) {
-                const uint8_t *al = sp.tb.alpha + a * D;
-                double pr = mom[a] * ispow[sp.tb.deg[a]];
-                for (int d = 0; d < D; ++d) pr *= Hs[w][d * nH + al[d] + be[d]];
+                const uint8_t *al = al_s + a * D;
+                double pr = A[a];
+                for (int d = 0; d < D; ++d) pr *= Hs[d * nH + al[d] + be[d]];
                 s += pr;
             }
-            const double sign = (sp.tb.deg[bt] & 1) ? -1.0 : 1.0;
+            const double sign = (dg_s[bt] & 1) ? -1.0 : 1.0;
             atomicAdd(&Bq[bt], sign * sp.tb.inv_fact[bt] * et * s);
         }
         if (lane == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
@@ -332,26 +378,34 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         }
         cx.phase(GS_PH_SERIES);
         int rc;
-        auto grid_for = [&](int64_t n) {
-            int64_t g = (n + 7) / 8;
-            const int64_t mx = fb.grid_warps / 8;
-            return (unsigned)(g < 1 ? 1 : (g > mx ? mx : g));
+        const int tbytes = table_bytes(sp.T, sp.D);
+        auto launch = [&](int which, int64_t n, size_t per_warp) -> int {
+            if (n <= 0) return GS_OK;
+            int wpb = 8;
+            while (wpb > 1 && tbytes + wpb * per_warp > 200 * 1024) wpb >>= 1;
+            const size_t sm = tbytes + wpb * per_warp;
+            if (sm > 220 * 1024) {
+                set_error("series order too high for shared memory (D=%d, P=%d)", sp.D, sp.P);
+                return GS_ERR_ARG;
+            }
+            int64_t g = (n + wpb - 1) / wpb;
+            const int64_t mx = fb.grid_warps / wpb;
+            const unsigned grid = (unsigned)(g < 1 ? 1 : (g > mx ? mx : g));
+            const void *fn = which == 0 ? (const void *)k_series_dh
+                           : which == 1 ? (const void *)k_series_dl : (const void *)k_series_h2l;
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (which == 0)
+                k_series_dh<<<grid, wpb * 32, sm, st>>>(sp, fb.fs, fb.series[0]);
+            else if (which == 1)
+                k_series_dl<<<grid, wpb * 32, sm, st>>>(sp, fb.fs, fb.series[1]);
+            else
+                k_series_h2l<<<grid, wpb * 32, sm, st>>>(sp, fb.fs, fb.series[2]);
+            cx.launches += 1;
+            return cx.check(which == 0 ? "k_series_dh" : which == 1 ? "k_series_dl" : "k_series_h2l");
         };
-        if (fb.n_series[0] > 0) {
-            k_series_dh<<<grid_for(fb.n_series[0]), 256, 0, st>>>(sp, fb.fs, fb.series[0]);
-            cx.launches += 1;
-            if ((rc = cx.check("k_series_dh"))) return rc;
-        }
-        if (fb.n_series[1] > 0) {
-            k_series_dl<<<grid_for(fb.n_series[1]), 256, 0, st>>>(sp, fb.fs, fb.series[1]);
-            cx.launches += 1;
-            if ((rc = cx.check("k_series_dl"))) return rc;
-        }
-        if (fb.n_series[2] > 0) {
-            k_series_h2l<<<grid_for(fb.n_series[2]), 256, 0, st>>>(sp, fb.fs, fb.series[2]);
-            cx.launches += 1;
-            if ((rc = cx.check("k_series_h2l"))) return rc;
-        }
+        if ((rc = launch(0, fb.n_series[0], 8 * (size_t)(sp.T + sp.D * sp.P * 32)))) return rc;
+        if ((rc = launch(1, fb.n_series[1], 8 * (size_t)(32 * sp.D * sp.P + 32)))) return rc;
+        if ((rc = launch(2, fb.n_series[2], 8 * (size_t)(sp.T + sp.D * (2 * sp.P - 1))))) return rc;
         cx.phase(GS_PH_DOWN);
         for (int k = 0; k < in.qt->depth; ++k) {
             const int64_t items = (1ll << k) * in.nh;

@@ -86,6 +86,8 @@ SIGNATURES = {
     "gs_sum_host": (ctypes.c_int, _SUM_ARGS),
     "gs_probe_rates": (ctypes.c_int, [_VP, _VP, _VP]),
     "gs_sum_trace": (ctypes.c_int, _SUM_ARGS + [_VP, _I64, _VP, _VP, _VP]),
+    "gs_lscv": (ctypes.c_int, [_VP, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                               _VP, _VP, _VP, _VP, _VP]),
 }
 
 
@@ -193,6 +195,21 @@ def gs_sum_trace(queries, refs, weights, h, eps, opts: gs_opts | None = None, st
     if n.value > trace_cap:
         raise GSError(GS_ERR_CAPACITY, "trace of %d records exceeds trace_cap=%d" % (n.value, trace_cap))
     return out, tr[:n.value], qperm, rperm
+
+
+def gs_lscv(points, weights, h, eps, opts: gs_opts | None = None, stream=None, stats: gs_stats | None = None):
+    """LSCV scores (and their eps-implied error bounds) for every bandwidth in
+    h, from a torch CUDA tensor of points (N x D) and float32 weights."""
+    assert points.is_cuda and weights.is_cuda and points.is_contiguous() and weights.is_contiguous()
+    N, D = points.shape
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    score = np.empty(hh.size)
+    err = np.empty(hh.size)
+    _check(load().gs_lscv(_VP(points.data_ptr()), N, D, _dtype_code(points), _VP(weights.data_ptr()),
+                          hh.ctypes.data, hh.size, float(eps), score.ctypes.data, err.ctypes.data,
+                          ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream),
+                          ctypes.byref(stats) if stats is not None else None))
+    return score, err
 
 
 def gs_sum_host(queries: np.ndarray, refs: np.ndarray, weights: np.ndarray, h, eps,

@@ -1,0 +1,50 @@
+"""gs_lscv against the oracle's exact LSCV scores (Section 7's bandwidth
+selection criterion)."""
+import numpy as np
+import pytest
+
+from oracle import lscv as oracle_lscv
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+    from paper_1206_6857_gb300 import build, gs as _gs
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    _gs.load()
+    return _gs
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("D,n", [(2, 3000), (3, 2500), (5, 1500)])
+def test_lscv_exhaustive_and_dualtree(gs, D, n):
+    x, _, w = synth.small_random(200 + D, n, D)
+    h = synth.log_bandwidths(synth.bbox_diagonal(x), 8, 1e-2, 1.0)
+    want = oracle_lscv.lscv(x, w, h)
+    tx, tw = _dev(x), _dev(w)
+    got0, err0 = gs.gs_lscv(tx, tw, h, 0.0)
+    # exhaustive mode: every G within 1e-5, so the score within the bound that 1e-5 implies
+    _, scale = gs.gs_lscv(tx, tw, h, 1e-2)
+    tol0 = scale / 1e-2 * 1e-5
+    assert np.all(np.abs(got0 - want) <= tol0 + 1e-12 * np.abs(want))
+    for eps in (1e-2, 1e-3):
+        got, err = gs.gs_lscv(tx, tw, h, eps)
+        assert np.all(np.abs(got - want) <= err * (1 + 1e-6) + tol0)
+
+
+def test_lscv_full_size_sweep_runs(gs):
+    wl = synth.config2(0.05)
+    score, err = gs.gs_lscv(_dev(wl.queries), _dev(wl.weights), wl.h, wl.eps)
+    assert np.all(np.isfinite(score)) and np.all(err >= 0)
+    # the optimum lies strictly inside the sweep for clustered data
+    k = int(np.argmin(score))
+    assert 0 < k < wl.h.size - 1
