@@ -37,8 +37,9 @@ readings listed in the design doc; in short:
     inherit a copy of their parent's token and finished lower bound;
   * all group sums use one fixed order: 32 strided partial sums followed by
     an xor butterfly over the 32 partials;
-  * exp is evaluated with a Cody-Waite reduction and a degree-13 Taylor
-    polynomial (below), identically on both sides.
+  * the per-pair kernel bounds are FP32 with rigorous relative margins (an
+    exp2 written for this purpose, identically on both sides); everything
+    that sums or compares budgets is FP64.
 """
 from __future__ import annotations
 
@@ -51,28 +52,65 @@ from . import exhaustive as _ex
 from . import series as _S
 
 # --------------------------------------------------------------------------
-# exp(x), x <= 0, by Cody & Waite (1980) argument reduction x = k ln2 + r,
-# |r| <= ln2/2, and the Taylor polynomial of e^r to degree 13 (truncation
-# below 2^-56), evaluated by Horner's rule with separately rounded products
-# and sums; 2^k is applied exactly.  Results below e^-708 are returned as 0.
+# 2^x in FP32 for -125 <= x <= 0: x = k + f with k = rint(x), |f| <= 1/2,
+# 2^f by Horner on its degree-7 Taylor polynomial in f (coefficients
+# ln2^n / n!, truncation below 2^-27), times 2^k applied exactly.  Every
+# operation is a single IEEE round-to-nearest FP32 operation.  Its relative
+# error stays below 2^-20, which the bound margins below cover.
 # --------------------------------------------------------------------------
-INV_LN2 = 1.4426950408889634
-LN2_HI = float.fromhex("0x1.62e42fee00000p-1")     # ln 2 with 21 trailing zero bits
-LN2_LO = 1.9082149292705877e-10                   # ln 2 - LN2_HI to double precision
-_TAYLOR = [1.0 / math.factorial(n) for n in range(14)]
+def _exp2_coeffs():
+    c, t = [], 1.0
+    for n in range(8):
+        c.append(np.float32(t))
+        t = (t * 0.6931471805599453) / float(n + 1)
+    return c
 
 
-def exp_neg(x):
-    x = np.asarray(x, dtype=np.float64)
-    under = x < -708.0
-    x = np.where(under, 0.0, x)
-    k = np.rint(x * INV_LN2)
-    r = (x - k * LN2_HI) - k * LN2_LO
-    p = np.full(x.shape, _TAYLOR[13])
-    for n in range(12, -1, -1):
-        p = p * r + _TAYLOR[n]
-    out = np.ldexp(p, k.astype(np.int64))
-    return np.where(under, 0.0, out)
+E2C = _exp2_coeffs()
+F32_LO18 = np.float32(1.0 - 2.0 ** -18)
+F32_HI18 = np.float32(1.0 + 2.0 ** -18)
+F32_LO20 = np.float32(1.0 - 2.0 ** -20)
+F32_HI20 = np.float32(1.0 + 2.0 ** -20)
+F32_TINY = np.float32(2.0 ** -125)
+F32_AMAX = np.float32(125.0)
+
+
+def exp2_f32(x):
+    x = np.asarray(x, np.float32)
+    k = np.rint(x)
+    f = x - k
+    p = np.full(x.shape, E2C[7], dtype=np.float32)
+    for n in range(6, -1, -1):
+        p = p * f + E2C[n]
+    return np.ldexp(p, k.astype(np.int32)).astype(np.float32)
+
+
+def kernel_bounds(qt, rt, pq, pr, c32):
+    """Rigorous FP32 bounds of the kernel over a node pair (Section 5's
+    delta_min / delta_max from the bounding boxes): returns (K(delta_max)
+    lower bound, K(delta_min) upper bound, e^{-delta_min^2 / 4h^2} upper
+    bound).  The boxes are rounded outward to FP32; squared distances,
+    exponent arguments and exponentials carry relative margins of 2^-18,
+    2^-20 and 2^-18, each larger than the rounding they cover."""
+    D = qt.D
+    gsum = np.zeros(pq.size, np.float32)
+    fsum = np.zeros(pq.size, np.float32)
+    for d in range(D):
+        ql, qh = qt.lo32[pq, d], qt.hi32[pq, d]
+        rl, rh = rt.lo32[pr, d], rt.hi32[pr, d]
+        g = np.maximum(np.float32(0), np.maximum(rl - qh, ql - rh))
+        f = np.maximum(qh - rl, rh - ql)
+        gsum = gsum + g * g
+        fsum = fsum + f * f
+    dmin2 = gsum * F32_LO18
+    dmax2 = fsum * F32_HI18
+    amax = (dmax2 * c32) * F32_HI20
+    amin = (dmin2 * c32) * F32_LO20
+    a4 = amin * np.float32(0.5)
+    kmax = np.where(amax > F32_AMAX, np.float32(0), exp2_f32(-np.minimum(amax, F32_AMAX)) * F32_LO18)
+    kmin = np.where(amin > F32_AMAX, F32_TINY, exp2_f32(-np.minimum(amin, F32_AMAX)) * F32_HI18)
+    e4 = np.where(a4 > F32_AMAX, F32_TINY, exp2_f32(-np.minimum(a4, F32_AMAX)) * F32_HI18)
+    return kmax.astype(np.float32), kmin.astype(np.float32), e4.astype(np.float32)
 
 
 # --------------------------------------------------------------------------
@@ -111,6 +149,8 @@ class Tree:
     perm: np.ndarray          # sorted position -> original index
     lo: np.ndarray            # (nodes, D) float64
     hi: np.ndarray
+    lo32: np.ndarray          # lo rounded down to FP32
+    hi32: np.ndarray          # hi rounded up to FP32
     center: np.ndarray
     rad: np.ndarray           # half the widest extent
     W: np.ndarray             # node weight sums
@@ -168,7 +208,24 @@ def build_tree(x: np.ndarray, w: np.ndarray, L: int) -> Tree:
         W[node] = W[2 * node + 1] + W[2 * node + 2]
     center = (lo + hi) * 0.5
     rad = ((hi - lo) * 0.5).max(axis=1)
-    return Tree(n, D, depth, perm, lo, hi, center, rad, W, wmin, begin, end, split_dim)
+    return Tree(n, D, depth, perm, lo, hi, f32_down(lo), f32_up(hi), center, rad, W, wmin, begin, end,
+                split_dim)
+
+
+def f32_down(x):
+    """Round FP64 values to FP32 toward -infinity."""
+    f = np.asarray(x, np.float64).astype(np.float32)
+    bad = f.astype(np.float64) > x
+    f[bad] = np.nextafter(f[bad], np.float32(-np.inf))
+    return f
+
+
+def f32_up(x):
+    """Round FP64 values to FP32 toward +infinity."""
+    f = np.asarray(x, np.float64).astype(np.float32)
+    bad = f.astype(np.float64) < x
+    f[bad] = np.nextafter(f[bad], np.float32(np.inf))
+    return f
 
 
 # --------------------------------------------------------------------------
@@ -256,9 +313,7 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
     Dpow = [1.0]
     for _ in range(2 * P + 1):
         Dpow.append(Dpow[-1] * float(D))
-    two_h2 = (2.0 * h) * h
-    inv_2h2 = 1.0 / two_h2
-    inv_4h2 = 1.0 / ((4.0 * h) * h)
+    c32 = (1.4426950408889634 / ((2.0 * h) * h)).astype(np.float32)   # log2(e) / 2h^2
     inv_h = 1.0 / h
     nQ = qt.nodes
     fin = np.zeros((nQ, nh))
@@ -287,16 +342,10 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
         gq = pq[gstart]
         gj = pj[gstart]
 
-        # per-pair distance bounds (Section 5), summed dimension by dimension
-        dmin2 = np.zeros(pq.size)
-        dmax2 = np.zeros(pq.size)
-        for d in range(D):
-            g = np.maximum(0.0, np.maximum(rt.lo[pr, d] - qt.hi[pq, d], qt.lo[pq, d] - rt.hi[pr, d]))
-            f = np.maximum(qt.hi[pq, d] - rt.lo[pr, d], rt.hi[pr, d] - qt.lo[pq, d])
-            dmin2 = dmin2 + g * g
-            dmax2 = dmax2 + f * f
-        kmax = exp_neg(-(dmax2 * inv_2h2[pj]))
-        kmin = exp_neg(-(dmin2 * inv_2h2[pj]))
+        # per-pair kernel bounds (Section 5) in FP32 with rigorous margins
+        kmax32, kmin32, e4_32 = kernel_bounds(qt, rt, pq, pr, c32[pj])
+        kmax = kmax32.astype(np.float64)
+        kmin = kmin32.astype(np.float64)
         WR = rt.W[pr]
         dl = WR * kmax
         front = group_reduce(dl, gid, pos, ng)
@@ -323,8 +372,7 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
         leftover = np.where(use_fd, allot - n_fd, 0.0)
 
         if selector in (SEL_RULE, SEL_MLP) and P >= 1:
-            e4 = exp_neg(-(dmin2 * inv_4h2[pj]))
-            base = (WR * e4)
+            base = WR * e4_32.astype(np.float64)
             rR = rt.rad[pr] * inv_h[pj]
             rQ = qt.rad[pq] * inv_h[pj]
             best_c = np.full(pq.size, np.inf)

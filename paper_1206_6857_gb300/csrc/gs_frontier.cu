@@ -32,24 +32,26 @@
 
 namespace gs {
 
-__constant__ double c_taylor[14];
+__constant__ float c_e2[8];   // ln2^n / n!, rounded to FP32
 
-static const double kInvLn2 = 1.4426950408889634;
-static const double kLn2Hi = 0x1.62e42fee00000p-1;
-static const double kLn2Lo = 1.9082149292705877e-10;
 static const double kSqrt2 = 1.4142135623730951;
+#define F32_LO18 0x1.ffff8p-1f    // 1 - 2^-18
+#define F32_HI18 0x1.00004p+0f    // 1 + 2^-18
+#define F32_LO20 0x1.ffffep-1f    // 1 - 2^-20
+#define F32_HI20 0x1.00001p+0f    // 1 + 2^-20
+#define F32_TINY 0x1p-125f
+#define F32_AMAX 125.0f
 
-// exp(x) for x <= 0: x = k ln2 + r (Cody & Waite), e^r by Horner on the
-// degree-13 Taylor polynomial, times 2^k built exactly; 0 below -708.
-__device__ __forceinline__ double exp_neg(double x) {
-    if (x < -708.0) return 0.0;
-    const double k = rint(x * kInvLn2);
-    const double r = (x - k * kLn2Hi) - k * kLn2Lo;
-    double p = c_taylor[13];
+// 2^x in FP32 for -125 <= x <= 0: k = rint(x), f = x - k, 2^f by Horner on
+// its degree-7 Taylor polynomial, times 2^k built exactly.  Relative error
+// below 2^-20 (covered by the bound margins).
+__device__ __forceinline__ float exp2_f32(float x) {
+    const float k = rintf(x);
+    const float f = x - k;
+    float p = c_e2[7];
 #pragma unroll
-    for (int n = 12; n >= 0; --n) p = p * r + c_taylor[n];
-    const long long e = (long long)((int)k + 1023) << 52;
-    return p * __longlong_as_double(e);
+    for (int n = 6; n >= 0; --n) p = p * f + c_e2[n];
+    return p * __int_as_float(((int)k + 127) << 23);
 }
 
 __device__ __forceinline__ double rpow(double r, int p) {
@@ -69,14 +71,16 @@ struct FrontierParams {
     int t, q_depth, r_depth, q_leaf, r_leaf;
     int floor_log2;
     int64_t qn, rn;
-    const double *qlo, *qhi, *qrad;
+    const float *qlo32, *qhi32, *rlo32, *rhi32;
+    const double *qrad;
     const float *qwmin;
-    const double *rlo, *rhi, *rrad, *rW;
-    const double *inv_2h2, *inv_4h2, *inv_h;
+    const double *rrad, *rW;
+    const double *inv_h;
     double *fin, *tok, *est;
-    double *geo;          // per pair cache: K(delta_max), K(delta_min), delta_min^2
+    float *geo;           // per pair cache: K(delta_max) lower, K(delta_min) upper, e^{-dmin^2/4h^2} upper
     double F[17], BT[17], Dpow[34];
     double cw[4];         // cost weights of c_DH, c_DL, c_H2L, c_Direct
+    float c32[64];        // log2(e) / 2h_j^2 rounded to FP32
 };
 
 __device__ __forceinline__ double node_count(int64_t n, int depth, int64_t node) {
@@ -84,23 +88,34 @@ __device__ __forceinline__ double node_count(int64_t n, int depth, int64_t node)
     return (double)(level_begin(n, depth, i + 1) - level_begin(n, depth, i));
 }
 
-struct PairGeom {
-    double dmin2, dmax2;
+struct KBounds {
+    float kmax, kmin, e4;
 };
 
-__device__ __forceinline__ PairGeom pair_geom(const FrontierParams &fp, int64_t q, int64_t r) {
-    PairGeom g;
-    g.dmin2 = 0.0;
-    g.dmax2 = 0.0;
+// Rigorous FP32 bounds of the kernel over a node pair (Section 5's
+// delta_min / delta_max from the bounding boxes, which are stored rounded
+// outward): squared distances, exponent arguments and exponentials carry
+// relative margins of 2^-18, 2^-20 and 2^-18, each larger than the rounding
+// they cover.
+__device__ __forceinline__ KBounds kernel_bounds(const FrontierParams &fp, int64_t q, int64_t r, float c32) {
+    float gsum = 0.f, fsum = 0.f;
     for (int d = 0; d < fp.D; ++d) {
-        const double ql = fp.qlo[q * fp.D + d], qh = fp.qhi[q * fp.D + d];
-        const double rl = fp.rlo[r * fp.D + d], rh = fp.rhi[r * fp.D + d];
-        const double gap = fmax(0.0, fmax(rl - qh, ql - rh));
-        const double far = fmax(qh - rl, rh - ql);
-        g.dmin2 = g.dmin2 + gap * gap;
-        g.dmax2 = g.dmax2 + far * far;
+        const float ql = fp.qlo32[q * fp.D + d], qh = fp.qhi32[q * fp.D + d];
+        const float rl = fp.rlo32[r * fp.D + d], rh = fp.rhi32[r * fp.D + d];
+        const float g = fmaxf(0.f, fmaxf(rl - qh, ql - rh));
+        const float f = fmaxf(qh - rl, rh - ql);
+        gsum = gsum + g * g;
+        fsum = fsum + f * f;
     }
-    return g;
+    const float dmin2 = gsum * F32_LO18, dmax2 = fsum * F32_HI18;
+    const float amax = (dmax2 * c32) * F32_HI20;
+    const float amin = (dmin2 * c32) * F32_LO20;
+    const float a4 = amin * 0.5f;
+    KBounds b;
+    b.kmax = amax > F32_AMAX ? 0.f : exp2_f32(-amax) * F32_LO18;
+    b.kmin = amin > F32_AMAX ? F32_TINY : exp2_f32(-amin) * F32_HI18;
+    b.e4 = a4 > F32_AMAX ? F32_TINY : exp2_f32(-a4) * F32_HI18;
+    return b;
 }
 
 // ---------------------------------------------------------------------------
@@ -119,20 +134,19 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const Group G = groups[g];
         const int64_t q = G.q;
         const int j = G.j;
-        const double inv2 = fp.inv_2h2[j], inv4 = fp.inv_4h2[j], invh = fp.inv_h[j];
-        // pass 1: bounding-box distances, kernel bounds, lower bound over the group
+        const double invh = fp.inv_h[j];
+        const float c32 = fp.c32[j];
+        // pass 1: kernel bounds of every pair, lower bound over the group
         double s_dl = 0.0, s_W = 0.0;
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
-            const PairGeom pg = pair_geom(fp, q, r);
-            const double kmax = exp_neg(-(pg.dmax2 * inv2));
-            const double kmin = exp_neg(-(pg.dmin2 * inv2));
-            double *gc = fp.geo + 3 * (G.off + k);
-            gc[0] = kmax;
-            gc[1] = kmin;
-            gc[2] = pg.dmin2;
+            const KBounds kb = kernel_bounds(fp, q, r, c32);
+            float *gc = fp.geo + 3 * (G.off + k);
+            gc[0] = kb.kmax;
+            gc[1] = kb.kmin;
+            gc[2] = kb.e4;
             const double WR = fp.rW[r];
-            s_dl = s_dl + WR * kmax;
+            s_dl = s_dl + WR * (double)kb.kmax;
             s_W = s_W + WR;
         }
         const double front = warp_sum(s_dl), Wg = warp_sum(s_W);
@@ -148,8 +162,9 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         int n_m[6] = {0, 0, 0, 0, 0, 0};
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
-            const double *gc = fp.geo + 3 * (G.off + k);
-            const double kmax = gc[0], kmin = gc[1], dmin2 = gc[2];
+            const float *gc = fp.geo + 3 * (G.off + k);
+            const double kmax = (double)gc[0], kmin = (double)gc[1];
+            const float e4f = gc[2];
             const double WR = fp.rW[r];
             const double dl = WR * kmax;
             const double allot = fp.tokens ? (tok0 * WR) / Wg : 0.0;
@@ -176,7 +191,7 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                 const double c_ex = (((double)fp.D * cq) * cr) * fp.cw[3];
                 double best_c = INFINITY, best_need = 0.0;
                 int best_m = -1, best_p = 0;
-                double e4 = -1.0, base = 0.0;
+                const double base = WR * (double)e4f;
                 const double rR = fp.rrad[r] * invh;
                 const double x2 = kSqrt2 * rQ;
                 const double sr = kSqrt2 * rR;
@@ -190,10 +205,6 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                         else
                             c = fp.Dpow[2 * p + 1] * fp.cw[2];
                         if (c >= best_c || c > c_ex) break;
-                        if (e4 < 0.0) {
-                            e4 = exp_neg(-(dmin2 * inv4));
-                            base = WR * e4;
-                        }
                         double Ep;
                         if (m == M_DH) {
                             Ep = (base * fp.F[p]) * rpow(rR, p);
@@ -491,20 +502,22 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
-static bool g_taylor_ready[64] = {false};
+static bool g_consts_ready[64] = {false};
 
-static int ensure_taylor() {
+// exp2 coefficients ln2^n / n! built in FP64 by repeated multiplication,
+// then rounded to FP32; uploaded once per device
+static int ensure_consts() {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && g_taylor_ready[dev]) return GS_OK;
-    double c[14];
-    double f = 1.0;
-    for (int n = 0; n < 14; ++n) {
-        if (n > 1) f = f * (double)n;
-        c[n] = 1.0 / f;
+    if (dev >= 0 && dev < 64 && g_consts_ready[dev]) return GS_OK;
+    float c[8];
+    double t = 1.0;
+    for (int n = 0; n < 8; ++n) {
+        c[n] = (float)t;
+        t = (t * 0.6931471805599453) / (double)(n + 1);
     }
-    GS_CUDA_TRY(cudaMemcpyToSymbol(c_taylor, c, sizeof(c)));
-    if (dev >= 0 && dev < 64) g_taylor_ready[dev] = true;
+    GS_CUDA_TRY(cudaMemcpyToSymbol(c_e2, c, sizeof(c)));
+    if (dev >= 0 && dev < 64) g_consts_ready[dev] = true;
     return GS_OK;
 }
 
@@ -540,7 +553,7 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     cudaStream_t st = cx.st;
     int rc = cx.check("before frontier");
     if (rc) return rc;
-    rc = ensure_taylor();
+    rc = ensure_consts();
     if (rc) return rc;
     FrontierParams fp;
     memset(&fp, 0, sizeof(fp));
@@ -553,9 +566,10 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.floor_log2 = in.floor_log2;
     fp.qn = in.qt->n;
     fp.rn = in.rt->n;
-    fp.qlo = in.qt->lo; fp.qhi = in.qt->hi; fp.qrad = in.qt->rad; fp.qwmin = in.qt->wmin;
-    fp.rlo = in.rt->lo; fp.rhi = in.rt->hi; fp.rrad = in.rt->rad; fp.rW = in.rt->W;
-    fp.inv_2h2 = fb.inv_2h2; fp.inv_4h2 = fb.inv_4h2; fp.inv_h = fb.inv_h;
+    fp.qlo32 = in.qt->lo32; fp.qhi32 = in.qt->hi32; fp.qrad = in.qt->rad; fp.qwmin = in.qt->wmin;
+    fp.rlo32 = in.rt->lo32; fp.rhi32 = in.rt->hi32; fp.rrad = in.rt->rad; fp.rW = in.rt->W;
+    fp.inv_h = fb.inv_h;
+    for (int j = 0; j < in.nh; ++j) fp.c32[j] = (float)(1.4426950408889634 / ((2.0 * in.h[j]) * in.h[j]));
     fp.fin = fb.fin; fp.tok = fb.tok; fp.est = fb.est;
     for (int k = 0; k < 4; ++k) fp.cw[k] = in.cost_w[k];
     const int D = in.D;

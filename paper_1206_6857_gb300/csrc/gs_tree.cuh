@@ -18,6 +18,7 @@ struct TreeDev {
     int32_t *perm = nullptr;  // sorted position -> original index
     void *xs = nullptr;       // n x D permuted coordinates (source dtype)
     double *lo = nullptr, *hi = nullptr, *center = nullptr;   // nodes x D
+    float *lo32 = nullptr, *hi32 = nullptr;  // boxes rounded outward to FP32
     double *rad = nullptr;    // half the widest extent
     double *W = nullptr;      // weight sums
     float *wmin = nullptr;    // smallest weight (monochromatic lower bound)

@@ -16,16 +16,36 @@ from oracle import exhaustive as oracle_ex
 from workloads import synth
 
 
-def test_exp_neg_accuracy_and_cutoff():
-    mp = pytest.importorskip("mpmath")
-    mp.mp.dps = 40
-    xs = np.concatenate([-np.linspace(0, 708, 5001), np.random.default_rng(1).uniform(-708, 0, 500)])
-    got = T.exp_neg(xs)
-    for x, g in zip(xs[::7], got[::7]):
-        want = mp.e ** mp.mpf(float(x))
-        assert abs(g - float(want)) <= 2.5e-16 * float(want)
-    assert np.all(T.exp_neg(np.array([-708.5, -1e300])) == 0.0)
-    assert T.exp_neg(np.array([0.0]))[0] == 1.0
+def test_exp2_f32_error_below_margin():
+    """The FP32 exp2 used for the kernel bounds stays within 2^-20 relative
+    error of 2^x over its whole domain [-125, 0]."""
+    x = np.concatenate([-np.linspace(0, 125, 400001), np.random.default_rng(1).uniform(-125, 0, 100000)])
+    x32 = x.astype(np.float32)
+    got = T.exp2_f32(x32).astype(np.float64)
+    want = np.exp2(x32.astype(np.float64))
+    assert np.max(np.abs(got - want) / want) < 2.0 ** -20
+
+
+def test_kernel_bounds_bracket_exact_values():
+    """K(delta_max) lower and K(delta_min) / e^{-delta_min^2/4h^2} upper
+    bounds hold against the FP64 box distances for every random pair."""
+    import math
+    from oracle import series as S
+    rng = np.random.default_rng(5)
+    for D in (1, 2, 3, 7):
+        x = rng.uniform(0, 1, (600, D)).astype(np.float32)
+        w = np.ones(600, np.float32)
+        t = T.build_tree(x, w, 8)
+        pq = rng.integers(0, t.nodes, 3000)
+        pr = rng.integers(0, t.nodes, 3000)
+        for h in (1e-3, 0.02, 0.3, 5.0):
+            c32 = np.full(pq.size, np.float32(1.4426950408889634 / ((2.0 * h) * h)))
+            kmax, kmin, e4 = T.kernel_bounds(t, t, pq, pr, c32)
+            for i in range(0, 3000, 7):
+                dmin, dmax = S.box_distances(t.lo[pq[i]], t.hi[pq[i]], t.lo[pr[i]], t.hi[pr[i]])
+                assert kmax[i] <= math.exp(-dmax * dmax / (2 * h * h))
+                assert kmin[i] >= math.exp(-dmin * dmin / (2 * h * h))
+                assert e4[i] >= math.exp(-dmin * dmin / (4 * h * h))
 
 
 def test_group_reduce_matches_exact_sums():
