@@ -69,13 +69,17 @@ typedef struct gs_opts {
     int32_t floor_log2;     /* relative floor: results are certified to
                                |G~ - G| <= eps * max(G, 2^floor_log2 * W), W = sum w;
                                0 -> -40                                                 */
-    int32_t reserved0;
+    int32_t flags;          /* GS_FLAG_* bits                                            */
     int64_t pair_capacity;  /* initial work-list capacity in pairs; 0 -> automatic     */
     double  cost_weight[4]; /* multipliers of the Fig. 6 costs c_DH, c_DL, c_H2L and
                                c_Direct; all 0 -> GS_COST_* defaults below (calibrated
                                to GB300 unit costs); all 1 -> the paper's cost model   */
     int64_t reserved[4];
 } gs_opts;
+
+/* gs_opts.flags */
+#define GS_FLAG_NO_MERGE 1  /* base case per bandwidth, without merging the leaf pairs
+                               that several bandwidths share                           */
 
 /* Default cost weights: a series action runs in FP64 on the GPU while a
  * direct (base-case) term is an FP32 exponential, so on GB300 one unit of

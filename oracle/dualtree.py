@@ -355,10 +355,14 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
             G = np.maximum(G, qt.wmin[gq])
         G = np.maximum(G, floorW)
         Gp = G[gid]
-        allot = (tok[gq, gj][gid] * WR) / Wg[gid] if tokens else np.zeros(pq.size)
+        # per group: token per unit weight and the Theorem 2 scale W / (eps G)
+        share = tok[gq, gj] / Wg
+        kappa = W / (eps_t * G)
+        allot = WR * share[gid] if tokens else np.zeros(pq.size)
+        kap = kappa[gid]
 
         def need(E):
-            return (W * E) / (eps_t * Gp) - WR
+            return E * kap - WR
 
         e_fd = (WR * (kmin - kmax)) * 0.5
         est_fd = (WR * (kmin + kmax)) * 0.5

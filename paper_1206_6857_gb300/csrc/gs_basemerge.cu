@@ -1,0 +1,348 @@
+// Leaf-leaf base case with the bandwidths of one leaf pair merged.
+//
+// The traversal emits its base cases per bandwidth: (query leaf Q, h_j, list
+// of reference leaves).  A bandwidth sweep leaves the same leaf pair
+// unpruned for several neighbouring bandwidths, and every one of them needs
+// the same squared distances.  This pass folds the per-bandwidth lists into
+// one list of (Q, R, bandwidth mask) entries per query leaf:
+//   mark    -- atomicOr of bit j into a dense lq x lr mask array;
+//   count   -- nonzero masks per query-leaf row;
+//   scan    -- row offsets;
+//   compact -- (R, mask) entries per row in ascending R.
+// The base-case kernel then forms each squared distance once per (query,
+// reference) and evaluates one exponential per bandwidth in the mask
+// (Section 1's sum term, DITOBase of Fig. 7).  Sums: FP32 over the terms of
+// one reference leaf, then compensated (Kahan) FP32 per (bandwidth, query)
+// across leaves, then FP64 across warps.
+#include <math.h>
+
+#include "gs_device.cuh"
+#include "gs_frontier.cuh"
+#include "gs_internal.h"
+#include "gs_tree.cuh"
+
+namespace gs {
+
+struct MergedEntry {
+    int32_t r;       // reference leaf (heap number)
+    uint32_t mask;   // bandwidths j with bit j set
+};
+
+__global__ void k_mark_masks(const Group *__restrict__ bgroups, int64_t nbg, const int32_t *__restrict__ base_r,
+                             int64_t qleaf0, int64_t rleaf0, int64_t lr, uint32_t *mask) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < nbg; g += warps) {
+        const Group G = bgroups[g];
+        uint32_t *row = mask + (G.q - qleaf0) * lr;
+        const uint32_t bit = 1u << G.j;
+        for (int k = lane; k < G.cnt; k += 32) atomicOr(&row[base_r[G.off + k] - rleaf0], bit);
+    }
+}
+
+__global__ void k_row_count(const uint32_t *__restrict__ mask, int64_t lq, int64_t lr, long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < lq; i += warps) {
+        const uint32_t *row = mask + i * lr;
+        int c = 0;
+        for (int64_t k = lane; k < lr; k += 32) c += row[k] != 0u;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) cnt[i] = c;
+    }
+}
+
+// single-block exclusive scan of n int64 values in place; total in *tot
+__global__ void __launch_bounds__(1024) k_scan_i64(long long *v, int64_t n, long long *tot) {
+    __shared__ long long ws[32];
+    __shared__ long long carry_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < n; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        const long long x = i < n ? v[i] : 0;
+        long long inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) ws[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            long long s = ws[lane], si = s;
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u = __shfl_up_sync(0xffffffffu, si, o);
+                if (lane >= o) si += u;
+            }
+            ws[lane] = si - s;
+        }
+        __syncthreads();
+        const long long carry = carry_s;
+        if (i < n) v[i] = carry + ws[w] + inc - x;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry_s = carry + ws[w] + inc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *tot = carry_s;
+}
+
+__global__ void k_row_compact(const uint32_t *__restrict__ mask, int64_t lq, int64_t lr, int64_t rleaf0,
+                              const long long *__restrict__ off, MergedEntry *ent) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < lq; i += warps) {
+        const uint32_t *row = mask + i * lr;
+        int64_t o = off[i];
+        for (int64_t k0 = 0; k0 < lr; k0 += 32) {
+            const int64_t k = k0 + lane;
+            const uint32_t m = k < lr ? row[k] : 0u;
+            const unsigned b = __ballot_sync(0xffffffffu, m != 0u);
+            if (m) {
+                MergedEntry e;
+                e.r = (int32_t)(rleaf0 + k);
+                e.mask = m;
+                ent[o + __popc(b & lt)] = e;
+            }
+            o += __popc(b);
+        }
+    }
+}
+
+constexpr int kMW = 4;   // warps per CTA
+
+struct MergedParams {
+    const float *qrec, *rrec;
+    int64_t qn, rn;
+    int q_depth, r_depth;
+    const double *qcenter, *rcenter;
+    int D, nh;
+    float negc[32];
+    double *Gq;
+    const Ingest *ing;
+    unsigned long long *evals;
+};
+
+// Sum over one reference leaf for NJ bandwidths at once: one squared
+// distance per (query, reference), NJ exponentials.
+template <int DP, int QPL, bool ANCH, int NJ>
+__device__ __forceinline__ void leaf_terms(const MergedParams &bp, const float (&xq)[QPL][DP], const float (&dc)[DP],
+                                           const float4 *rp, int nr, const float (&c)[8], float (&part)[QPL][8]) {
+    constexpr int NT = RefRec<float, DP>::NT;
+#pragma unroll
+    for (int s = 0; s < QPL; ++s)
+#pragma unroll
+        for (int k = 0; k < NJ; ++k) part[s][k] = 0.f;
+#pragma unroll 2
+    for (int i = 0; i < nr; ++i) {
+        float rv[NT];
+#pragma unroll
+        for (int v = 0; v < NT / 4; ++v) {
+            const float4 f = __ldg(rp + i * (NT / 4) + v);
+            rv[4 * v] = f.x; rv[4 * v + 1] = f.y; rv[4 * v + 2] = f.z; rv[4 * v + 3] = f.w;
+        }
+        const float l = rv[DP];
+#pragma unroll
+        for (int s = 0; s < QPL; ++s) {
+            float d2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                const float df = ANCH ? (xq[s][d] - rv[d]) + dc[d] : xq[s][d] - rv[d];
+                d2 = fmaf(df, df, d2);
+            }
+#pragma unroll
+            for (int k = 0; k < NJ; ++k) part[s][k] += ex2_approx(fmaf(d2, c[k], l));
+        }
+    }
+}
+
+template <int DP, int QPL, bool ANCH>
+__global__ void __launch_bounds__(32 * kMW)
+k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const long long *__restrict__ off,
+                  int64_t lq) {
+    constexpr int NT = RefRec<float, DP>::NT;
+    extern __shared__ float sm_f[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = blockIdx.x;
+    const int64_t e0 = off[i], e1 = off[i + 1];
+    if (e0 == e1) return;
+    const int nh = bp.nh;
+    // per warp: Kahan sum and compensation per (bandwidth, query slot)
+    float *ksum = sm_f + (size_t)w * 2 * nh * QPL * 32;
+    float *kcmp = ksum + nh * QPL * 32;
+    for (int t = lane; t < 2 * nh * QPL * 32; t += 32) ksum[t] = 0.f;
+    __syncwarp();
+    const int64_t qleaf0 = (1ll << bp.q_depth) - 1, rleaf0 = (1ll << bp.r_depth) - 1;
+    const int64_t qnode = qleaf0 + i;
+    const int64_t qb = level_begin(bp.qn, bp.q_depth, i), qe = level_begin(bp.qn, bp.q_depth, i + 1);
+    const int nq = (int)(qe - qb);
+    float xq[QPL][DP];
+#pragma unroll
+    for (int s = 0; s < QPL; ++s) {
+        const int qq = lane + 32 * s;
+        const int64_t pos = qb + (qq < nq ? qq : 0);
+#pragma unroll
+        for (int d = 0; d < DP; ++d) xq[s][d] = bp.qrec[pos * NT + d];
+    }
+    unsigned long long evals = 0;
+    for (int64_t e = e0 + w; e < e1; e += kMW) {
+        const MergedEntry E = ent[e];
+        const int64_t ri = E.r - rleaf0;
+        const int64_t rb = level_begin(bp.rn, bp.r_depth, ri), re = level_begin(bp.rn, bp.r_depth, ri + 1);
+        const int nr = (int)(re - rb);
+        float dc[DP];
+#pragma unroll
+        for (int d = 0; d < DP; ++d) dc[d] = 0.f;
+        if (ANCH) {
+            for (int d = 0; d < bp.D; ++d) dc[d] = (float)(bp.qcenter[qnode * bp.D + d] - bp.rcenter[(int64_t)E.r * bp.D + d]);
+        }
+        const float4 *rp = reinterpret_cast<const float4 *>(bp.rrec + rb * NT);
+        uint32_t m = E.mask;
+        evals += (unsigned long long)__popc(m) * (unsigned long long)nr;
+        while (m) {
+            int js[8];
+            float c[8];
+            int nj = 0;
+            while (m && nj < 4) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                js[nj] = j;
+                c[nj] = bp.negc[j];
+                ++nj;
+            }
+            float part[QPL][8];
+            switch (nj) {
+                case 1: leaf_terms<DP, QPL, ANCH, 1>(bp, xq, dc, rp, nr, c, part); break;
+                case 2: leaf_terms<DP, QPL, ANCH, 2>(bp, xq, dc, rp, nr, c, part); break;
+                case 3: leaf_terms<DP, QPL, ANCH, 3>(bp, xq, dc, rp, nr, c, part); break;
+                default: leaf_terms<DP, QPL, ANCH, 4>(bp, xq, dc, rp, nr, c, part); break;
+            }
+            for (int k = 0; k < nj; ++k) {
+#pragma unroll
+                for (int s = 0; s < QPL; ++s) {
+                    const int slot = (js[k] * QPL + s) * 32 + lane;
+                    const float y = part[s][k] - kcmp[slot];
+                    const float t = ksum[slot] + y;
+                    kcmp[slot] = (t - ksum[slot]) - y;
+                    ksum[slot] = t;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const double wmax = (double)__uint_as_float(bp.ing->wmax_bits);
+    for (int t = threadIdx.x; t < nh * QPL * 32; t += blockDim.x) {
+        const int j = t / (QPL * 32), s = (t / 32) % QPL, ln = t % 32;
+        const int qq = ln + 32 * s;
+        if (qq >= nq) continue;
+        double v = 0.0;
+        for (int k = 0; k < kMW; ++k) {
+            const float *ks = sm_f + (size_t)k * 2 * nh * QPL * 32;
+            v += (double)ks[t] - (double)ks[nh * QPL * 32 + t];
+        }
+        if (v != 0.0) atomicAdd(&bp.Gq[(qb + qq) * nh + j], v * wmax);
+    }
+    if (bp.evals && lane == 0 && evals) atomicAdd(bp.evals, evals * (unsigned long long)nq);
+}
+
+template <int DP>
+static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const MergedEntry *ent, const long long *off,
+                            int64_t lq, cudaStream_t st) {
+    const size_t sm = (size_t)kMW * 2 * bp.nh * qpl * 32 * sizeof(float);
+#define GS_M(Q, A)                                                                                  \
+    do {                                                                                            \
+        cudaFuncSetAttribute(k_basecase_merged<DP, Q, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)sm);                                                              \
+        k_basecase_merged<DP, Q, A><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq);          \
+    } while (0)
+    if (anch) {
+        if (qpl <= 1) GS_M(1, true); else if (qpl <= 2) GS_M(2, true); else GS_M(4, true);
+    } else {
+        if (qpl <= 1) GS_M(1, false); else if (qpl <= 2) GS_M(2, false); else GS_M(4, false);
+    }
+#undef GS_M
+    return GS_OK;
+}
+
+bool merged_base_possible(const TraversalIn &in) {
+    const int64_t lq = 1ll << in.qt->depth, lr = 1ll << in.rt->depth;
+    return in.nh <= 32 && lq * lr <= (3ll << 30);   // mask array at most 12 GB
+}
+
+int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, CallCtx &cx) {
+    cudaStream_t st = cx.st;
+    const int64_t lq = 1ll << in.qt->depth, lr = 1ll << in.rt->depth;
+    const int64_t qleaf0 = lq - 1, rleaf0 = lr - 1;
+    cx.phase(GS_PH_BASE);
+    if (fb.n_base_groups == 0) {
+        cx.phase(GS_PH_OTHER);
+        return GS_OK;
+    }
+    uint32_t *mask = nullptr;
+    long long *off = nullptr;
+    MergedEntry *ent = nullptr;
+    GS_CUDA_TRY(cudaMallocAsync((void **)&mask, (size_t)lq * lr * sizeof(uint32_t), st));
+    GS_CUDA_TRY(cudaMemsetAsync(mask, 0, (size_t)lq * lr * sizeof(uint32_t), st));
+    GS_CUDA_TRY(cudaMallocAsync((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
+    const int grid = fb.grid_warps / 8;
+    k_mark_masks<<<grid, 256, 0, st>>>(fb.base_groups, fb.n_base_groups, fb.base_r, qleaf0, rleaf0, lr, mask);
+    k_row_count<<<grid, 256, 0, st>>>(mask, lq, lr, off);
+    k_scan_i64<<<1, 1024, 0, st>>>(off, lq, off + lq);
+    cx.launches += 3;
+    long long total = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
+    GS_CUDA_TRY(cudaStreamSynchronize(st));
+    GS_CUDA_TRY(cudaMallocAsync((void **)&ent, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
+    k_row_compact<<<grid, 256, 0, st>>>(mask, lq, lr, rleaf0, off, ent);
+    cx.launches += 1;
+    cudaFreeAsync(mask, st);
+    int rc = cx.check("merge base pairs");
+    if (!rc) {
+        MergedParams bp;
+        memset(&bp, 0, sizeof(bp));
+        bp.qrec = in.qt->rec;
+        bp.rrec = in.rt->rec;
+        bp.qn = in.qt->n;
+        bp.rn = in.rt->n;
+        bp.q_depth = in.qt->depth;
+        bp.r_depth = in.rt->depth;
+        bp.qcenter = in.qt->center;
+        bp.rcenter = in.rt->center;
+        bp.D = in.D;
+        bp.nh = in.nh;
+        for (int j = 0; j < in.nh; ++j) bp.negc[j] = (float)(-1.4426950408889634 / (2.0 * in.h[j] * in.h[j]));
+        bp.Gq = Gq;
+        bp.ing = in.ing;
+        bp.evals = fb.evals;
+        const int64_t maxq = (in.qt->n + lq - 1) / lq;
+        const int qpl = (int)((maxq + 31) / 32);
+        const bool anch = in.qt->dtype == GS_F64;
+        switch (DP) {
+            case 1: rc = launch_merged_dp<1>(qpl, anch, bp, ent, off, lq, st); break;
+            case 2: rc = launch_merged_dp<2>(qpl, anch, bp, ent, off, lq, st); break;
+            case 3: rc = launch_merged_dp<3>(qpl, anch, bp, ent, off, lq, st); break;
+            case 4: rc = launch_merged_dp<4>(qpl, anch, bp, ent, off, lq, st); break;
+            case 5: rc = launch_merged_dp<5>(qpl, anch, bp, ent, off, lq, st); break;
+            case 6: rc = launch_merged_dp<6>(qpl, anch, bp, ent, off, lq, st); break;
+            case 7: rc = launch_merged_dp<7>(qpl, anch, bp, ent, off, lq, st); break;
+            case 8: rc = launch_merged_dp<8>(qpl, anch, bp, ent, off, lq, st); break;
+            case 12: rc = launch_merged_dp<12>(qpl, anch, bp, ent, off, lq, st); break;
+            case 16: rc = launch_merged_dp<16>(qpl, anch, bp, ent, off, lq, st); break;
+            case 24: rc = launch_merged_dp<24>(qpl, anch, bp, ent, off, lq, st); break;
+            default: rc = launch_merged_dp<32>(qpl, anch, bp, ent, off, lq, st); break;
+        }
+        cx.launches += 1;
+        cx.launches_base += 1;
+        if (!rc) rc = cx.check("k_basecase_merged");
+    }
+    cudaFreeAsync(ent, st);
+    cudaFreeAsync(off, st);
+    cx.phase(GS_PH_OTHER);
+    if (rc) return rc;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "merged base case launch");
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -208,7 +208,8 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
             GS_ALLOC(pL, (size_t)qt.nodes * nh * sizeof(int32_t));
             GS_CUDA_TRY(cudaMemsetAsync(pL, 0, (size_t)qt.nodes * nh * sizeof(int32_t), st));
         }
-        rc = run_basecase(in, fb, Gq, DP, cx);
+        rc = (merged_base_possible(in) && !(o.flags & GS_FLAG_NO_MERGE)) ? run_basecase_merged(in, fb, Gq, DP, cx)
+                                                         : run_basecase(in, fb, Gq, DP, cx);
     }
     if (!rc) rc = run_series_and_final(in, fb, series ? &tb : nullptr, Gq, B, pL, out, cx);
     if (!rc && trace && trace->qperm) {

@@ -157,6 +157,9 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         Gb = fmax(Gb, floorW);
         const double cq = node_count(fp.qn, fp.q_depth, q);
         const double rQ = fp.qrad[q] * invh;
+        // per group: token per unit weight and the Theorem 2 scale W / (eps G)
+        const double share = tok0 / Wg;
+        const double kappa = Wtot / (eps_t * Gb);
         // pass 2: decisions
         double s_left = 0.0, s_fin = 0.0, s_est = 0.0;
         int n_m[6] = {0, 0, 0, 0, 0, 0};
@@ -167,14 +170,14 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             const float e4f = gc[2];
             const double WR = fp.rW[r];
             const double dl = WR * kmax;
-            const double allot = fp.tokens ? (tok0 * WR) / Wg : 0.0;
+            const double allot = fp.tokens ? WR * share : 0.0;
             int method = (fp.q_leaf && fp.r_leaf) ? M_BASE : M_SPLIT;
             int pord = 0;
             double leftover = 0.0;
             bool decided = false;
             if (fp.selector != GS_SEL_EXHAUSTIVE) {
                 const double e_fd = (WR * (kmin - kmax)) * 0.5;
-                const double n_fd = (Wtot * e_fd) / (eps_t * Gb) - WR;
+                const double n_fd = e_fd * kappa - WR;
                 if (n_fd <= allot) {
                     method = M_FD;
                     leftover = allot - n_fd;
@@ -214,7 +217,7 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                             const double tail = (x2 <= 1.0) ? 1.0 : rpow(x2, p - 1);
                             Ep = (base * fp.F[p]) * (rpow(rQ, p) + (rpow(sr, p) * fp.BT[p]) * tail);
                         }
-                        const double np_ = (Wtot * Ep) / (eps_t * Gb) - WR;
+                        const double np_ = Ep * kappa - WR;
                         if (np_ <= allot) {
                             best_c = c;
                             best_m = m;

@@ -34,12 +34,13 @@ GS_SEL_FD_ONLY = 2
 GS_SEL_EXHAUSTIVE = 3
 
 GS_COST_DEFAULT = (32.0, 32.0, 32.0, 1.0)     # c_DH, c_DL, c_H2L, c_Direct weights
+GS_FLAG_NO_MERGE = 1
 
 
 class gs_opts(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int32), ("plimit", ctypes.c_int32),
                 ("selector", ctypes.c_int32), ("no_tokens", ctypes.c_int32),
-                ("floor_log2", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("floor_log2", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("pair_capacity", ctypes.c_int64), ("cost_weight", ctypes.c_double * 4),
                 ("reserved", ctypes.c_int64 * 4)]
 

@@ -123,6 +123,18 @@ def test_config2_scaled_sweep(gs):
     _check_eps(gs, synth.config2(0.02))
 
 
+def test_merged_and_unmerged_base_case_agree(gs):
+    """The bandwidth-merged base case and the per-bandwidth one sum the same
+    leaf pairs: results agree to FP32 summation accuracy."""
+    wl = synth.config2(0.02)
+    tq, tw = _dev(wl.queries), _dev(wl.weights)
+    a = gs.gs_sum(tq, tq, tw, wl.h, wl.eps).cpu().numpy()
+    o = _opts(gs)
+    o.flags = gs.GS_FLAG_NO_MERGE
+    b = gs.gs_sum(tq, tq, tw, wl.h, wl.eps, opts=o).cpu().numpy()
+    assert np.max(np.abs(a - b) / b) <= 1e-5
+
+
 @pytest.mark.parametrize("eps", [1e-3, 1e-4])
 def test_config3_scaled_series_regime(gs, eps):
     _check_eps(gs, synth.config3(0.02, eps=eps), eps=eps)
