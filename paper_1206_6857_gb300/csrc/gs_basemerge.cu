@@ -249,9 +249,10 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
 template <int DP>
 static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const MergedEntry *ent, const long long *off,
                             int64_t lq, cudaStream_t st) {
-    const size_t sm = (size_t)kMW * 2 * bp.nh * qpl * 32 * sizeof(float);
+    // shared memory sized from the instantiated QPL (the kernel indexes with it)
 #define GS_M(Q, A)                                                                                  \
     do {                                                                                            \
+        const size_t sm = (size_t)kMW * 2 * bp.nh * (Q) * 32 * sizeof(float);                      \
         cudaFuncSetAttribute(k_basecase_merged<DP, Q, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)sm);                                                              \
         k_basecase_merged<DP, Q, A><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq);          \
