@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--eps", type=float, default=None, help="override eps (0 = exhaustive)")
     ap.add_argument("--scale", type=float, default=1.0, help="workload size factor (1 = full)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -219,11 +220,21 @@ def run_gs(args):
     stream = torch.cuda.current_stream()
     scores = {}
 
+    # autotuner (setup, not timed): leaf size, PLIMIT and bestMethod cost
+    # weights chosen by timing the library on a seeded 25% subsample
+    tuned, opts = None, None
+    if eps > 0 and not args.no_tune:
+        from paper_1206_6857_gb300 import autotune
+        t0 = time.perf_counter()
+        tuned, _table = autotune.tune(tq, tw, hs, eps, fraction=0.25)
+        tuned["tuning_seconds"] = time.perf_counter() - t0
+        opts = autotune.options(tuned)
+
     def step(stats=None):
         if args.mode == "lscv":
-            scores["lscv"] = gs.gs_lscv(tq, tw, wl.h, eps, stream=stream, stats=stats)
+            scores["lscv"] = gs.gs_lscv(tq, tw, wl.h, eps, opts=opts, stream=stream, stats=stats)
         else:
-            gs.gs_sum(tq, tq, tw, wl.h, eps, out=out, stream=stream, stats=stats)
+            gs.gs_sum(tq, tq, tw, wl.h, eps, out=out, opts=opts, stream=stream, stats=stats)
 
     for _ in range(args.warmup):
         step()
@@ -290,13 +301,13 @@ def run_gs(args):
             def e2e_step():
                 dq = hq.to(dev, non_blocking=True)
                 dw = hw.to(dev, non_blocking=True)
-                return gs.gs_lscv(dq, dw, wl.h, eps, stream=stream)   # returns host arrays
+                return gs.gs_lscv(dq, dw, wl.h, eps, opts=opts, stream=stream)   # returns host arrays
             d2h = 2 * 8 * wl.h.size
         else:
             hout = torch.empty((wl.M, wl.h.size), dtype=torch.float64).pin_memory().numpy()
 
             def e2e_step():
-                gs.gs_sum_host(hq.numpy(), hq.numpy(), hw.numpy(), wl.h, eps, out=hout)
+                gs.gs_sum_host(hq.numpy(), hq.numpy(), hw.numpy(), wl.h, eps, out=hout, opts=opts)
             d2h = int(hout.nbytes)
         e2e_step()
         torch.cuda.synchronize()
@@ -319,10 +330,13 @@ def run_gs(args):
 
     if rank == 0:
         s0 = stats_list[-1]
+        cfg = wl_config(wl, args.mode, eps)
+        if tuned is not None:
+            cfg["tuned"] = tuned
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": wl_config(wl, args.mode, eps), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches * args.steps,
                 "stats": {k: v for k, v in s0.as_dict().items()}}
         if "lscv" in scores:

@@ -52,41 +52,6 @@ __global__ void k_row_count(const uint32_t *__restrict__ mask, int64_t lq, int64
     }
 }
 
-// single-block exclusive scan of n int64 values in place; total in *tot
-__global__ void __launch_bounds__(1024) k_scan_i64(long long *v, int64_t n, long long *tot) {
-    __shared__ long long ws[32];
-    __shared__ long long carry_s;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    for (int64_t b0 = 0; b0 < n; b0 += blockDim.x) {
-        const int64_t i = b0 + threadIdx.x;
-        const long long x = i < n ? v[i] : 0;
-        long long inc = x;
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long u = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += u;
-        }
-        if (lane == 31) ws[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            long long s = ws[lane], si = s;
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long u = __shfl_up_sync(0xffffffffu, si, o);
-                if (lane >= o) si += u;
-            }
-            ws[lane] = si - s;
-        }
-        __syncthreads();
-        const long long carry = carry_s;
-        if (i < n) v[i] = carry + ws[w] + inc - x;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry_s = carry + ws[w] + inc;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *tot = carry_s;
-}
-
 __global__ void k_row_compact(const uint32_t *__restrict__ mask, int64_t lq, int64_t lr, int64_t rleaf0,
                               const long long *__restrict__ off, MergedEntry *ent) {
     const int lane = threadIdx.x & 31;
@@ -289,8 +254,12 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     const int grid = fb.grid_warps / 8;
     k_mark_masks<<<grid, 256, 0, st>>>(fb.base_groups, fb.n_base_groups, fb.base_r, qleaf0, rleaf0, lr, mask);
     k_row_count<<<grid, 256, 0, st>>>(mask, lq, lr, off);
-    k_scan_i64<<<1, 1024, 0, st>>>(off, lq, off + lq);
-    cx.launches += 3;
+    cx.launches += 2;
+    if (int rc0 = scan_i64(off, lq, off + lq, cx)) {
+        cudaFreeAsync(mask, st);
+        cudaFreeAsync(off, st);
+        return rc0;
+    }
     long long total = 0;
     GS_CUDA_TRY(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
     GS_CUDA_TRY(cudaStreamSynchronize(st));

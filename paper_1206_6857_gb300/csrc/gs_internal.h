@@ -145,6 +145,8 @@ void free_series_tables(SeriesTables *tb, cudaStream_t st);
 int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx);
 int run_basecase(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, CallCtx &cx);
 bool merged_base_possible(const TraversalIn &in);
+// In-place exclusive prefix sum of n int64 values; *total (device) receives the sum.
+int scan_i64(long long *v, int64_t n, long long *total, CallCtx &cx);
 int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, CallCtx &cx);
 int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTables *tb, double *Gq,
                          double *B, int32_t *pL, double *out, CallCtx &cx);

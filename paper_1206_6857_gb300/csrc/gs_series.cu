@@ -73,11 +73,39 @@ __device__ __forceinline__ void load_tables(const SeriesTables &tb, int D, uint8
 
 __host__ __device__ inline int table_bytes(int T, int D) { return ((T * D + 7) / 8 + (T + 7) / 8) * 8; }
 
+// Work chunks: a DH action over a large query node or a DL action over a
+// large reference node is split into pieces of kChunk points; piece counts
+// are prefix-summed and warps take pieces from the flattened list.
+constexpr int kChunk = 64;
+
+__global__ void k_chunk_count(const SeriesEntry *__restrict__ ent, int64_t ne, int use_q, int64_t nq, int64_t nr,
+                              long long *cnt) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t node = use_q ? ent[e].q : ent[e].r;
+        const int dd = node_depth(node);
+        const int64_t ii = node - ((1ll << dd) - 1);
+        const int64_t n = use_q ? nq : nr;
+        const int64_t c = level_begin(n, dd, ii + 1) - level_begin(n, dd, ii);
+        cnt[e] = (c + kChunk - 1) / kChunk;
+    }
+}
+
+// entry owning flattened piece c (off = exclusive prefix of piece counts)
+__device__ __forceinline__ int64_t owner(const long long *off, int64_t ne, long long c) {
+    int64_t lo = 0, hi = ne - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
-// DH: one warp per action, lanes over the queries of Q; per-lane Hermite
-// polynomial tables in shared memory (lane-minor, conflict-free)
+// DH: one warp per piece of kChunk queries; lanes over queries; per-lane
+// Hermite polynomial tables in shared memory (lane-minor, conflict-free)
 // ---------------------------------------------------------------------------
-__global__ void k_series_dh(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+__global__ void k_series_dh(SeriesParams sp, const SeriesEntry *__restrict__ ent, int64_t ne,
+                            const long long *__restrict__ off, const long long *__restrict__ npieces) {
     extern __shared__ double smem_d[];
     const int D = sp.D, T = sp.T, P = sp.P;
     uint8_t *al_s = (uint8_t *)smem_d;
@@ -86,9 +114,10 @@ __global__ void k_series_dh(SeriesParams sp, const FrontierState *__restrict__ f
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double *A = smem_d + table_bytes(T, D) / 8 + (size_t)w * (T + D * P * 32);
     double *Hs = A + T;
-    const int64_t ne = fs->series_count[0];
+    const long long C = *npieces;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; e < ne; e += warps) {
+    for (long long c = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; c < C; c += warps) {
+        const int64_t e = owner(off, ne, c);
         const SeriesEntry E = ent[e];
         const int p = E.p, Tp = sp.tb.Tp[p];
         const double is = sp.inv_s[E.j];
@@ -103,7 +132,8 @@ __global__ void k_series_dh(SeriesParams sp, const FrontierState *__restrict__ f
         const double *cR = sp.rcenter + (int64_t)E.r * D;
         const int qd = node_depth(E.q);
         const int64_t qi = E.q - ((1ll << qd) - 1);
-        const int64_t b = level_begin(sp.qn, qd, qi), en = level_begin(sp.qn, qd, qi + 1);
+        const int64_t b = level_begin(sp.qn, qd, qi) + (c - off[e]) * kChunk;
+        const int64_t en = min(b + kChunk, level_begin(sp.qn, qd, qi + 1));
         for (int64_t pos = b + lane; pos < en; pos += 32) {
             double t2 = 0.0;
             for (int d = 0; d < D; ++d) {
@@ -132,11 +162,12 @@ __global__ void k_series_dh(SeriesParams sp, const FrontierState *__restrict__ f
 }
 
 // ---------------------------------------------------------------------------
-// DL: one warp per action, lanes over the coefficients b; references of R
-// in chunks of 32 whose Hermite tables are built cooperatively in shared
-// memory
+// DL: one warp per piece of kChunk references, lanes over the coefficients b;
+// the piece's references in groups of 32 have their Hermite tables built
+// cooperatively in shared memory; partial coefficients are added atomically
 // ---------------------------------------------------------------------------
-__global__ void k_series_dl(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+__global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent, int64_t ne,
+                            const long long *__restrict__ off, const long long *__restrict__ npieces) {
     extern __shared__ double smem_d[];
     const int D = sp.D, T = sp.T, P = sp.P;
     uint8_t *al_s = (uint8_t *)smem_d;
@@ -146,16 +177,18 @@ __global__ void k_series_dl(SeriesParams sp, const FrontierState *__restrict__ f
     const int DPp = D * P;
     double *Hr = smem_d + table_bytes(T, D) / 8 + (size_t)w * (32 * DPp + 32);
     double *we = Hr + 32 * DPp;
-    const int64_t ne = fs->series_count[1];
+    const long long C = *npieces;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; e < ne; e += warps) {
+    for (long long c = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; c < C; c += warps) {
+        const int64_t e = owner(off, ne, c);
         const SeriesEntry E = ent[e];
         const int p = E.p, Tp = sp.tb.Tp[p];
         const double is = sp.inv_s[E.j];
         const double *cQ = sp.qcenter + (int64_t)E.q * D;
         const int rd = node_depth(E.r);
         const int64_t ri = E.r - ((1ll << rd) - 1);
-        const int64_t rb = level_begin(sp.rn, rd, ri), re = level_begin(sp.rn, rd, ri + 1);
+        const int64_t rb = level_begin(sp.rn, rd, ri) + (c - off[e]) * kChunk;
+        const int64_t re = min(rb + kChunk, level_begin(sp.rn, rd, ri + 1));
         double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * T;
         for (int b0 = 0; b0 < Tp; b0 += 32) {
             const int bt = b0 + lane;
@@ -379,6 +412,17 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         cx.phase(GS_PH_SERIES);
         int rc;
         const int tbytes = table_bytes(sp.T, sp.D);
+        // pieces of the DH (queries) and DL (references) actions
+        long long *pieces[2] = {nullptr, nullptr};
+        for (int m = 0; m < 2; ++m) {
+            const int64_t ne = fb.n_series[m];
+            if (ne == 0) continue;
+            GS_CUDA_TRY(cudaMallocAsync((void **)&pieces[m], (size_t)(ne + 1) * sizeof(long long), st));
+            k_chunk_count<<<(unsigned)((ne + 255) / 256 < 4096 ? (ne + 255) / 256 : 4096), 256, 0, st>>>(
+                fb.series[m], ne, m == 0, sp.qn, sp.rn, pieces[m]);
+            cx.launches += 1;
+            if ((rc = scan_i64(pieces[m], ne, pieces[m] + ne, cx))) return rc;
+        }
         auto launch = [&](int which, int64_t n, size_t per_warp) -> int {
             if (n <= 0) return GS_OK;
             int wpb = 8;
@@ -388,24 +432,28 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
                 set_error("series order too high for shared memory (D=%d, P=%d)", sp.D, sp.P);
                 return GS_ERR_ARG;
             }
-            int64_t g = (n + wpb - 1) / wpb;
-            const int64_t mx = fb.grid_warps / wpb;
-            const unsigned grid = (unsigned)(g < 1 ? 1 : (g > mx ? mx : g));
+            const unsigned grid = (unsigned)(fb.grid_warps / wpb);
             const void *fn = which == 0 ? (const void *)k_series_dh
                            : which == 1 ? (const void *)k_series_dl : (const void *)k_series_h2l;
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (which == 0)
-                k_series_dh<<<grid, wpb * 32, sm, st>>>(sp, fb.fs, fb.series[0]);
+                k_series_dh<<<grid, wpb * 32, sm, st>>>(sp, fb.series[0], n, pieces[0], pieces[0] + n);
             else if (which == 1)
-                k_series_dl<<<grid, wpb * 32, sm, st>>>(sp, fb.fs, fb.series[1]);
-            else
-                k_series_h2l<<<grid, wpb * 32, sm, st>>>(sp, fb.fs, fb.series[2]);
+                k_series_dl<<<grid, wpb * 32, sm, st>>>(sp, fb.series[1], n, pieces[1], pieces[1] + n);
+            else {
+                int64_t g = (n + wpb - 1) / wpb;
+                const int64_t mx = fb.grid_warps / wpb;
+                k_series_h2l<<<(unsigned)(g < 1 ? 1 : (g > mx ? mx : g)), wpb * 32, sm, st>>>(sp, fb.fs, fb.series[2]);
+            }
             cx.launches += 1;
             return cx.check(which == 0 ? "k_series_dh" : which == 1 ? "k_series_dl" : "k_series_h2l");
         };
-        if ((rc = launch(0, fb.n_series[0], 8 * (size_t)(sp.T + sp.D * sp.P * 32)))) return rc;
-        if ((rc = launch(1, fb.n_series[1], 8 * (size_t)(32 * sp.D * sp.P + 32)))) return rc;
-        if ((rc = launch(2, fb.n_series[2], 8 * (size_t)(sp.T + sp.D * (2 * sp.P - 1))))) return rc;
+        rc = launch(0, fb.n_series[0], 8 * (size_t)(sp.T + sp.D * sp.P * 32));
+        if (!rc) rc = launch(1, fb.n_series[1], 8 * (size_t)(32 * sp.D * sp.P + 32));
+        if (!rc) rc = launch(2, fb.n_series[2], 8 * (size_t)(sp.T + sp.D * (2 * sp.P - 1)));
+        for (int m = 0; m < 2; ++m)
+            if (pieces[m]) cudaFreeAsync(pieces[m], st);
+        if (rc) return rc;
         cx.phase(GS_PH_DOWN);
         for (int k = 0; k < in.qt->depth; ++k) {
             const int64_t items = (1ll << k) * in.nh;
