@@ -202,3 +202,19 @@ def test_paper_cost_model_within_eps(gs, D):
         assert rel_err(out, exact).max() <= eps
         if D <= 3:
             assert st.pairs_dh + st.pairs_dl + st.pairs_h2l > 0
+
+
+def test_autotuner_picks_a_certified_configuration(gs, tmp_path):
+    from paper_1206_6857_gb300 import autotune
+    wl = synth.config2(0.02)
+    tq, tw = _dev(wl.queries), _dev(wl.weights)
+    best, table = autotune.tune(tq, tw, wl.h, wl.eps, fraction=0.5, leaves=(16, 32))
+    assert len(table) == 2 * len(autotune.DEFAULT_COSTS)
+    assert best["seconds"] == min(r["seconds"] for r in table)
+    out = gs.gs_sum(tq, tq, tw, wl.h, wl.eps, opts=autotune.options(best)).cpu().numpy()
+    exact = oracle_ex.gauss_sum(wl.queries, wl.refs, wl.weights, wl.h)
+    assert rel_err(out, exact).max() <= wl.eps
+    key = autotune.key_for(wl.D, wl.N, wl.h, wl.diameter)
+    path = str(tmp_path / "tuned.json")
+    autotune.cache(path, key, best)
+    assert autotune.cache(path, key) == best
