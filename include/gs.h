@@ -214,6 +214,37 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
                 const gs_opts *opts, void *stream, gs_stats *stats);
 
 /*
+ * gs_sum_exhaustive_noalloc -- the exhaustive sum (gs_sum with eps = 0) for
+ * callers that cannot let the library allocate device memory: runtimes that
+ * own all device memory through their own allocator and forbid direct
+ * cudaMalloc calls, or processes that allocate everything up front and must
+ * not fail or stall on an allocation mid-run.  The paper has no counterpart;
+ * this is a deployment variant of the same computation.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
+ * (a status word and the packed reference records) lives in one fixed 16 MiB
+ * array of the library's device memory, resident on every device that loads
+ * the library until the process exits.  Limits: the packed references must
+ * fit that array -- e.g. up to about 1.0e6 references for FP32 data with
+ * D <= 3, 5.2e5 for D <= 7, 2.1e5 for D = 16; larger N returns GS_ERR_ARG with
+ * a message naming the limit.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the array and each call resets what it needs,
+ * but calls whose GPU work overlaps (other streams, other host threads) race
+ * on it: serialise them.
+ *
+ * Arguments, layouts and results are those of gs_sum (device queries, refs,
+ * weights and out; HOST h; dtype GS_F32 or GS_F64; 1 <= nh <= 64).  Returns
+ * when out is ready, with GS_OK or GS_ERR_ARG, GS_ERR_WEIGHT,
+ * GS_ERR_NONFINITE or GS_ERR_CUDA.
+ */
+int gs_sum_exhaustive_noalloc(const void *queries, int64_t M, const void *refs, const float *weights,
+                              int64_t N, int D, int dtype, const double *h, int nh, double *out,
+                              void *stream);
+
+/*
  * gs_probe_rates -- measures this device's throughput, in lanes per SM per
  * SM clock cycle, of the two instructions the base case is built from: MUFU
  * ex2.approx.ftz.f32 and FP32 FFMA.  A short kernel with independent chains

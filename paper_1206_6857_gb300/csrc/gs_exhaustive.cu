@@ -336,6 +336,132 @@ int exhaustive_sum(const void *queries, int64_t M, const void *refs, const float
 }
 
 // --------------------------------------------------------------------------
+// Allocation-free exhaustive sum.
+//
+// Some callers cannot let a library call cudaMalloc: runtimes that own all
+// device memory through their own allocator and forbid direct allocations,
+// processes that allocate everything up front and must not fail or stall in
+// the middle of a run, and code that cannot afford the implicit
+// synchronisation an allocation may cause.  For them this variant of the
+// exhaustive sum keeps its scratch -- the status word and the packed
+// reference records -- in one fixed array in the library's device memory
+// instead of allocating it.  The caller still provides inputs and outputs.
+//
+// The array exists once per device that loads the library and stays resident
+// until the process exits.  Every call uses the same array, so calls whose GPU
+// work overlaps (concurrent streams, several host threads) race on it and
+// must be serialised by the caller.  Each call resets the status word and
+// overwrites the records it reads, so nothing depends on what a previous call
+// left there.
+// --------------------------------------------------------------------------
+constexpr size_t kNoAllocBytes = (size_t)16 << 20;   // 16 MiB
+constexpr size_t kNoAllocHeader = 256;               // status word (Ingest) at the start
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static void *g_noalloc_addr[64] = {nullptr};
+
+// Device address of g_noalloc_scratch for the current device.  The symbol's
+// name in host code is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress once per device (with that device current) and
+// cached.
+static int noalloc_scratch(void **out) {
+    int dev = 0;
+    GS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return GS_ERR_CUDA;
+    }
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        GS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return GS_OK;
+}
+
+template <typename T, int DP, int NJ>
+static int run_exhaustive_noalloc(const void *queries, int64_t M, const void *refs, const float *weights,
+                                  int64_t N, int D, const double *h, int nh, unsigned char *scratch,
+                                  double *out, cudaStream_t st) {
+    using Cfg = TileCfg<T, DP>;
+    constexpr int NT = Cfg::NT, TILE = Cfg::TILE;
+    constexpr int QPT = (DP <= 8) ? 2 : 1;
+    const int64_t Npad = (N + TILE - 1) / TILE * TILE;
+    const int64_t max_pad = (int64_t)((kNoAllocBytes - kNoAllocHeader) / (NT * sizeof(T))) / TILE * TILE;
+    if (Npad > max_pad) {
+        set_error("gs_sum_exhaustive_noalloc: N=%lld references exceed the %lld this build's fixed "
+                  "16 MiB scratch holds for D=%d", (long long)N, (long long)max_pad, D);
+        return GS_ERR_ARG;
+    }
+    Ingest *ing = reinterpret_cast<Ingest *>(scratch);
+    T *rec = reinterpret_cast<T *>(scratch + kNoAllocHeader);
+    CallCtx cx;
+    cx.st = st;
+    cudaError_t e = launch_ingest(ing, queries, M, refs, weights, N, D, sizeof(T) == 8 ? GS_F64 : GS_F32, cx);
+    if (e != cudaSuccess) return cuda_fail(e, "ingest launch");
+    k_pack_refs<T, DP><<<grid_for(Npad, 256), 256, 0, st>>>((const T *)refs, weights, N, Npad, D, ing, rec);
+    NegC nc;
+    for (int j = 0; j < 64; ++j) nc.v[j] = 0.f;
+    for (int j = 0; j < nh; ++j) nc.v[j] = (float)(-1.4426950408889634 / (2.0 * h[j] * h[j]));
+    const int64_t bx = (M + kThreads * QPT - 1) / (kThreads * QPT);
+    const int nz = (nh + NJ - 1) / NJ;
+    const int64_t tiles = Npad / TILE;
+    const int64_t target = (int64_t)num_sms() * 8;
+    int64_t splits = (target + bx * nz - 1) / (bx * nz);
+    if (splits < 1) splits = 1;
+    if (splits > tiles) splits = tiles;
+    if (splits > 65535) splits = 65535;
+    const int64_t chunk = (tiles + splits - 1) / splits * TILE;
+    splits = (Npad + chunk - 1) / chunk;
+    if (bx > 2147483647LL) {
+        set_error("too many queries for one launch");
+        return GS_ERR_ARG;
+    }
+    if (splits > 1) GS_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)M * nh * sizeof(double), st));
+    dim3 grid((unsigned)bx, (unsigned)splits, (unsigned)nz);
+    k_exhaustive<T, DP, NJ, QPT><<<grid, kThreads, 0, st>>>((const T *)queries, M, D, rec, chunk, Npad, nc, nh, ing,
+                                                           out, splits > 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_exhaustive launch");
+    Ingest hing;
+    e = cudaMemcpyAsync(&hing, ing, sizeof(Ingest), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "gs_sum_exhaustive_noalloc");
+    if (hing.status & ST_NONFINITE) {
+        set_error("non-finite coordinate or weight");
+        return GS_ERR_NONFINITE;
+    }
+    if (hing.status & ST_WEIGHT) {
+        set_error("a weight is <= 0 (weights must be positive)");
+        return GS_ERR_WEIGHT;
+    }
+    return GS_OK;
+}
+
+template <typename T, int DP>
+static int noalloc_nj(const void *q, int64_t M, const void *r, const float *w, int64_t N, int D, const double *h,
+                      int nh, unsigned char *scr, double *out, cudaStream_t st) {
+    if (nh <= 1) return run_exhaustive_noalloc<T, DP, 1>(q, M, r, w, N, D, h, nh, scr, out, st);
+    if (nh <= 2) return run_exhaustive_noalloc<T, DP, 2>(q, M, r, w, N, D, h, nh, scr, out, st);
+    if (nh <= 4) return run_exhaustive_noalloc<T, DP, 4>(q, M, r, w, N, D, h, nh, scr, out, st);
+    return run_exhaustive_noalloc<T, DP, 8>(q, M, r, w, N, D, h, nh, scr, out, st);
+}
+
+template <typename T>
+static int noalloc_d(const void *q, int64_t M, const void *r, const float *w, int64_t N, int D, const double *h,
+                     int nh, unsigned char *scr, double *out, cudaStream_t st) {
+#define GS_CASE(DPV) \
+    if (D <= DPV) return noalloc_nj<T, DPV>(q, M, r, w, N, D, h, nh, scr, out, st);
+    GS_CASE(1) GS_CASE(2) GS_CASE(3) GS_CASE(4) GS_CASE(5) GS_CASE(6) GS_CASE(7) GS_CASE(8)
+    GS_CASE(12) GS_CASE(16) GS_CASE(24) GS_CASE(32)
+#undef GS_CASE
+    set_error("D=%d exceeds 32", D);
+    return GS_ERR_ARG;
+}
+
+// --------------------------------------------------------------------------
 // Instruction-rate probe: independent ex2 / FFMA chains on every SM, timed
 // with the per-SM cycle counter.  Each block records its SM and its start and
 // end cycle; an SM's rate is the work of all blocks it ran over the span from
@@ -436,3 +562,29 @@ int probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, cudaStream_t st
 }
 
 }  // namespace gs
+
+extern "C" int gs_sum_exhaustive_noalloc(const void *queries, int64_t M, const void *refs, const float *weights,
+                                         int64_t N, int D, int dtype, const double *h, int nh, double *out,
+                                         void *stream) {
+    using namespace gs;
+    if (!queries || !refs || !weights || !out || !h) {
+        set_error("NULL array argument");
+        return GS_ERR_ARG;
+    }
+    if (M < 1 || N < 1 || D < 1 || D > 32 || nh < 1 || nh > 64 || (dtype != GS_F32 && dtype != GS_F64)) {
+        set_error("gs_sum_exhaustive_noalloc: bad size, dimension, bandwidth count or dtype");
+        return GS_ERR_ARG;
+    }
+    for (int j = 0; j < nh; ++j)
+        if (!(h[j] > 0.0) || !isfinite(h[j])) {
+            set_error("bandwidth h[%d]=%g is not finite and positive", j, h[j]);
+            return GS_ERR_ARG;
+        }
+    void *scr = nullptr;
+    int rc = noalloc_scratch(&scr);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == GS_F64)
+        return noalloc_d<double>(queries, M, refs, weights, N, D, h, nh, (unsigned char *)scr, out, st);
+    return noalloc_d<float>(queries, M, refs, weights, N, D, h, nh, (unsigned char *)scr, out, st);
+}

@@ -87,6 +87,8 @@ SIGNATURES = {
     "gs_sum_host": (ctypes.c_int, _SUM_ARGS),
     "gs_probe_rates": (ctypes.c_int, [_VP, _VP, _VP]),
     "gs_sum_trace": (ctypes.c_int, _SUM_ARGS + [_VP, _I64, _VP, _VP, _VP]),
+    "gs_sum_exhaustive_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, _VP,
+                                                  ctypes.c_int, _VP, _VP]),
     "gs_lscv": (ctypes.c_int, [_VP, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                _VP, _VP, _VP, _VP, _VP]),
 }
@@ -196,6 +198,25 @@ def gs_sum_trace(queries, refs, weights, h, eps, opts: gs_opts | None = None, st
     if n.value > trace_cap:
         raise GSError(GS_ERR_CAPACITY, "trace of %d records exceeds trace_cap=%d" % (n.value, trace_cap))
     return out, tr[:n.value], qperm, rperm
+
+
+def gs_sum_exhaustive_noalloc(queries, refs, weights, h, out=None, stream=None, raise_on_error: bool = True):
+    """Exhaustive sums through the allocation-free entry point (its scratch is a
+    fixed array inside the library); same tensors as gs_sum with eps = 0."""
+    import torch
+    assert queries.is_cuda and refs.is_cuda and weights.is_cuda
+    M, D = queries.shape
+    N = refs.shape[0]
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    if out is None:
+        out = torch.empty((M, hh.size), dtype=torch.float64, device=queries.device)
+    rc = load().gs_sum_exhaustive_noalloc(_VP(queries.data_ptr()), M, _VP(refs.data_ptr()),
+                                          _VP(weights.data_ptr()), N, D, _dtype_code(queries), hh.ctypes.data,
+                                          hh.size, _VP(out.data_ptr()), _stream_ptr(stream))
+    if raise_on_error:
+        _check(rc)
+        return out
+    return rc, out
 
 
 def gs_lscv(points, weights, h, eps, opts: gs_opts | None = None, stream=None, stats: gs_stats | None = None):
