@@ -221,12 +221,12 @@ def run_gs(args):
     scores = {}
 
     # autotuner (setup, not timed): leaf size, PLIMIT and bestMethod cost
-    # weights chosen by timing the library on a seeded 25% subsample
+    # weights chosen by timing the library on the data with 8 of the bandwidths
     tuned, opts = None, None
     if eps > 0 and not args.no_tune:
         from paper_1206_6857_gb300 import autotune
         t0 = time.perf_counter()
-        tuned, _table = autotune.tune(tq, tw, hs, eps, fraction=0.25)
+        tuned, _table = autotune.tune(tq, tw, hs, eps)
         tuned["tuning_seconds"] = time.perf_counter() - t0
         opts = autotune.options(tuned)
 

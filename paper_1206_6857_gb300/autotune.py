@@ -24,8 +24,9 @@ import numpy as np
 
 from . import gs
 
-DEFAULT_LEAVES = (16, 32, 64)
-DEFAULT_COSTS = ((32.0, 32.0, 32.0, 1.0), (128.0, 128.0, 16.0, 1.0), (512.0, 512.0, 64.0, 1.0))
+DEFAULT_LEAVES = (32, 64)
+DEFAULT_COSTS = ((32.0, 32.0, 32.0, 1.0), (128.0, 128.0, 16.0, 1.0), (512.0, 512.0, 64.0, 1.0),
+                 (2048.0, 2048.0, 64.0, 1.0))
 
 
 def key_for(D, N, h, diameter):
@@ -44,13 +45,20 @@ def _opts(leaf, plimit, cw):
     return o
 
 
-def tune(points, weights, h, eps, fraction=0.25, leaves=DEFAULT_LEAVES, costs=DEFAULT_COSTS,
+def tune(points, weights, h, eps, fraction=1.0, h_subset=8, leaves=DEFAULT_LEAVES, costs=DEFAULT_COSTS,
          plimits=(0,), seed=0, reps=1, queries=None):
     """Time every candidate on a seeded subsample; returns (best dict, table).
 
     points, weights (and queries for a bichromatic problem) are torch CUDA
-    tensors; h is a host sequence; fraction is the subsample size."""
+    tensors; h is a host sequence.  The timing problem keeps a fraction of the
+    points (all by default: point density decides how deep the traversal
+    goes, so a thinned sample would favour the wrong settings) and h_subset
+    bandwidths spread evenly over h (bandwidths are summed independently, so a
+    spread subset predicts the full sweep's balance)."""
     import torch
+    h = np.asarray(h, dtype=np.float64)
+    if h_subset and h.size > h_subset:
+        h = np.sort(h)[np.linspace(0, h.size - 1, h_subset).round().astype(int)]
     N = points.shape[0]
     g = torch.Generator(device="cpu").manual_seed(seed)
     n = max(2, int(N * fraction))

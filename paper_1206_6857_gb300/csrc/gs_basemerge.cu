@@ -89,11 +89,11 @@ struct MergedParams {
     unsigned long long *evals;
 };
 
-// Sum over one reference leaf for NJ bandwidths at once: one squared
-// distance per (query, reference), NJ exponentials.
+// Sum over one reference leaf (staged in shared memory) for NJ bandwidths
+// at once: one squared distance per (query, reference), NJ exponentials.
 template <int DP, int QPL, bool ANCH, int NJ>
-__device__ __forceinline__ void leaf_terms(const MergedParams &bp, const float (&xq)[QPL][DP], const float (&dc)[DP],
-                                           const float4 *rp, int nr, const float (&c)[8], float (&part)[QPL][8]) {
+__device__ __forceinline__ void leaf_terms(const float (&xq)[QPL][DP], const float (&dc)[DP], const float4 *rp,
+                                           int nr, const float (&c)[8], float (&part)[QPL][8]) {
     constexpr int NT = RefRec<float, DP>::NT;
 #pragma unroll
     for (int s = 0; s < QPL; ++s)
@@ -104,7 +104,7 @@ __device__ __forceinline__ void leaf_terms(const MergedParams &bp, const float (
         float rv[NT];
 #pragma unroll
         for (int v = 0; v < NT / 4; ++v) {
-            const float4 f = __ldg(rp + i * (NT / 4) + v);
+            const float4 f = rp[i * (NT / 4) + v];
             rv[4 * v] = f.x; rv[4 * v + 1] = f.y; rv[4 * v + 2] = f.z; rv[4 * v + 3] = f.w;
         }
         const float l = rv[DP];
@@ -122,10 +122,20 @@ __device__ __forceinline__ void leaf_terms(const MergedParams &bp, const float (
     }
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Shared memory per warp: Kahan sums and compensations (2 x nh x QPL x 32
+// floats), then two staging buffers of lmax reference records each.
 template <int DP, int QPL, bool ANCH>
 __global__ void __launch_bounds__(32 * kMW)
 k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const long long *__restrict__ off,
-                  int64_t lq) {
+                  int64_t lq, int lmax) {
     constexpr int NT = RefRec<float, DP>::NT;
     extern __shared__ float sm_f[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -133,11 +143,11 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
     const int64_t e0 = off[i], e1 = off[i + 1];
     if (e0 == e1) return;
     const int nh = bp.nh;
-    // per warp: Kahan sum and compensation per (bandwidth, query slot)
-    float *ksum = sm_f + (size_t)w * 2 * nh * QPL * 32;
+    const size_t per_warp = (size_t)2 * nh * QPL * 32 + (size_t)2 * lmax * NT;
+    float *ksum = sm_f + (size_t)w * per_warp;
     float *kcmp = ksum + nh * QPL * 32;
+    float *stage = ksum + 2 * nh * QPL * 32;   // 2 x lmax x NT floats, 16-byte aligned
     for (int t = lane; t < 2 * nh * QPL * 32; t += 32) ksum[t] = 0.f;
-    __syncwarp();
     const int64_t qleaf0 = (1ll << bp.q_depth) - 1, rleaf0 = (1ll << bp.r_depth) - 1;
     const int64_t qnode = qleaf0 + i;
     const int64_t qb = level_begin(bp.qn, bp.q_depth, i), qe = level_begin(bp.qn, bp.q_depth, i + 1);
@@ -150,19 +160,37 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
 #pragma unroll
         for (int d = 0; d < DP; ++d) xq[s][d] = bp.qrec[pos * NT + d];
     }
+    // stage the reference leaf of entry e into buffer b (cooperative 16-byte async copies)
+    auto stage_leaf = [&](int64_t e, int b) {
+        const int64_t ri = ent[e].r - rleaf0;
+        const int64_t rb = level_begin(bp.rn, bp.r_depth, ri), re = level_begin(bp.rn, bp.r_depth, ri + 1);
+        const int nv = (int)(re - rb) * (NT / 4);
+        const float4 *src = reinterpret_cast<const float4 *>(bp.rrec + rb * NT);
+        float4 *dst = reinterpret_cast<float4 *>(stage + (size_t)b * lmax * NT);
+        for (int v = lane; v < nv; v += 32) cp_async16(dst + v, src + v);
+        cp_async_commit();
+    };
     unsigned long long evals = 0;
+    int buf = 0;
+    if (e0 + w < e1) stage_leaf(e0 + w, 0);
     for (int64_t e = e0 + w; e < e1; e += kMW) {
         const MergedEntry E = ent[e];
         const int64_t ri = E.r - rleaf0;
-        const int64_t rb = level_begin(bp.rn, bp.r_depth, ri), re = level_begin(bp.rn, bp.r_depth, ri + 1);
-        const int nr = (int)(re - rb);
+        const int nr = (int)(level_begin(bp.rn, bp.r_depth, ri + 1) - level_begin(bp.rn, bp.r_depth, ri));
+        if (e + kMW < e1) {
+            stage_leaf(e + kMW, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
         float dc[DP];
 #pragma unroll
         for (int d = 0; d < DP; ++d) dc[d] = 0.f;
         if (ANCH) {
             for (int d = 0; d < bp.D; ++d) dc[d] = (float)(bp.qcenter[qnode * bp.D + d] - bp.rcenter[(int64_t)E.r * bp.D + d]);
         }
-        const float4 *rp = reinterpret_cast<const float4 *>(bp.rrec + rb * NT);
+        const float4 *rp = reinterpret_cast<const float4 *>(stage + (size_t)buf * lmax * NT);
         uint32_t m = E.mask;
         evals += (unsigned long long)__popc(m) * (unsigned long long)nr;
         while (m) {
@@ -178,10 +206,10 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
             }
             float part[QPL][8];
             switch (nj) {
-                case 1: leaf_terms<DP, QPL, ANCH, 1>(bp, xq, dc, rp, nr, c, part); break;
-                case 2: leaf_terms<DP, QPL, ANCH, 2>(bp, xq, dc, rp, nr, c, part); break;
-                case 3: leaf_terms<DP, QPL, ANCH, 3>(bp, xq, dc, rp, nr, c, part); break;
-                default: leaf_terms<DP, QPL, ANCH, 4>(bp, xq, dc, rp, nr, c, part); break;
+                case 1: leaf_terms<DP, QPL, ANCH, 1>(xq, dc, rp, nr, c, part); break;
+                case 2: leaf_terms<DP, QPL, ANCH, 2>(xq, dc, rp, nr, c, part); break;
+                case 3: leaf_terms<DP, QPL, ANCH, 3>(xq, dc, rp, nr, c, part); break;
+                default: leaf_terms<DP, QPL, ANCH, 4>(xq, dc, rp, nr, c, part); break;
             }
             for (int k = 0; k < nj; ++k) {
 #pragma unroll
@@ -194,6 +222,8 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                 }
             }
         }
+        __syncwarp();   // everyone is done with this buffer before it is refilled
+        buf ^= 1;
     }
     __syncthreads();
     const double wmax = (double)__uint_as_float(bp.ing->wmax_bits);
@@ -203,7 +233,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
         if (qq >= nq) continue;
         double v = 0.0;
         for (int k = 0; k < kMW; ++k) {
-            const float *ks = sm_f + (size_t)k * 2 * nh * QPL * 32;
+            const float *ks = sm_f + (size_t)k * per_warp;
             v += (double)ks[t] - (double)ks[nh * QPL * 32 + t];
         }
         if (v != 0.0) atomicAdd(&bp.Gq[(qb + qq) * nh + j], v * wmax);
@@ -213,14 +243,16 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
 
 template <int DP>
 static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const MergedEntry *ent, const long long *off,
-                            int64_t lq, cudaStream_t st) {
+                            int64_t lq, int lmax, cudaStream_t st) {
+    constexpr int NT = RefRec<float, DP>::NT;
     // shared memory sized from the instantiated QPL (the kernel indexes with it)
 #define GS_M(Q, A)                                                                                  \
     do {                                                                                            \
-        const size_t sm = (size_t)kMW * 2 * bp.nh * (Q) * 32 * sizeof(float);                      \
+        const size_t sm = (size_t)kMW * (2 * bp.nh * (Q) * 32 + 2 * lmax * NT) * sizeof(float);    \
+        if (sm > 220 * 1024) return GS_ERR_UNSUPPORTED;                                             \
         cudaFuncSetAttribute(k_basecase_merged<DP, Q, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)sm);                                                              \
-        k_basecase_merged<DP, Q, A><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq);          \
+        k_basecase_merged<DP, Q, A><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq, lmax);    \
     } while (0)
     if (anch) {
         if (qpl <= 1) GS_M(1, true); else if (qpl <= 2) GS_M(2, true); else GS_M(4, true);
@@ -287,20 +319,21 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         bp.evals = fb.evals;
         const int64_t maxq = (in.qt->n + lq - 1) / lq;
         const int qpl = (int)((maxq + 31) / 32);
+        const int lmax = (int)((in.rt->n + lr - 1) / lr);
         const bool anch = in.qt->dtype == GS_F64;
         switch (DP) {
-            case 1: rc = launch_merged_dp<1>(qpl, anch, bp, ent, off, lq, st); break;
-            case 2: rc = launch_merged_dp<2>(qpl, anch, bp, ent, off, lq, st); break;
-            case 3: rc = launch_merged_dp<3>(qpl, anch, bp, ent, off, lq, st); break;
-            case 4: rc = launch_merged_dp<4>(qpl, anch, bp, ent, off, lq, st); break;
-            case 5: rc = launch_merged_dp<5>(qpl, anch, bp, ent, off, lq, st); break;
-            case 6: rc = launch_merged_dp<6>(qpl, anch, bp, ent, off, lq, st); break;
-            case 7: rc = launch_merged_dp<7>(qpl, anch, bp, ent, off, lq, st); break;
-            case 8: rc = launch_merged_dp<8>(qpl, anch, bp, ent, off, lq, st); break;
-            case 12: rc = launch_merged_dp<12>(qpl, anch, bp, ent, off, lq, st); break;
-            case 16: rc = launch_merged_dp<16>(qpl, anch, bp, ent, off, lq, st); break;
-            case 24: rc = launch_merged_dp<24>(qpl, anch, bp, ent, off, lq, st); break;
-            default: rc = launch_merged_dp<32>(qpl, anch, bp, ent, off, lq, st); break;
+            case 1: rc = launch_merged_dp<1>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 2: rc = launch_merged_dp<2>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 3: rc = launch_merged_dp<3>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 4: rc = launch_merged_dp<4>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 5: rc = launch_merged_dp<5>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 6: rc = launch_merged_dp<6>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 7: rc = launch_merged_dp<7>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 8: rc = launch_merged_dp<8>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 12: rc = launch_merged_dp<12>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 16: rc = launch_merged_dp<16>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 24: rc = launch_merged_dp<24>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            default: rc = launch_merged_dp<32>(qpl, anch, bp, ent, off, lq, lmax, st); break;
         }
         cx.launches += 1;
         cx.launches_base += 1;

@@ -208,7 +208,7 @@ def test_autotuner_picks_a_certified_configuration(gs, tmp_path):
     from paper_1206_6857_gb300 import autotune
     wl = synth.config2(0.02)
     tq, tw = _dev(wl.queries), _dev(wl.weights)
-    best, table = autotune.tune(tq, tw, wl.h, wl.eps, fraction=0.5, leaves=(16, 32))
+    best, table = autotune.tune(tq, tw, wl.h, wl.eps, fraction=0.5, h_subset=4, leaves=(16, 32))
     assert len(table) == 2 * len(autotune.DEFAULT_COSTS)
     assert best["seconds"] == min(r["seconds"] for r in table)
     out = gs.gs_sum(tq, tq, tw, wl.h, wl.eps, opts=autotune.options(best)).cpu().numpy()
