@@ -373,7 +373,7 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
         use_fd = (n_fd <= allot) & (selector != SEL_EXHAUSTIVE)
         method[use_fd] = FD
         E[use_fd] = e_fd[use_fd]
-        leftover = np.where(use_fd, allot - n_fd, 0.0)
+        spent = np.where(use_fd, n_fd, 0.0)          # token needed by each pruned pair
 
         if selector in (SEL_RULE, SEL_MLP) and P >= 1:
             base = WR * e4_32.astype(np.float64)
@@ -421,15 +421,17 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
             method[series] = best_m[series]
             porder[series] = best_p[series]
             E[series] = best_E[series]
-            leftover = np.where(series, allot - best_need, leftover)
-        undecided = (method == SPLIT) | (method == BASE)
-        if tokens:
-            leftover = np.where(undecided & (method == BASE), allot + WR, leftover)
-            leftover = np.where(method == SPLIT, allot, leftover)
-        else:
-            leftover = np.zeros(pq.size)
+            spent = np.where(series, best_need, spent)
+        # Fig. 7's token update over the whole group: pruned pairs pay their
+        # need (negative needs bank the excess), base cases bank W_R, splits
+        # leave the token alone
         finished = method != SPLIT
-        tok_new = group_reduce(leftover, gid, pos, ng)
+        if tokens:
+            banked = group_reduce(np.where(method == BASE, WR, 0.0), gid, pos, ng)
+            paid = group_reduce(spent, gid, pos, ng)
+            tok_new = np.maximum(0.0, (tok[gq, gj] + banked) - paid)
+        else:
+            tok_new = np.zeros(ng)
         fin_add = group_reduce(np.where(finished, dl, 0.0), gid, pos, ng)
         est_add = group_reduce(np.where(method == FD, est_fd, 0.0), gid, pos, ng)
         fin[gq, gj] = fin[gq, gj] + fin_add

@@ -161,26 +161,33 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const double share = tok0 / Wg;
         const double kappa = Wtot / (eps_t * Gb);
         // pass 2: decisions
-        double s_left = 0.0, s_fin = 0.0, s_est = 0.0;
+        double s_bank = 0.0, s_paid = 0.0, s_fin = 0.0, s_est = 0.0;
         int n_m[6] = {0, 0, 0, 0, 0, 0};
+        // FP32 screen of the FD test (n_fd <= allot  <=>  (K(dmin)-K(dmax)) kappa/2 <= 1 + share):
+        // pairs it rejects fail the exact FP64 test by a margin of 1e-4, so the
+        // FP64 test only runs where it can succeed; decisions are unchanged
+        const bool screen = 0.5 * kappa < 1e37;   // kappa/2 representable in FP32
+        const float hk32 = screen ? (float)(0.5 * kappa) : 0.f;
+        const float thr32 = (float)(1.0 + (fp.tokens ? share : 0.0)) * 1.0001f;
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
             const float *gc = fp.geo + 3 * (G.off + k);
-            const double kmax = (double)gc[0], kmin = (double)gc[1];
+            const float kmax32 = gc[0], kmin32 = gc[1];
             const float e4f = gc[2];
+            const double kmax = (double)kmax32, kmin = (double)kmin32;
             const double WR = fp.rW[r];
             const double dl = WR * kmax;
             const double allot = fp.tokens ? WR * share : 0.0;
             int method = (fp.q_leaf && fp.r_leaf) ? M_BASE : M_SPLIT;
             int pord = 0;
-            double leftover = 0.0;
+            double spent = 0.0;
             bool decided = false;
-            if (fp.selector != GS_SEL_EXHAUSTIVE) {
+            if (fp.selector != GS_SEL_EXHAUSTIVE && !(screen && (kmin32 - kmax32) * hk32 > thr32)) {
                 const double e_fd = (WR * (kmin - kmax)) * 0.5;
                 const double n_fd = e_fd * kappa - WR;
                 if (n_fd <= allot) {
                     method = M_FD;
-                    leftover = allot - n_fd;
+                    spent = n_fd;
                     decided = true;
                     s_est = s_est + (WR * (kmin + kmax)) * 0.5;
                 }
@@ -230,15 +237,12 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                 if (best_m >= 0) {
                     method = best_m;
                     pord = best_p;
-                    leftover = allot - best_need;
+                    spent = best_need;
                     decided = true;
                 }
             }
-            if (!decided) {
-                if (fp.tokens) leftover = method == M_BASE ? allot + WR : allot;
-            }
-            if (!fp.tokens) leftover = 0.0;
-            s_left = s_left + leftover;
+            if (method == M_FD || (method >= M_DH && method <= M_H2L)) s_paid = s_paid + spent;
+            if (method == M_BASE) s_bank = s_bank + WR;
             if (method != M_SPLIT) s_fin = s_fin + dl;
             n_m[method]++;
             dec[G.off + k] = (uint8_t)(method | (pord << 3));
@@ -248,7 +252,11 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     trace[ti] = make_int4((int)q, (int)r, j, method | (pord << 8) | (fp.t << 16));
             }
         }
-        const double tok_new = warp_sum(s_left), fin_add = warp_sum(s_fin), est_add = warp_sum(s_est);
+        const double banked = warp_sum(s_bank), paid = warp_sum(s_paid);
+        const double fin_add = warp_sum(s_fin), est_add = warp_sum(s_est);
+        // Fig. 7's token update over the whole group: pruned pairs pay their
+        // need, base cases bank W_R, splits leave the token alone
+        const double tok_new = fp.tokens ? fmax(0.0, (tok0 + banked) - paid) : 0.0;
 #pragma unroll
         for (int m = 0; m < 6; ++m) n_m[m] = __reduce_add_sync(0xffffffffu, n_m[m]);
         if (lane == 0) {
