@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload size factor (1 = full)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--leaf", type=int, default=0, help="fixed leaf size (skips the autotuner)")
+    ap.add_argument("--cost", default="", help="fixed cost weights c_DH,c_DL,c_H2L,c_Direct (skips the autotuner)")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -223,7 +225,12 @@ def run_gs(args):
     # autotuner (setup, not timed): leaf size, PLIMIT and bestMethod cost
     # weights chosen by timing the library on the data with 8 of the bandwidths
     tuned, opts = None, None
-    if eps > 0 and not args.no_tune:
+    if args.leaf or args.cost:
+        from paper_1206_6857_gb300 import autotune
+        cw = [float(v) for v in args.cost.split(",")] if args.cost else list(gs.GS_COST_DEFAULT)
+        tuned = {"leaf_size": args.leaf or 32, "plimit": 0, "cost_weight": cw, "fixed": True}
+        opts = autotune.options(tuned)
+    elif eps > 0 and not args.no_tune:
         from paper_1206_6857_gb300 import autotune
         t0 = time.perf_counter()
         tuned, _table = autotune.tune(tq, tw, hs, eps)
