@@ -28,14 +28,18 @@ struct MergedEntry {
     uint32_t mask;   // bandwidths j with bit j set
 };
 
+struct BitMap {
+    int8_t rank[64];    // bandwidth j -> mask bit (bandwidths ranked by ascending h)
+};
+
 __global__ void k_mark_masks(const Group *__restrict__ bgroups, int64_t nbg, const int32_t *__restrict__ base_r,
-                             int64_t qleaf0, int64_t rleaf0, int64_t lr, uint32_t *mask) {
+                             int64_t qleaf0, int64_t rleaf0, int64_t lr, uint32_t *mask, BitMap bm) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < nbg; g += warps) {
         const Group G = bgroups[g];
         uint32_t *row = mask + (G.q - qleaf0) * lr;
-        const uint32_t bit = 1u << G.j;
+        const uint32_t bit = 1u << bm.rank[G.j];
         for (int k = lane; k < G.cnt; k += 32) atomicOr(&row[base_r[G.off + k] - rleaf0], bit);
     }
 }
@@ -83,7 +87,8 @@ struct MergedParams {
     int q_depth, r_depth;
     const double *qcenter, *rcenter;
     int D, nh;
-    float negc[32];
+    float negc[32];     // by mask bit: -log2(e) / (2 h^2)
+    int jcol[32];       // by mask bit: output column (bandwidth index)
     double *Gq;
     const Ingest *ing;
     unsigned long long *evals;
@@ -130,24 +135,29 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Shared memory per warp: Kahan sums and compensations (2 x nh x QPL x 32
-// floats), then two staging buffers of lmax reference records each.
+constexpr int kBlk = 8;   // bandwidths accumulated per pass
+
+// Shared memory per warp: Kahan sums and compensations for one block of
+// kBlk bandwidths (2 x kBlk x QPL x 32 floats), then two staging buffers of
+// lmax reference records each.  Mask bits are bandwidths in ascending h, so
+// the bandwidths a leaf pair needs sit in one or two blocks; the CTA makes one
+// pass over its entries per block of bandwidths.
 template <int DP, int QPL, bool ANCH>
 __global__ void __launch_bounds__(32 * kMW)
 k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const long long *__restrict__ off,
                   int64_t lq, int lmax) {
     constexpr int NT = RefRec<float, DP>::NT;
+    constexpr int KS = kBlk * QPL * 32;
     extern __shared__ float sm_f[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = blockIdx.x;
     const int64_t e0 = off[i], e1 = off[i + 1];
     if (e0 == e1) return;
     const int nh = bp.nh;
-    const size_t per_warp = (size_t)2 * nh * QPL * 32 + (size_t)2 * lmax * NT;
+    const size_t per_warp = (size_t)2 * KS + (size_t)2 * lmax * NT;
     float *ksum = sm_f + (size_t)w * per_warp;
-    float *kcmp = ksum + nh * QPL * 32;
-    float *stage = ksum + 2 * nh * QPL * 32;   // 2 x lmax x NT floats, 16-byte aligned
-    for (int t = lane; t < 2 * nh * QPL * 32; t += 32) ksum[t] = 0.f;
+    float *kcmp = ksum + KS;
+    float *stage = ksum + 2 * KS;   // 2 x lmax x NT floats, 16-byte aligned
     const int64_t qleaf0 = (1ll << bp.q_depth) - 1, rleaf0 = (1ll << bp.r_depth) - 1;
     const int64_t qnode = qleaf0 + i;
     const int64_t qb = level_begin(bp.qn, bp.q_depth, i), qe = level_begin(bp.qn, bp.q_depth, i + 1);
@@ -170,73 +180,88 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
         for (int v = lane; v < nv; v += 32) cp_async16(dst + v, src + v);
         cp_async_commit();
     };
+    const double wmax = (double)__uint_as_float(bp.ing->wmax_bits);
     unsigned long long evals = 0;
-    int buf = 0;
-    if (e0 + w < e1) stage_leaf(e0 + w, 0);
-    for (int64_t e = e0 + w; e < e1; e += kMW) {
-        const MergedEntry E = ent[e];
-        const int64_t ri = E.r - rleaf0;
-        const int nr = (int)(level_begin(bp.rn, bp.r_depth, ri + 1) - level_begin(bp.rn, bp.r_depth, ri));
-        if (e + kMW < e1) {
-            stage_leaf(e + kMW, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncwarp();
-        float dc[DP];
-#pragma unroll
-        for (int d = 0; d < DP; ++d) dc[d] = 0.f;
-        if (ANCH) {
-            for (int d = 0; d < bp.D; ++d) dc[d] = (float)(bp.qcenter[qnode * bp.D + d] - bp.rcenter[(int64_t)E.r * bp.D + d]);
-        }
-        const float4 *rp = reinterpret_cast<const float4 *>(stage + (size_t)buf * lmax * NT);
-        uint32_t m = E.mask;
-        evals += (unsigned long long)__popc(m) * (unsigned long long)nr;
-        while (m) {
-            int js[8];
-            float c[8];
-            int nj = 0;
-            while (m && nj < 4) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1;
-                js[nj] = j;
-                c[nj] = bp.negc[j];
-                ++nj;
+    const int nblk = (nh + kBlk - 1) / kBlk;
+    for (int jb = 0; jb < nblk; ++jb) {
+        const uint32_t bmask = 0xFFu << (kBlk * jb);
+        for (int t = lane; t < 2 * KS; t += 32) ksum[t] = 0.f;
+        auto next_used = [&](int64_t e) {
+            while (e < e1 && !(ent[e].mask & bmask)) e += kMW;
+            return e;
+        };
+        int64_t e = next_used(e0 + w);
+        int buf = 0;
+        if (e < e1) stage_leaf(e, 0);
+        while (e < e1) {
+            const int64_t en = next_used(e + kMW);
+            if (en < e1) {
+                stage_leaf(en, buf ^ 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
-            float part[QPL][8];
-            switch (nj) {
-                case 1: leaf_terms<DP, QPL, ANCH, 1>(xq, dc, rp, nr, c, part); break;
-                case 2: leaf_terms<DP, QPL, ANCH, 2>(xq, dc, rp, nr, c, part); break;
-                case 3: leaf_terms<DP, QPL, ANCH, 3>(xq, dc, rp, nr, c, part); break;
-                default: leaf_terms<DP, QPL, ANCH, 4>(xq, dc, rp, nr, c, part); break;
-            }
-            for (int k = 0; k < nj; ++k) {
+            __syncwarp();
+            const MergedEntry E = ent[e];
+            const int64_t ri = E.r - rleaf0;
+            const int nr = (int)(level_begin(bp.rn, bp.r_depth, ri + 1) - level_begin(bp.rn, bp.r_depth, ri));
+            float dc[DP];
 #pragma unroll
-                for (int s = 0; s < QPL; ++s) {
-                    const int slot = (js[k] * QPL + s) * 32 + lane;
-                    const float y = part[s][k] - kcmp[slot];
-                    const float t = ksum[slot] + y;
-                    kcmp[slot] = (t - ksum[slot]) - y;
-                    ksum[slot] = t;
+            for (int d = 0; d < DP; ++d) dc[d] = 0.f;
+            if (ANCH) {
+                for (int d = 0; d < bp.D; ++d)
+                    dc[d] = (float)(bp.qcenter[qnode * bp.D + d] - bp.rcenter[(int64_t)E.r * bp.D + d]);
+            }
+            const float4 *rp = reinterpret_cast<const float4 *>(stage + (size_t)buf * lmax * NT);
+            uint32_t m = (E.mask & bmask) >> (kBlk * jb);
+            evals += (unsigned long long)__popc(m) * (unsigned long long)nr;
+            while (m) {
+                int ks[8];
+                float c[8];
+                int nj = 0;
+                while (m && nj < 4) {
+                    const int k = __ffs(m) - 1;
+                    m &= m - 1;
+                    ks[nj] = k;
+                    c[nj] = bp.negc[kBlk * jb + k];
+                    ++nj;
+                }
+                float part[QPL][8];
+                switch (nj) {
+                    case 1: leaf_terms<DP, QPL, ANCH, 1>(xq, dc, rp, nr, c, part); break;
+                    case 2: leaf_terms<DP, QPL, ANCH, 2>(xq, dc, rp, nr, c, part); break;
+                    case 3: leaf_terms<DP, QPL, ANCH, 3>(xq, dc, rp, nr, c, part); break;
+                    default: leaf_terms<DP, QPL, ANCH, 4>(xq, dc, rp, nr, c, part); break;
+                }
+                for (int k = 0; k < nj; ++k) {
+#pragma unroll
+                    for (int s = 0; s < QPL; ++s) {
+                        const int slot = (ks[k] * QPL + s) * 32 + lane;
+                        const float y = part[s][k] - kcmp[slot];
+                        const float t = ksum[slot] + y;
+                        kcmp[slot] = (t - ksum[slot]) - y;
+                        ksum[slot] = t;
+                    }
                 }
             }
+            __syncwarp();   // everyone is done with this buffer before it is refilled
+            buf ^= 1;
+            e = en;
         }
-        __syncwarp();   // everyone is done with this buffer before it is refilled
-        buf ^= 1;
-    }
-    __syncthreads();
-    const double wmax = (double)__uint_as_float(bp.ing->wmax_bits);
-    for (int t = threadIdx.x; t < nh * QPL * 32; t += blockDim.x) {
-        const int j = t / (QPL * 32), s = (t / 32) % QPL, ln = t % 32;
-        const int qq = ln + 32 * s;
-        if (qq >= nq) continue;
-        double v = 0.0;
-        for (int k = 0; k < kMW; ++k) {
-            const float *ks = sm_f + (size_t)k * per_warp;
-            v += (double)ks[t] - (double)ks[nh * QPL * 32 + t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < KS; t += blockDim.x) {
+            const int k = t / (QPL * 32), s = (t / 32) % QPL, ln = t % 32;
+            const int qq = ln + 32 * s;
+            const int bit = kBlk * jb + k;
+            if (qq >= nq || bit >= nh) continue;
+            double v = 0.0;
+            for (int ww = 0; ww < kMW; ++ww) {
+                const float *ks2 = sm_f + (size_t)ww * per_warp;
+                v += (double)ks2[t] - (double)ks2[KS + t];
+            }
+            if (v != 0.0) atomicAdd(&bp.Gq[(qb + qq) * nh + bp.jcol[bit]], v * wmax);
         }
-        if (v != 0.0) atomicAdd(&bp.Gq[(qb + qq) * nh + j], v * wmax);
+        __syncthreads();
     }
     if (bp.evals && lane == 0 && evals) atomicAdd(bp.evals, evals * (unsigned long long)nq);
 }
@@ -248,7 +273,7 @@ static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const Me
     // shared memory sized from the instantiated QPL (the kernel indexes with it)
 #define GS_M(Q, A)                                                                                  \
     do {                                                                                            \
-        const size_t sm = (size_t)kMW * (2 * bp.nh * (Q) * 32 + 2 * lmax * NT) * sizeof(float);    \
+        const size_t sm = (size_t)kMW * (2 * kBlk * (Q) * 32 + 2 * lmax * NT) * sizeof(float);     \
         if (sm > 220 * 1024) return GS_ERR_UNSUPPORTED;                                             \
         cudaFuncSetAttribute(k_basecase_merged<DP, Q, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)sm);                                                              \
@@ -284,7 +309,18 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     GS_CUDA_TRY(cudaMemsetAsync(mask, 0, (size_t)lq * lr * sizeof(uint32_t), st));
     GS_CUDA_TRY(cudaMallocAsync((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
     const int grid = fb.grid_warps / 8;
-    k_mark_masks<<<grid, 256, 0, st>>>(fb.base_groups, fb.n_base_groups, fb.base_r, qleaf0, rleaf0, lr, mask);
+    // mask bit of each bandwidth: its rank in ascending h
+    int order[64];
+    for (int j = 0; j < in.nh; ++j) order[j] = j;
+    for (int a = 1; a < in.nh; ++a)
+        for (int b = a; b > 0 && in.h[order[b]] < in.h[order[b - 1]]; --b) {
+            const int t = order[b];
+            order[b] = order[b - 1];
+            order[b - 1] = t;
+        }
+    BitMap bmap;
+    for (int b = 0; b < in.nh; ++b) bmap.rank[order[b]] = (int8_t)b;
+    k_mark_masks<<<grid, 256, 0, st>>>(fb.base_groups, fb.n_base_groups, fb.base_r, qleaf0, rleaf0, lr, mask, bmap);
     k_row_count<<<grid, 256, 0, st>>>(mask, lq, lr, off);
     cx.launches += 2;
     if (int rc0 = scan_i64(off, lq, off + lq, cx)) {
@@ -313,7 +349,11 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         bp.rcenter = in.rt->center;
         bp.D = in.D;
         bp.nh = in.nh;
-        for (int j = 0; j < in.nh; ++j) bp.negc[j] = (float)(-1.4426950408889634 / (2.0 * in.h[j] * in.h[j]));
+        for (int b = 0; b < in.nh; ++b) {
+            const double hb = in.h[order[b]];
+            bp.negc[b] = (float)(-1.4426950408889634 / (2.0 * hb * hb));
+            bp.jcol[b] = order[b];
+        }
         bp.Gq = Gq;
         bp.ing = in.ing;
         bp.evals = fb.evals;
