@@ -81,8 +81,12 @@ __global__ void k_row_compact(const uint32_t *__restrict__ mask, int64_t lq, int
 
 constexpr int kMW = 4;   // warps per CTA
 
+// The packed f32x2 path takes two query slots per register pair.
+__host__ __device__ constexpr bool merged_x2(int DP, int QPL) { return QPL >= 2 && DP <= 16; }
+
 struct MergedParams {
     const float *qrec, *rrec;
+    const float *rrec2;      // reference records with every float duplicated (packed path)
     int64_t qn, rn;
     int q_depth, r_depth;
     const double *qcenter, *rcenter;
@@ -127,6 +131,75 @@ __device__ __forceinline__ void leaf_terms(const float (&xq)[QPL][DP], const flo
     }
 }
 
+// Two FP32 values in one 64-bit register pair, for the packed f32x2
+// instructions of sm_100-family GPUs: element-wise IEEE operations, so a
+// packed sum rounds exactly like the two scalar ones.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// leaf_terms for two query slots per register pair: the staged reference
+// records hold every float twice, (x_0, x_0, x_1, x_1, ..., l, l, ...), so a
+// 16-byte shared load gives two broadcast pairs.  Same operations, in the
+// same order, as the scalar version.
+template <int DP, int QPL, bool ANCH, int NJ>
+__device__ __forceinline__ void leaf_terms_x2(const f2_t (&xq)[QPL / 2][DP], const f2_t (&dc)[DP],
+                                              const ulonglong2 *rp, int nr, const f2_t (&c)[4],
+                                              f2_t (&part)[QPL / 2][4]) {
+    constexpr int NT = RefRec<float, DP>::NT;   // pairs per staged record
+#pragma unroll
+    for (int s = 0; s < QPL / 2; ++s)
+#pragma unroll
+        for (int k = 0; k < NJ; ++k) part[s][k] = 0ull;
+#pragma unroll 2
+    for (int i = 0; i < nr; ++i) {
+        f2_t rv[NT];
+#pragma unroll
+        for (int v = 0; v < NT / 2; ++v) {
+            const ulonglong2 u = rp[i * (NT / 2) + v];
+            rv[2 * v] = u.x;
+            rv[2 * v + 1] = u.y;
+        }
+#pragma unroll
+        for (int s = 0; s < QPL / 2; ++s) {
+            f2_t d2 = 0ull;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                f2_t df = f2_sub(xq[s][d], rv[d]);
+                if (ANCH) df = f2_add(df, dc[d]);
+                d2 = f2_fma(df, df, d2);
+            }
+#pragma unroll
+            for (int k = 0; k < NJ; ++k) {
+                float a0, a1;
+                f2_unpack(f2_fma(d2, c[k], rv[DP]), a0, a1);
+                part[s][k] = f2_add(part[s][k], f2_pack(ex2_approx(a0), ex2_approx(a1)));
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
@@ -147,6 +220,8 @@ __global__ void __launch_bounds__(32 * kMW)
 k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const long long *__restrict__ off,
                   int64_t lq, int lmax) {
     constexpr int NT = RefRec<float, DP>::NT;
+    constexpr bool X2 = merged_x2(DP, QPL);
+    constexpr int NS = X2 ? 2 * NT : NT;   // floats per staged reference record
     constexpr int KS = kBlk * QPL * 32;
     extern __shared__ float sm_f[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -154,7 +229,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
     const int64_t e0 = off[i], e1 = off[i + 1];
     if (e0 == e1) return;
     const int nh = bp.nh;
-    const size_t per_warp = (size_t)2 * KS + (size_t)2 * lmax * NT;
+    const size_t per_warp = (size_t)2 * KS + (size_t)2 * lmax * NS;
     float *ksum = sm_f + (size_t)w * per_warp;
     float *kcmp = ksum + KS;
     float *stage = ksum + 2 * KS;   // 2 x lmax x NT floats, 16-byte aligned
@@ -174,9 +249,9 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
     auto stage_leaf = [&](int64_t e, int b) {
         const int64_t ri = ent[e].r - rleaf0;
         const int64_t rb = level_begin(bp.rn, bp.r_depth, ri), re = level_begin(bp.rn, bp.r_depth, ri + 1);
-        const int nv = (int)(re - rb) * (NT / 4);
-        const float4 *src = reinterpret_cast<const float4 *>(bp.rrec + rb * NT);
-        float4 *dst = reinterpret_cast<float4 *>(stage + (size_t)b * lmax * NT);
+        const int nv = (int)(re - rb) * (NS / 4);
+        const float4 *src = reinterpret_cast<const float4 *>((X2 ? bp.rrec2 : bp.rrec) + rb * NS);
+        float4 *dst = reinterpret_cast<float4 *>(stage + (size_t)b * lmax * NS);
         for (int v = lane; v < nv; v += 32) cp_async16(dst + v, src + v);
         cp_async_commit();
     };
@@ -207,17 +282,16 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
             const int nr = (int)(level_begin(bp.rn, bp.r_depth, ri + 1) - level_begin(bp.rn, bp.r_depth, ri));
             float dc[DP];
 #pragma unroll
-            for (int d = 0; d < DP; ++d) dc[d] = 0.f;
-            if (ANCH) {
-                for (int d = 0; d < bp.D; ++d)
-                    dc[d] = (float)(bp.qcenter[qnode * bp.D + d] - bp.rcenter[(int64_t)E.r * bp.D + d]);
-            }
-            const float4 *rp = reinterpret_cast<const float4 *>(stage + (size_t)buf * lmax * NT);
+            for (int d = 0; d < DP; ++d)
+                dc[d] = (ANCH && d < bp.D)
+                            ? (float)(bp.qcenter[qnode * bp.D + d] - bp.rcenter[(int64_t)E.r * bp.D + d])
+                            : 0.f;
+            const float *rp = stage + (size_t)buf * lmax * NS;
             uint32_t m = (E.mask & bmask) >> (kBlk * jb);
             evals += (unsigned long long)__popc(m) * (unsigned long long)nr;
             while (m) {
                 int ks[8];
-                float c[8];
+                float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 int nj = 0;
                 while (m && nj < 4) {
                     const int k = __ffs(m) - 1;
@@ -227,11 +301,36 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                     ++nj;
                 }
                 float part[QPL][8];
-                switch (nj) {
-                    case 1: leaf_terms<DP, QPL, ANCH, 1>(xq, dc, rp, nr, c, part); break;
-                    case 2: leaf_terms<DP, QPL, ANCH, 2>(xq, dc, rp, nr, c, part); break;
-                    case 3: leaf_terms<DP, QPL, ANCH, 3>(xq, dc, rp, nr, c, part); break;
-                    default: leaf_terms<DP, QPL, ANCH, 4>(xq, dc, rp, nr, c, part); break;
+                if constexpr (X2) {
+                    constexpr int QH = QPL / 2 > 0 ? QPL / 2 : 1;
+                    f2_t xq2[QH][DP], dc2[DP], c2[4], part2[QH][4];
+#pragma unroll
+                    for (int h2 = 0; h2 < QH; ++h2)
+#pragma unroll
+                        for (int d = 0; d < DP; ++d) xq2[h2][d] = f2_pack(xq[2 * h2][d], xq[2 * h2 + 1][d]);
+#pragma unroll
+                    for (int d = 0; d < DP; ++d) dc2[d] = f2_pack(dc[d], dc[d]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) c2[k] = f2_pack(c[k], c[k]);
+                    const ulonglong2 *rp2 = reinterpret_cast<const ulonglong2 *>(rp);
+                    switch (nj) {
+                        case 1: leaf_terms_x2<DP, QPL, ANCH, 1>(xq2, dc2, rp2, nr, c2, part2); break;
+                        case 2: leaf_terms_x2<DP, QPL, ANCH, 2>(xq2, dc2, rp2, nr, c2, part2); break;
+                        case 3: leaf_terms_x2<DP, QPL, ANCH, 3>(xq2, dc2, rp2, nr, c2, part2); break;
+                        default: leaf_terms_x2<DP, QPL, ANCH, 4>(xq2, dc2, rp2, nr, c2, part2); break;
+                    }
+#pragma unroll
+                    for (int h2 = 0; h2 < QH; ++h2)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) f2_unpack(part2[h2][k], part[2 * h2][k], part[2 * h2 + 1][k]);
+                } else {
+                    const float4 *rp4 = reinterpret_cast<const float4 *>(rp);
+                    switch (nj) {
+                        case 1: leaf_terms<DP, QPL, ANCH, 1>(xq, dc, rp4, nr, c, part); break;
+                        case 2: leaf_terms<DP, QPL, ANCH, 2>(xq, dc, rp4, nr, c, part); break;
+                        case 3: leaf_terms<DP, QPL, ANCH, 3>(xq, dc, rp4, nr, c, part); break;
+                        default: leaf_terms<DP, QPL, ANCH, 4>(xq, dc, rp4, nr, c, part); break;
+                    }
                 }
                 for (int k = 0; k < nj; ++k) {
 #pragma unroll
@@ -273,7 +372,8 @@ static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const Me
     // shared memory sized from the instantiated QPL (the kernel indexes with it)
 #define GS_M(Q, A)                                                                                  \
     do {                                                                                            \
-        const size_t sm = (size_t)kMW * (2 * kBlk * (Q) * 32 + 2 * lmax * NT) * sizeof(float);     \
+        const size_t ns = merged_x2(DP, Q) ? 2 * NT : NT;                                            \
+        const size_t sm = (size_t)kMW * (2 * kBlk * (Q) * 32 + 2 * lmax * ns) * sizeof(float);     \
         if (sm > 220 * 1024) return GS_ERR_UNSUPPORTED;                                             \
         cudaFuncSetAttribute(k_basecase_merged<DP, Q, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              (int)sm);                                                              \
@@ -288,9 +388,37 @@ static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const Me
     return GS_OK;
 }
 
+// shared memory of the merged kernel for records of NT floats, query slots
+// per lane qpl (instantiated as 1, 2 or 4) and leaves of at most lmax points
+static size_t merged_smem(int DP, int NT, int qpl, int lmax) {
+    const int Q = qpl <= 1 ? 1 : (qpl <= 2 ? 2 : 4);
+    const size_t ns = merged_x2(DP, Q) ? 2 * NT : NT;
+    return (size_t)kMW * (2 * kBlk * Q * 32 + 2 * lmax * ns) * sizeof(float);
+}
+
+static void merged_shape(const TraversalIn &in, int &qpl, int &lmax) {
+    const int64_t lq = 1ll << in.qt->depth, lr = 1ll << in.rt->depth;
+    const int64_t maxq = (in.qt->n + lq - 1) / lq;
+    qpl = (int)((maxq + 31) / 32);
+    lmax = (int)((in.rt->n + lr - 1) / lr);
+}
+
 bool merged_base_possible(const TraversalIn &in) {
     const int64_t lq = 1ll << in.qt->depth, lr = 1ll << in.rt->depth;
-    return in.nh <= 32 && lq * lr <= (3ll << 30);   // mask array at most 12 GB
+    int qpl, lmax;
+    merged_shape(in, qpl, lmax);
+    const int DP = dp_for(in.D);
+    const int NT = (int)(((DP + 1) * sizeof(float) + 15) / 16) * 4;
+    return in.nh <= 32 && lq * lr <= (3ll << 30)   // mask array at most 12 GB
+           && qpl <= 4 && merged_smem(DP, NT, qpl, lmax) <= 220 * 1024;
+}
+
+// records with every float duplicated, for the packed path
+__global__ void k_dup_records(const float *__restrict__ rec, int64_t nf, float2 *rec2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = rec[i];
+        rec2[i] = make_float2(v, v);
+    }
 }
 
 int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, CallCtx &cx) {
@@ -305,6 +433,7 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     uint32_t *mask = nullptr;
     long long *off = nullptr;
     MergedEntry *ent = nullptr;
+    float *rec2 = nullptr;
     GS_CUDA_TRY(cudaMallocAsync((void **)&mask, (size_t)lq * lr * sizeof(uint32_t), st));
     GS_CUDA_TRY(cudaMemsetAsync(mask, 0, (size_t)lq * lr * sizeof(uint32_t), st));
     GS_CUDA_TRY(cudaMallocAsync((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
@@ -357,10 +486,17 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         bp.Gq = Gq;
         bp.ing = in.ing;
         bp.evals = fb.evals;
-        const int64_t maxq = (in.qt->n + lq - 1) / lq;
-        const int qpl = (int)((maxq + 31) / 32);
-        const int lmax = (int)((in.rt->n + lr - 1) / lr);
+        int qpl, lmax;
+        merged_shape(in, qpl, lmax);
         const bool anch = in.qt->dtype == GS_F64;
+        const int Q = qpl <= 1 ? 1 : (qpl <= 2 ? 2 : 4);
+        if (merged_x2(DP, Q)) {
+            const int64_t nf = in.rt->n * (int64_t)in.rt->rec_stride;
+            GS_CUDA_TRY(cudaMallocAsync((void **)&rec2, (size_t)nf * 2 * sizeof(float), st));
+            k_dup_records<<<grid, 256, 0, st>>>(in.rt->rec, nf, (float2 *)rec2);
+            cx.launches += 1;
+            bp.rrec2 = rec2;
+        }
         switch (DP) {
             case 1: rc = launch_merged_dp<1>(qpl, anch, bp, ent, off, lq, lmax, st); break;
             case 2: rc = launch_merged_dp<2>(qpl, anch, bp, ent, off, lq, lmax, st); break;
@@ -381,6 +517,7 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     }
     cudaFreeAsync(ent, st);
     cudaFreeAsync(off, st);
+    if (rec2) cudaFreeAsync(rec2, st);
     cx.phase(GS_PH_OTHER);
     if (rc) return rc;
     cudaError_t e = cudaGetLastError();

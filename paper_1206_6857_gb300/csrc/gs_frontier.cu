@@ -20,10 +20,12 @@
 // child frontier (still grouped and sorted), the base-case pairs and the
 // series actions.
 //
-// Everything that decides an action is FP64 with no FMA contraction (this
-// file is compiled with -fmad=false) and an exp written for this purpose
-// (Cody-Waite reduction + degree-13 Taylor polynomial), so the pair lists are
-// reproducible bit for bit by a plain CPU evaluation of the same formulas.
+// Every decision is taken with IEEE operations in a fixed order and no FMA
+// contraction (this file is compiled with -fmad=false): kernel bounds in FP32
+// with rigorous margins and an exp2 written for this purpose, budgets and
+// comparisons in FP64, and FP32 screens that only skip FP64 tests they prove
+// to fail.  The pair lists are therefore reproducible bit for bit by a plain
+// CPU evaluation of the same formulas.
 #include <math.h>
 
 #include "gs_frontier.cuh"
@@ -75,18 +77,25 @@ struct FrontierParams {
     const double *qrad;
     const float *qwmin;
     const double *rrad, *rW;
+    const float *rrad32;  // reference radii rounded down to FP32
     const double *inv_h;
     double *fin, *tok, *est;
     float *geo;           // per pair cache: K(delta_max) lower, K(delta_min) upper, e^{-dmin^2/4h^2} upper
     double F[17], BT[17], Dpow[34];
     double cw[4];         // cost weights of c_DH, c_DL, c_H2L, c_Direct
+    // weighted bestMethod costs of this iteration, for node sizes floor(n / 2^depth) + {0, 1}
+    double cDH[2][17], cDL[2][17], cH2L[17], cex[2][2];
     float c32[64];        // log2(e) / 2h_j^2 rounded to FP32
 };
 
-__device__ __forceinline__ double node_count(int64_t n, int depth, int64_t node) {
+__device__ __forceinline__ int64_t node_size(int64_t n, int depth, int64_t node) {
     const int64_t i = node - ((1ll << depth) - 1);
-    return (double)(level_begin(n, depth, i + 1) - level_begin(n, depth, i));
+    return level_begin(n, depth, i + 1) - level_begin(n, depth, i);
 }
+
+// floats per warp of the per-group screen tables (4 x 17)
+constexpr int kTab = 68;
+static_assert(sizeof(FrontierParams) <= 4096, "kernel parameters above 4 KB");
 
 struct KBounds {
     float kmax, kmin, e4;
@@ -130,6 +139,7 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
     const double Wtot = fs->Wtot, floorW = fs->floorW, eps_t = fs->eps_t;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t trace_base = fs->trace_count;
+    __shared__ float s_tab[8][kTab];
     for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += warps) {
         const Group G = groups[g];
         const int64_t q = G.q;
@@ -155,34 +165,66 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         double Gb = fin0 + front;
         if (fp.mono) Gb = fmax(Gb, (double)fp.qwmin[q]);
         Gb = fmax(Gb, floorW);
-        const double cq = node_count(fp.qn, fp.q_depth, q);
+        const int64_t cq = node_size(fp.qn, fp.q_depth, q);
         const double rQ = fp.qrad[q] * invh;
         // per group: token per unit weight and the Theorem 2 scale W / (eps G)
         const double share = tok0 / Wg;
         const double kappa = Wtot / (eps_t * Gb);
         // pass 2: decisions
         double s_bank = 0.0, s_paid = 0.0, s_fin = 0.0, s_est = 0.0;
-        int n_m[6] = {0, 0, 0, 0, 0, 0};
+        int n_fd = 0, n_dh = 0, n_dl = 0, n_h2l = 0, n_base = 0, n_split = 0;
+        const double share_t = fp.tokens ? share : 0.0;
         // FP32 screen of the FD test (n_fd <= allot  <=>  (K(dmin)-K(dmax)) kappa/2 <= 1 + share):
         // pairs it rejects fail the exact FP64 test by a margin of 1e-4, so the
         // FP64 test only runs where it can succeed; decisions are unchanged
         const bool screen = 0.5 * kappa < 1e37;   // kappa/2 representable in FP32
         const float hk32 = screen ? (float)(0.5 * kappa) : 0.f;
-        const float thr32 = (float)(1.0 + (fp.tokens ? share : 0.0)) * 1.0001f;
+        const float thr32 = (float)(1.0 + share_t) * 1.0001f;
+        // Screen of the series bounds: a lower bound of E_p kappa / W_R computed
+        // with every FP32 operation rounded down from inputs rounded down
+        // (overflow gives FLT_MAX, underflow rounds towards zero, so it is a
+        // lower bound whatever the magnitudes).  The exact FP64 test passes
+        // only if E_p kappa / W_R <= (1 + share)(1 + 2^-40), so a lower bound
+        // above (1 + share)(1 + 2^-20) rejects only bounds the FP64 test
+        // rejects.  Per group and order: hk = F_p kappa, gdl = hk r_Q^p (DL),
+        // A = r_Q^p and B = C(D+p-1, D) tail_p (H2L).
+        const bool series = (fp.selector == GS_SEL_RULE || fp.selector == GS_SEL_MLP) && fp.P >= 1;
+        const float thrL = __fmul_ru(__double2float_ru(1.0 + share_t), 0x1.00001p+0f);
+        const float invhd = __double2float_rd(invh);
+        float *tab = s_tab[threadIdx.x >> 5];
+        __syncwarp();
+        if (series && lane >= 1 && lane <= fp.P) {
+            const int p = lane;
+            const float hk = __double2float_rd(fp.F[p] * kappa);
+            const float rq = __double2float_rd(rQ);
+            float a = 1.f;
+            for (int i = 0; i < p; ++i) a = __fmul_rd(a, rq);
+            float tl = 1.f;
+            const double x2 = kSqrt2 * rQ;
+            if (!(x2 <= 1.0)) {
+                const float x2d = __double2float_rd(x2);
+                for (int i = 0; i < p - 1; ++i) tl = __fmul_rd(tl, x2d);
+            }
+            tab[0 * 17 + p] = hk;
+            tab[1 * 17 + p] = __fmul_rd(hk, a);
+            tab[2 * 17 + p] = a;
+            tab[3 * 17 + p] = __fmul_rd(__double2float_rd(fp.BT[p]), tl);
+        }
+        __syncwarp();
+        const int iq = (int)(cq - (fp.qn >> fp.q_depth));
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
             const float *gc = fp.geo + 3 * (G.off + k);
             const float kmax32 = gc[0], kmin32 = gc[1];
             const float e4f = gc[2];
-            const double kmax = (double)kmax32, kmin = (double)kmin32;
             const double WR = fp.rW[r];
-            const double dl = WR * kmax;
-            const double allot = fp.tokens ? WR * share : 0.0;
             int method = (fp.q_leaf && fp.r_leaf) ? M_BASE : M_SPLIT;
             int pord = 0;
             double spent = 0.0;
             bool decided = false;
             if (fp.selector != GS_SEL_EXHAUSTIVE && !(screen && (kmin32 - kmax32) * hk32 > thr32)) {
+                const double kmax = (double)kmax32, kmin = (double)kmin32;
+                const double allot = fp.tokens ? WR * share : 0.0;
                 const double e_fd = (WR * (kmin - kmax)) * 0.5;
                 const double n_fd = e_fd * kappa - WR;
                 if (n_fd <= allot) {
@@ -192,35 +234,52 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     s_est = s_est + (WR * (kmin + kmax)) * 0.5;
                 }
             }
-            if (!decided && (fp.selector == GS_SEL_RULE || fp.selector == GS_SEL_MLP) && fp.P >= 1) {
+            if (!decided && series) {
                 // bestMethod (Fig. 6).  Costs grow with p, so a method whose
                 // cost already reaches the best so far (or exceeds c_Direct)
                 // cannot be chosen and its remaining bounds are skipped; the
-                // choice is the same as evaluating every bound.
-                const double cr = node_count(fp.rn, fp.r_depth, r);
-                const double c_ex = (((double)fp.D * cq) * cr) * fp.cw[3];
-                double best_c = INFINITY, best_need = 0.0;
+                // choice is the same as evaluating every bound.  Costs are
+                // positive, so their order is that of their bit patterns.
+                const int ir = (int)(node_size(fp.rn, fp.r_depth, r) - (fp.rn >> fp.r_depth));
+                const long long c_ex = __double_as_longlong(fp.cex[iq][ir]);
+                long long best_c = 0x7ff0000000000000ll;   // +inf
+                double best_need = 0.0;
                 int best_m = -1, best_p = 0;
-                const double base = WR * (double)e4f;
-                const double rR = fp.rrad[r] * invh;
-                const double x2 = kSqrt2 * rQ;
-                const double sr = kSqrt2 * rR;
+                const float rRd = __fmul_rd(fp.rrad32[r], invhd);
+                const float srd = __fmul_rd(rRd, 0x1.6a09e6p+0f);   // sqrt(2) rounded down
+                bool have64 = false;
+                double base = 0.0, rR = 0.0, sr = 0.0, allot = 0.0;
                 for (int m = M_DH; m <= M_H2L; ++m) {
+                    float pw = 1.f;
                     for (int p = 1; p <= fp.P; ++p) {
-                        double c;
-                        if (m == M_DH)
-                            c = (cq * fp.Dpow[p + 1]) * fp.cw[0];
-                        else if (m == M_DL)
-                            c = (cr * fp.Dpow[p + 1]) * fp.cw[1];
-                        else
-                            c = fp.Dpow[2 * p + 1] * fp.cw[2];
+                        const double cd = m == M_DH ? fp.cDH[iq][p] : (m == M_DL ? fp.cDL[ir][p] : fp.cH2L[p]);
+                        const long long c = __double_as_longlong(cd);
                         if (c >= best_c || c > c_ex) break;
+                        float lb;
+                        if (m == M_DH) {
+                            pw = __fmul_rd(pw, rRd);
+                            lb = __fmul_rd(__fmul_rd(e4f, tab[p]), pw);
+                        } else if (m == M_DL) {
+                            lb = __fmul_rd(e4f, tab[17 + p]);
+                        } else {
+                            pw = __fmul_rd(pw, srd);
+                            lb = __fmul_rd(__fmul_rd(e4f, tab[p]), __fadd_rd(tab[34 + p], __fmul_rd(pw, tab[51 + p])));
+                        }
+                        if (lb > thrL) continue;
+                        if (!have64) {
+                            have64 = true;
+                            base = WR * (double)e4f;
+                            rR = fp.rrad[r] * invh;
+                            sr = kSqrt2 * rR;
+                            allot = fp.tokens ? WR * share : 0.0;
+                        }
                         double Ep;
                         if (m == M_DH) {
                             Ep = (base * fp.F[p]) * rpow(rR, p);
                         } else if (m == M_DL) {
                             Ep = (base * fp.F[p]) * rpow(rQ, p);
                         } else {
+                            const double x2 = kSqrt2 * rQ;
                             const double tail = (x2 <= 1.0) ? 1.0 : rpow(x2, p - 1);
                             Ep = (base * fp.F[p]) * (rpow(rQ, p) + (rpow(sr, p) * fp.BT[p]) * tail);
                         }
@@ -243,8 +302,14 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             }
             if (method == M_FD || (method >= M_DH && method <= M_H2L)) s_paid = s_paid + spent;
             if (method == M_BASE) s_bank = s_bank + WR;
-            if (method != M_SPLIT) s_fin = s_fin + dl;
-            n_m[method]++;
+            // at a leaf-leaf iteration no pair splits, so this sum equals pass 1's s_dl
+            if (method != M_SPLIT && !(fp.q_leaf && fp.r_leaf)) s_fin = s_fin + WR * (double)kmax32;
+            n_fd += method == M_FD;
+            n_dh += method == M_DH;
+            n_dl += method == M_DL;
+            n_h2l += method == M_H2L;
+            n_base += method == M_BASE;
+            n_split += method == M_SPLIT;
             dec[G.off + k] = (uint8_t)(method | (pord << 3));
             if (trace) {
                 const int64_t ti = trace_base + G.off + k;
@@ -252,11 +317,13 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     trace[ti] = make_int4((int)q, (int)r, j, method | (pord << 8) | (fp.t << 16));
             }
         }
+        if (fp.q_leaf && fp.r_leaf) s_fin = s_dl;
         const double banked = warp_sum(s_bank), paid = warp_sum(s_paid);
         const double fin_add = warp_sum(s_fin), est_add = warp_sum(s_est);
         // Fig. 7's token update over the whole group: pruned pairs pay their
         // need, base cases bank W_R, splits leave the token alone
         const double tok_new = fp.tokens ? fmax(0.0, (tok0 + banked) - paid) : 0.0;
+        int n_m[6] = {n_fd, n_dh, n_dl, n_h2l, n_base, n_split};
 #pragma unroll
         for (int m = 0; m < 6; ++m) n_m[m] = __reduce_add_sync(0xffffffffu, n_m[m]);
         if (lane == 0) {
@@ -270,17 +337,17 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     fp.tok[(2 * q + c) * fp.nh + j] = tok_new;
                 }
             }
-            const int n_split = n_m[M_SPLIT];
+            const int n_sp = n_m[M_SPLIT];
             int child_pairs, child_groups;
             if (fp.q_leaf) {
-                child_pairs = 2 * n_split;
-                child_groups = n_split > 0;
+                child_pairs = 2 * n_sp;
+                child_groups = n_sp > 0;
             } else if (fp.r_leaf) {
-                child_pairs = 2 * n_split;
-                child_groups = n_split > 0 ? 2 : 0;
+                child_pairs = 2 * n_sp;
+                child_groups = n_sp > 0 ? 2 : 0;
             } else {
-                child_pairs = 4 * n_split;
-                child_groups = n_split > 0 ? 2 : 0;
+                child_pairs = 4 * n_sp;
+                child_groups = n_sp > 0 ? 2 : 0;
             }
             int32_t *c = cnt + g * kCols;
             c[C_PAIRS] = child_pairs;
@@ -579,6 +646,7 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.rn = in.rt->n;
     fp.qlo32 = in.qt->lo32; fp.qhi32 = in.qt->hi32; fp.qrad = in.qt->rad; fp.qwmin = in.qt->wmin;
     fp.rlo32 = in.rt->lo32; fp.rhi32 = in.rt->hi32; fp.rrad = in.rt->rad; fp.rW = in.rt->W;
+    fp.rrad32 = in.rt->rad32;
     fp.inv_h = fb.inv_h;
     for (int j = 0; j < in.nh; ++j) fp.c32[j] = (float)(1.4426950408889634 / ((2.0 * in.h[j]) * in.h[j]));
     fp.fin = fb.fin; fp.tok = fb.tok; fp.est = fb.est;
@@ -612,6 +680,19 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         fp.r_depth = t < in.rt->depth ? t : in.rt->depth;
         fp.q_leaf = t >= in.qt->depth;
         fp.r_leaf = t >= in.rt->depth;
+        // bestMethod costs (Fig. 6) times their weights; node sizes at a level
+        // are floor(n / 2^depth) or one more, so each cost takes two values
+        for (int a = 0; a < 2; ++a) {
+            const double cq = (double)((fp.qn >> fp.q_depth) + a);
+            const double cr = (double)((fp.rn >> fp.r_depth) + a);
+            for (int p = 1; p <= 16 && p <= in.P; ++p) {
+                fp.cDH[a][p] = (cq * fp.Dpow[p + 1]) * fp.cw[0];
+                fp.cDL[a][p] = (cr * fp.Dpow[p + 1]) * fp.cw[1];
+            }
+            for (int b = 0; b < 2; ++b)
+                fp.cex[a][b] = (((double)D * cq) * (double)((fp.rn >> fp.r_depth) + b)) * fp.cw[3];
+        }
+        for (int p = 1; p <= 16 && p <= in.P; ++p) fp.cH2L[p] = fp.Dpow[2 * p + 1] * fp.cw[2];
         // this iteration's per-pair arrays
         if ((rc = grow(&fb.dec, &fb.cap_pairs, npairs, 0, st))) return rc;
         if ((rc = grow(&fb.geo, &fb.cap_geo, 3 * npairs, 0, st))) return rc;

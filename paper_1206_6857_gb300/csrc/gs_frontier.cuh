@@ -38,6 +38,7 @@ struct FrontierState {
     int64_t totals[kCols];      // column totals of the last scan
     unsigned long long method_count[6];
     double eps_t, rho, Wtot, floorW;
+    unsigned long long work;    // tile counter of dynamically scheduled kernels (zeroed before each)
     int32_t overflow;
     int32_t pad;
 };

@@ -225,11 +225,18 @@ __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent
 }
 
 // ---------------------------------------------------------------------------
-// H2L: one warp per action, lanes over b, loop over a; A_a and the 1-D
-// Hermite polynomials of tau = (x_Q - x_R)/s (orders 0 .. 2p-2) in shared
-// memory
+// H2L.  Warps take tiles of 32 consecutive actions.  Orders 1 and 2 (the
+// bulk of the actions: one and 1 + D coefficients) take one lane each, with
+// the Lemma 1 sums written out:
+//   b = 0:    s_0   = A_0 + sum_i A_{e_i} H_1(t_i),
+//   b = e_k:  s_e_k = H_1(t_k) (s_0 - A_{e_k} H_1(t_k)) + A_{e_k} H_2(t_k),
+// B_b += (-1)^|b| e^{-|t|^2} s_b.  When all 32 actions of a tile add into
+// the same (Q, h) they are summed across the warp first.  Higher orders are
+// done one at a time by the whole warp: lanes over b, loop over a, with A_a
+// and the 1-D Hermite polynomials of t = (x_Q - x_R)/s (orders 0 .. 2p-2)
+// in shared memory.
 // ---------------------------------------------------------------------------
-__global__ void k_series_h2l(SeriesParams sp, const FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+__global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
     extern __shared__ double smem_d[];
     const int D = sp.D, T = sp.T, P = sp.P;
     uint8_t *al_s = (uint8_t *)smem_d;
@@ -240,42 +247,108 @@ __global__ void k_series_h2l(SeriesParams sp, const FrontierState *__restrict__ 
     double *A = smem_d + table_bytes(T, D) / 8 + (size_t)w * (T + D * nHmax);
     double *Hs = A + T;
     const int64_t ne = fs->series_count[2];
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; e < ne; e += warps) {
-        const SeriesEntry E = ent[e];
-        const int p = E.p, Tp = sp.tb.Tp[p];
-        const int nH = 2 * p - 1;
-        const double is = sp.inv_s[E.j];
+    const unsigned full = 0xffffffffu;
+    // tiles are taken in list order from a counter: the high-order actions
+    // of the upper levels come first and the cheap leaf-level ones fill in
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(&fs->work, 1ull);
+        const int64_t t0 = (int64_t)__shfl_sync(full, tile, 0) * 32;
+        if (t0 >= ne) break;
+        const int64_t e = t0 + lane;
+        SeriesEntry E;
+        E.q = 0; E.r = 0; E.j = 0; E.p = 0; E.method = 0;
+        if (e < ne) E = ent[e];
+        // ---- orders 1 and 2: one lane per action
+        const bool small = E.p >= 1 && E.p <= 2;
+        double s0 = 0.0, et = 0.0;
+        double is = 0.0;
         const double *mom = sp.rmom + (int64_t)E.r * T;
-        __syncwarp();
-        for (int a = lane; a < Tp; a += 32) {
-            double v = mom[a];
-            for (int k = 0; k < dg_s[a]; ++k) v *= is;
-            A[a] = v;
-        }
-        double t2 = 0.0;
-        if (lane < D) {
-            const double tau = (sp.qcenter[(int64_t)E.q * D + lane] - sp.rcenter[(int64_t)E.r * D + lane]) * is;
-            hermite_polys(tau, nH, &Hs[lane * nH]);
-            t2 = tau * tau;
-        }
-        t2 = warp_sum_d(t2);
-        __syncwarp();
-        const double et = exp(-t2);
-        double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * T;
-        for (int bt = lane; bt < Tp; bt += 32) {
-            const uint8_t *be = al_s + bt * D;
-            double s = 0.0;
-            for (int a = 0; a < Tp; ++a) {
-                const uint8_t *al = al_s + a * D;
-                double pr = A[a];
-                for (int d = 0; d < D; ++d) pr *= Hs[d * nH + al[d] + be[d]];
-                s += pr;
+        const double *cq = sp.qcenter + (int64_t)E.q * D, *cr = sp.rcenter + (int64_t)E.r * D;
+        if (small) {
+            is = sp.inv_s[E.j];
+            double t2 = 0.0;
+            s0 = mom[0];
+            for (int d = 0; d < D; ++d) {
+                const double t = (cq[d] - cr[d]) * is;
+                t2 += t * t;
+                if (E.p == 2) s0 += (mom[1 + d] * is) * (2.0 * t);
             }
-            const double sign = (dg_s[bt] & 1) ? -1.0 : 1.0;
-            atomicAdd(&Bq[bt], sign * sp.tb.inv_fact[bt] * et * s);
+            et = exp(-t2);
         }
-        if (lane == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
+        const long long key = small ? (long long)E.q * sp.nh + E.j : -1 - lane;
+        const bool uniform = __all_sync(full, key == __shfl_sync(full, key, 0));
+        double *Bq = sp.B + (small ? key : 0) * T;
+        if (uniform) {
+            const double v = warp_sum_d(et * s0);
+            const int pmax = __reduce_max_sync(full, E.p);
+            if (lane == 0) {
+                atomicAdd(&Bq[0], v);
+                atomicMax(&sp.pL[key], pmax);
+            }
+            if (pmax == 2) {
+                for (int k = 0; k < D; ++k) {
+                    double u = 0.0;
+                    if (E.p == 2) {
+                        const double t = (cq[k] - cr[k]) * is, ak = mom[1 + k] * is;
+                        const double h1 = 2.0 * t, h2 = 4.0 * t * t - 2.0;
+                        u = -et * (h1 * (s0 - ak * h1) + ak * h2);
+                    }
+                    u = warp_sum_d(u);
+                    if (lane == 0) atomicAdd(&Bq[1 + k], u);
+                }
+            }
+        } else if (small) {
+            atomicAdd(&Bq[0], et * s0);
+            atomicMax(&sp.pL[key], (int)E.p);
+            if (E.p == 2) {
+                for (int k = 0; k < D; ++k) {
+                    const double t = (cq[k] - cr[k]) * is, ak = mom[1 + k] * is;
+                    const double h1 = 2.0 * t, h2 = 4.0 * t * t - 2.0;
+                    atomicAdd(&Bq[1 + k], -et * (h1 * (s0 - ak * h1) + ak * h2));
+                }
+            }
+        }
+        // ---- higher orders: the whole warp per action
+        unsigned big = __ballot_sync(full, E.p > 2);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const SeriesEntry Eb = ent[t0 + src];
+            const int p = Eb.p, Tp = sp.tb.Tp[p];
+            const int nH = 2 * p - 1;
+            const double isb = sp.inv_s[Eb.j];
+            const double *momb = sp.rmom + (int64_t)Eb.r * T;
+            __syncwarp();
+            for (int a = lane; a < Tp; a += 32) {
+                double v = momb[a];
+                for (int k = 0; k < dg_s[a]; ++k) v *= isb;
+                A[a] = v;
+            }
+            double t2 = 0.0;
+            if (lane < D) {
+                const double tau = (sp.qcenter[(int64_t)Eb.q * D + lane] - sp.rcenter[(int64_t)Eb.r * D + lane]) * isb;
+                hermite_polys(tau, nH, &Hs[lane * nH]);
+                t2 = tau * tau;
+            }
+            t2 = warp_sum_d(t2);
+            __syncwarp();
+            const double etb = exp(-t2);
+            double *Bb = sp.B + ((int64_t)Eb.q * sp.nh + Eb.j) * T;
+            for (int bt = lane; bt < Tp; bt += 32) {
+                const uint8_t *be = al_s + bt * D;
+                double sacc = 0.0;
+                for (int a = 0; a < Tp; ++a) {
+                    const uint8_t *al = al_s + a * D;
+                    double pr = A[a];
+                    for (int d = 0; d < D; ++d) pr *= Hs[d * nH + al[d] + be[d]];
+                    sacc += pr;
+                }
+                const double sign = (dg_s[bt] & 1) ? -1.0 : 1.0;
+                atomicAdd(&Bb[bt], sign * sp.tb.inv_fact[bt] * etb * sacc);
+            }
+            if (lane == 0) atomicMax(&sp.pL[(int64_t)Eb.q * sp.nh + Eb.j], p);
+        }
     }
 }
 
@@ -441,7 +514,8 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
             else if (which == 1)
                 k_series_dl<<<grid, wpb * 32, sm, st>>>(sp, fb.series[1], n, pieces[1], pieces[1] + n);
             else {
-                int64_t g = (n + wpb - 1) / wpb;
+                GS_CUDA_TRY(cudaMemsetAsync(&fb.fs->work, 0, sizeof(unsigned long long), st));
+                int64_t g = ((n + 31) / 32 + wpb - 1) / wpb;
                 const int64_t mx = fb.grid_warps / wpb;
                 k_series_h2l<<<(unsigned)(g < 1 ? 1 : (g > mx ? mx : g)), wpb * 32, sm, st>>>(sp, fb.fs, fb.series[2]);
             }

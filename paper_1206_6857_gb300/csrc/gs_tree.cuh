@@ -20,6 +20,7 @@ struct TreeDev {
     double *lo = nullptr, *hi = nullptr, *center = nullptr;   // nodes x D
     float *lo32 = nullptr, *hi32 = nullptr;  // boxes rounded outward to FP32
     double *rad = nullptr;    // half the widest extent
+    float *rad32 = nullptr;   // rad rounded down to FP32
     double *W = nullptr;      // weight sums
     float *wmin = nullptr;    // smallest weight (monochromatic lower bound)
     int32_t *split_dim = nullptr;
