@@ -10,8 +10,10 @@ HBM: `--mode lscv` (default) runs gs_lscv -- the dual-tree sums for all 16
 bandwidths h and their sqrt(2) h companions (32 Gaussian sums: tree build,
 frontier, series, base case, downward pass) and the LSCV reduction;
 `--mode sum` runs gs_sum over the 16 bandwidths only; `--eps 0` selects the
-exhaustive sums instead of the dual tree.  The L2 cache is flushed before
-every timed step (inputs are 12 MB, smaller than L2).
+exhaustive sums instead of the dual tree; `--mode batch` runs gs_sum_batched
+over 256 independent KDE problems (N = M log-uniform in [1e3, 2e5], D in
+2..8, 8 bandwidths each, eps = 1e-2).  The L2 cache is flushed before every
+timed step (inputs are 12 MB, smaller than L2).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded query sample of the same workload instead.
@@ -40,7 +42,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
-    ap.add_argument("--mode", default="lscv", choices=["lscv", "sum"])
+    ap.add_argument("--mode", default="lscv", choices=["lscv", "sum", "batch"])
+    ap.add_argument("--selector", default="rule", choices=["rule", "mlp"],
+                    help="pair selector: Fig. 6's rule or the stored learned network")
+    ap.add_argument("--count", type=int, default=256, help="problems in --mode batch")
+    ap.add_argument("--workers", type=int, default=16, help="concurrent problems in --mode batch")
     ap.add_argument("--eps", type=float, default=None, help="override eps (0 = exhaustive)")
     ap.add_argument("--scale", type=float, default=1.0, help="workload size factor (1 = full)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -237,6 +243,10 @@ def run_gs(args):
         tuned["tuning_seconds"] = time.perf_counter() - t0
         opts = autotune.options(tuned)
 
+    opts, _sel_params = selector_opts(args, opts)
+    if _sel_params is not None and tuned is not None:
+        tuned["selector"] = "mlp"
+
     def step(stats=None):
         if args.mode == "lscv":
             scores["lscv"] = gs.gs_lscv(tq, tw, wl.h, eps, opts=opts, stream=stream, stats=stats)
@@ -355,10 +365,118 @@ def run_gs(args):
         dist.destroy_process_group()
 
 
+def selector_opts(args, opts):
+    """Options with the stored learned selector when --selector mlp."""
+    if args.selector != "mlp":
+        return opts, None
+    from paper_1206_6857_gb300 import gs, selector
+    params = selector.load()
+    o = opts if opts is not None else gs.gs_opts_default()
+    o.selector = gs.GS_SEL_MLP
+    o.selector_params = params.data_ptr()
+    return o, params
+
+
+def run_batch(args):
+    """Many uneven problems per step through gs_sum_batched (one GPU)."""
+    import torch
+    from paper_1206_6857_gb300 import build as gbuild
+    from paper_1206_6857_gb300 import gs
+    from workloads import synth
+    gbuild.build()
+    gs.load()
+    dev = torch.device("cuda", 0)
+    wls = synth.config5(scale=args.scale, count=args.count)
+    eps = wls[0].eps if args.eps is None else args.eps
+    probs = []
+    for wl in wls:
+        q = torch.from_numpy(wl.queries).to(dev)
+        probs.append((q, q, torch.from_numpy(wl.weights).to(dev), wl.h, eps))
+    opts, keep = selector_opts(args, None)
+    units = float(sum(float(wl.M) * wl.N * wl.h.size for wl in wls))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        gs.gs_sum_batched(probs, opts=opts, nworkers=args.workers, stream=stream)
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(dev)
+    sampler = ClockSampler(getattr(props, "pci_bus_id", None))
+    sampler.start()
+    time.sleep(0.3)
+    evs, stats_list = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        st = gs.gs_stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gs.gs_sum_batched(probs, opts=opts, nworkers=args.workers, stream=stream, stats=st)
+        e1.record(stream)
+        evs.append((e0, e1))
+        stats_list.append(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = float(sum(a.elapsed_time(b) for a, b in evs)) / args.steps
+    value = units / (ms / 1e3)
+    s0 = stats_list[-1]
+    ex2_rate, ffma_rate = gs.gs_probe_rates()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = ex2_rate * props.multi_processor_count * sm_mhz * 1e6 / 1e12
+    base_ms = s0.ms_phase[gs.GS_PH_BASE]      # summed over problems (streams overlap)
+    achieved = s0.point_pairs_base / (base_ms / 1e3) / 1e12 if base_ms > 0 else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
+            "frac": achieved / peak if achieved else None, "traffic": None, "kernel": "k_basecase",
+            "peak_basis": "measured %.1f ex2 lanes/SM/clk x %d SMs x %.0f MHz; base-case device time summed "
+                          "over problems on concurrent streams" % (ex2_rate, props.multi_processor_count, sm_mhz)}
+    e2e = None
+    if not args.no_e2e:
+        hosts = [(torch.from_numpy(wl.queries).pin_memory(), torch.from_numpy(wl.weights).pin_memory(), wl.h)
+                 for wl in wls]
+        def e2e_step():
+            ps = []
+            for hq, hw, h in hosts:
+                dq = hq.to(dev, non_blocking=True)
+                ps.append((dq, dq, hw.to(dev, non_blocking=True), h, eps))
+            outs, _ = gs.gs_sum_batched(ps, opts=opts, nworkers=args.workers, stream=stream)
+            return [o.cpu() for o in outs]
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": units / dt, "unit": "evals/s",
+               "h2d_bytes_per_step": int(sum(h[0].numel() * 4 + h[1].numel() * 4 for h in hosts)),
+               "d2h_bytes_per_step": int(sum(wl.M * wl.h.size * 8 for wl in wls)), "ms_per_step": dt * 1e3}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import build as ob
+        ob.build()
+        rates, cores, tot = [], 1, 0.0
+        for wl in wls[:16]:
+            r, dt, cores = oracle_sample_rate(wl, min(wl.M, 20), wl.h)
+            rates.append(r)
+            tot += dt
+        cpu = {"value": float(np.mean(rates)), "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": "20 seeded queries x all refs x 8 bandwidths of each of the first 16 problems (%.1f s)" % tot}
+    cfg = {"workload": "kde_batch_%d_problems_d2-8_n1e3-2e5_8h" % len(wls), "problems": len(wls),
+           "sum_M_N_nh": units, "eps": eps, "mode": "batch", "workers": args.workers, "selector": args.selector,
+           "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"}
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(s0.launches) * args.steps,
+            "stats": s0.as_dict()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "batch":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_batch(args)
     else:
         run_gs(args)
 

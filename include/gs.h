@@ -74,7 +74,10 @@ typedef struct gs_opts {
     double  cost_weight[4]; /* multipliers of the Fig. 6 costs c_DH, c_DL, c_H2L and
                                c_Direct; all 0 -> GS_COST_* defaults below (calibrated
                                to GB300 unit costs); all 1 -> the paper's cost model   */
-    int64_t reserved[4];
+    const float *selector_params;  /* GS_SEL_MLP: DEVICE array of GS_MLP_NPARAM floats (the
+                               pair-selector network, see gs_mlp_train); read during the
+                               call; required for GS_SEL_MLP, ignored otherwise        */
+    int64_t reserved[3];
 } gs_opts;
 
 /* gs_opts.flags */
@@ -118,7 +121,8 @@ typedef struct gs_stats {
     double  eps_traversal;   /* eps left for pruning after the FP32 charge              */
     double  ms_total;        /* device time of the whole call (CUDA events)             */
     double  ms_phase[GS_NPHASE]; /* device time per GS_PH_* phase                       */
-    double  reserved[4];
+    double  ms_series[3];     /* device time of the DH, DL and H2L kernels (within GS_PH_SERIES) */
+    double  reserved[1];
 } gs_stats;
 
 /* Library version string (static storage). */
@@ -243,6 +247,137 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
 int gs_sum_exhaustive_noalloc(const void *queries, int64_t M, const void *refs, const float *weights,
                               int64_t N, int D, int dtype, const double *h, int nh, double *out,
                               void *stream);
+
+/* ---- many problems in one call ------------------------------------------
+ *
+ * One independent Gaussian-sum problem (the arguments of gs_sum). */
+typedef struct gs_problem {
+    const void  *queries;   /* DEVICE, M x D (may equal refs: monochromatic)        */
+    int64_t      M;
+    const void  *refs;      /* DEVICE, N x D                                        */
+    const float *weights;   /* DEVICE, N                                            */
+    int64_t      N;
+    int32_t      D;
+    int32_t      dtype;     /* GS_F32 / GS_F64                                      */
+    const double *h;        /* HOST, nh bandwidths                                  */
+    int32_t      nh;
+    int32_t      pad;
+    double       eps;       /* 0: exhaustive; > 0: dual tree                        */
+    double      *out;       /* DEVICE, M x nh (written)                             */
+} gs_problem;
+
+/*
+ * gs_sum_batched -- nprob independent problems (uneven N, M, D, bandwidths)
+ * with the same options.  Each is computed exactly as gs_sum would; up to
+ * nworkers problems (0 -> 8) run at once on library-owned streams, largest
+ * (M N nh) first.  Work starts after what is already enqueued on `stream`,
+ * and `stream` waits for all of it; the call returns when every out is ready.
+ *   stats   HOST, nullable: counters summed over problems, ms_phase and
+ *           ms_series summed device time, ms_total the batch's wall time
+ *   status  HOST, nullable, nprob: each problem's return code
+ * Returns GS_OK, or the first failing problem's code (its message names it).
+ */
+int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts *opts, int nworkers, void *stream,
+                   gs_stats *stats, int32_t *status);
+
+/* ---- learned pair selector (not in the paper) ---------------------------
+ *
+ * GS_SEL_MLP orders the certified actions of a node pair with a small
+ * network instead of Fig. 6's cost rule.  It is consulted only for pairs
+ * whose finite-difference test failed, for which at least one series
+ * method is certified at some order <= PLIMIT (Lemmas 4-6 against the
+ * Theorem 2 budget, the same FP64 test the rule uses) and whose exhaustive
+ * work N_Q N_R is at least GS_MLP_MIN_WORK: it scores DH, DL, H2L
+ * (each at its smallest certified order) and split / leaf base case, and the
+ * highest-scoring certified action is taken (ties: lowest action number).
+ * Every choice is therefore one the paper's bounds certify and the eps
+ * guarantee is unchanged; only the work done differs.
+ *
+ * Network: 12 inputs -> 64 -> 64 (ReLU) -> 5 scores (FD, DH, DL, H2L, split /
+ * base case), FP32.  Parameters are one array of GS_MLP_NPARAM floats, in this
+ * order: mu[12], sc[12] (input normalisation z = (x - mu) * sc), W1[12][64],
+ * b1[64], W2[64][64], b2[64], W3[64][5], b3[5] (row-major, input index first).
+ * Inference rounds every product and sum to FP32 separately, inputs in
+ * ascending order.
+ *
+ * Features of a pair (Q, R, h), with plog2(x) = e + (m - 1) for x = m 2^e,
+ * m in [1, 2) (0 -> -150, +inf -> 128), all FP32:
+ *   0 plog2(K upper bound at delta_min)      1 plog2(K lower bound at delta_max)
+ *   2 plog2(N_Q)                             3 plog2(N_R)
+ *   4 D                                      5 plog2(FD budget ratio
+ *                                              (1 + token share) / ((K(dmin) - K(dmax)) W / (2 eps G_lb)))
+ *   6 plog2(r_Q / h)                         7 plog2(r_R / h)
+ *   8 plog2(W_R / W)                         9 frontier iteration
+ *  10 plog2(diameter / h)                   11 PLIMIT
+ */
+#define GS_MLP_NIN    12
+#define GS_MLP_NOUT   5
+#define GS_MLP_NPARAM 5341
+/* The network is consulted only for pairs with N_Q * N_R >= GS_MLP_MIN_WORK:
+ * one inference is about 5.3e3 FP32 multiply-adds, so below that the
+ * exhaustive work a decision can save is not worth the inference; such pairs
+ * take Fig. 6's choice among the certified orders (as GS_SEL_RULE does). */
+#define GS_MLP_MIN_WORK (1 << 18)
+
+/*
+ * gs_mlp_forward -- scores of n inputs with the selector's FP32 inference.
+ *   params  DEVICE, GS_MLP_NPARAM floats
+ *   x       DEVICE, n x 12 floats;  logits  DEVICE, n x 5 floats (written)
+ * Returns GS_OK, GS_ERR_ARG or GS_ERR_CUDA; synchronises the stream.
+ */
+int gs_mlp_forward(const float *params, const float *x, int64_t n, float *logits, void *stream);
+
+/*
+ * gs_mlp_loss_grad -- mean weighted softmax cross entropy
+ *   L = (1/n) sum_i s_i (logsumexp(o_i) - o_i[y_i])
+ * and its gradient with respect to every parameter (0 for mu and sc),
+ * computed in FP32 per sample and summed in FP64.
+ *   x DEVICE n x 12, y DEVICE n labels in [0, 5), s DEVICE n weights (NULL: 1)
+ *   grad DEVICE GS_MLP_NPARAM doubles (overwritten), loss DEVICE 1 double (overwritten)
+ * Returns GS_OK, GS_ERR_ARG or GS_ERR_CUDA; synchronises the stream.
+ */
+int gs_mlp_loss_grad(const float *params, const float *x, const int32_t *y, const float *s, int64_t n,
+                     double *grad, double *loss, void *stream);
+
+/*
+ * gs_mlp_train -- trains params (DEVICE, updated in place) with Adam
+ * (beta1 0.9, beta2 0.999, 1e-8) on minibatches of `batch` samples for
+ * `epochs` passes; each epoch visits the samples in the order of the affine
+ * permutation i -> (a i + b) mod n drawn from `seed`.  set_norm != 0 first
+ * sets mu and sc from the data (mean, 1 / max(std, 1e-3)).  epoch_loss
+ * (HOST, epochs doubles, nullable) receives each epoch's mean batch loss.
+ * Returns GS_OK, GS_ERR_ARG, GS_ERR_OOM or GS_ERR_CUDA.
+ */
+int gs_mlp_train(float *params, const float *x, const int32_t *y, const float *s, int64_t n, int epochs,
+                 int batch, double lr, uint64_t seed, int set_norm, double *epoch_loss, void *stream);
+
+/*
+ * gs_selector_samples -- training samples for the selector from one problem
+ * (same arguments as gs_sum, eps > 0; opts->selector is ignored).  The
+ * traversal runs with FD-only decisions and logs every pair; a bottom-up
+ * pass then gives each pair the modelled cost of its cheapest certified
+ * handling (FD-pruned 0; leaf pair: base case or certified series; internal:
+ * its children's costs plus u_pair each, or certified series) with
+ *   unit_cost (HOST, 6): u_pair per frontier pair, u_base per base-case term,
+ *   u_dh, u_dl, u_h2l per FP64 operation slot of each series kernel, u_act
+ *   per series action; DH = u_act + N_Q (T_p (D+1) + 3Dp + 30) u_dh,
+ *   DL = u_act + N_R (T' (D+1) + 3Dp + 30) u_dl with T' = T_p if T_p <= 32
+ *   else 32 ceil(T_p / 32), H2L = u_act + U_p u_h2l with
+ *   U_p = 4D + 30 (p = 1), 16D + 30 (p = 2), T_p^2 (D+1) + T_p D + 3D(2p-1) + 30
+ *   (T_p <= 20, D(2p-1) <= 32), else 32 (ceil(T_p/32) T_p (D+1) + 40).
+ * Every pair the selector would be consulted on (FD test failed, a certified
+ * series method, N_Q N_R >= GS_MLP_MIN_WORK) becomes a sample: x (DEVICE, 12
+ * floats each), y (DEVICE, the cheapest action 1..4), s (DEVICE, nullable:
+ * the pair's regret -- second cheapest minus cheapest certified action --
+ * over the mean regret of the problem's samples).  *n_samples (HOST) gets the
+ * count; more than cap samples returns GS_ERR_CAPACITY with *n_samples set.
+ * model_cost (HOST, 2, nullable): modelled cost of the cheapest policy and of
+ * the FD-only policy over the same pairs.
+ */
+int gs_selector_samples(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
+                        int D, int dtype, const double *h, int nh, double eps, const gs_opts *opts,
+                        const double *unit_cost, float *x, int32_t *y, float *s, int64_t cap,
+                        int64_t *n_samples, double *model_cost, void *stream);
 
 /*
  * gs_probe_rates -- measures this device's throughput, in lanes per SM per

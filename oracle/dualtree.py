@@ -49,6 +49,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import exhaustive as _ex
+from . import mlp as _mlp
 from . import series as _S
 
 # --------------------------------------------------------------------------
@@ -276,6 +277,7 @@ def rpow(r, p):
 FD, DH, DL, H2L, BASE, SPLIT = 0, 1, 2, 3, 4, 5
 SEL_RULE, SEL_MLP, SEL_FD_ONLY, SEL_EXHAUSTIVE = 0, 1, 2, 3
 SQRT2 = 1.4142135623730951
+MLP_MIN_WORK = 2 ** 18      # the network is consulted for pairs with N_Q N_R at least this
 
 
 @dataclass
@@ -285,21 +287,69 @@ class Traversal:
     eps_t: float = 0.0
     rho: float = 0.0
     W: float = 0.0
+    consulted: int = 0          # pairs scored by the selector network
 
 
 COST_WEIGHTS = (32.0, 32.0, 32.0, 1.0)
 
 
+def selector_features(qt, rt, q, r, j, kmin32, kmax32, share_t, kappa, inv_h, W, diam, t, P, D, cnt_q, cnt_r):
+    """The 12 FP32 pair features of the selector network (same operations as
+    the frontier kernel): plog2 of the kernel bounds, node sizes, the FD budget
+    ratio (1 + share) / ((K(dmin) - K(dmax)) kappa / 2), radii / h, W_R / W,
+    diameter / h; D, iteration and PLIMIT as numbers."""
+    f32 = np.float32
+    pl = _mlp.plog2_f32
+    n = q.size
+    X = np.empty((n, _mlp.NIN), f32)
+    X[:, 0] = pl(kmin32)
+    X[:, 1] = pl(kmax32)
+    X[:, 2] = pl(cnt_q[q].astype(f32))
+    X[:, 3] = pl(cnt_r[r].astype(f32))
+    X[:, 4] = f32(D)
+    hk = np.where(0.5 * kappa < 1e37, 0.5 * kappa, 1e37).astype(f32)
+    thr = (1.0 + share_t).astype(f32)
+    with np.errstate(divide="ignore", over="ignore"):
+        X[:, 5] = pl((thr / ((kmin32 - kmax32).astype(f32) * hk).astype(f32)).astype(f32))
+    X[:, 6] = pl((qt.rad[q] * inv_h[j]).astype(f32))
+    X[:, 7] = pl((rt.rad[r] * inv_h[j]).astype(f32))
+    X[:, 8] = pl((rt.W[r] / W).astype(f32))
+    X[:, 9] = f32(t)
+    X[:, 10] = pl((diam * inv_h[j]).astype(f32))
+    X[:, 11] = f32(P)
+    return X
+
+
+def _argmax_certified(scores, certified):
+    """Action 1..4 with the highest score among the certified ones (4 always
+    is); ties go to the lowest action."""
+    n = scores.shape[0]
+    best = np.full(n, -1)
+    bs = np.full(n, -np.inf, np.float32)
+    for a in (1, 2, 3, 4):
+        ok = np.ones(n, bool) if a == 4 else certified[a - 1]
+        take = ok & ((best < 0) | (scores[:, a] > bs))
+        best = np.where(take, a, best)
+        bs = np.where(take, scores[:, a], bs)
+    return best
+
+
 def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None = None,
              selector: int = SEL_RULE, tokens: bool = True, floor_log2: int = -40,
-             w_max: float = None, cost_weight=COST_WEIGHTS):
+             w_max: float = None, cost_weight=COST_WEIGHTS, mlp_params=None):
     """Run the level-synchronous traversal; returns a Traversal whose iters[t]
     holds the frontier (q, r, j) and the decision (method, p, E) of every
     pair in the exact order the GPU processes them.
 
     bestMethod (Fig. 6) compares the paper's costs c_DH = N_Q D^{p+1},
     c_DL = N_R D^{p+1}, c_H2L = D^{2p+1} and c_Direct = D N_Q N_R, each
-    multiplied by its weight in cost_weight (all ones: the paper's model)."""
+    multiplied by its weight in cost_weight (all ones: the paper's model).
+
+    selector SEL_MLP: pairs whose FD test fails, that have a certified
+    series method and whose N_Q N_R is at least MLP_MIN_WORK take the
+    highest-scoring certified action of the selector network (mlp_params,
+    oracle.mlp layout; ties: lowest action), split / base case counting as
+    always certified; smaller such pairs keep the rule's choice."""
     kw = [float(v) for v in cost_weight]
     h = np.asarray(h, np.float64)
     nh = h.size
@@ -316,6 +366,10 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
     c32 = (1.4426950408889634 / ((2.0 * h) * h)).astype(np.float32)   # log2(e) / 2h^2
     inv_h = 1.0 / h
     nQ = qt.nodes
+    d2 = 0.0
+    for d in range(D):
+        d2 = d2 + (rt.hi[0, d] - rt.lo[0, d]) * (rt.hi[0, d] - rt.lo[0, d])
+    diam = math.sqrt(d2)
     fin = np.zeros((nQ, nh))
     tok = np.zeros((nQ, nh))
     est = np.zeros((nQ, nh))
@@ -385,6 +439,7 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
             best_need = np.zeros(pq.size)
             best_E = np.zeros(pq.size)
             x2 = SQRT2 * rQ
+            cert = {}
             for m in (DH, DL, H2L):
                 pm = np.zeros(pq.size, dtype=np.int64)
                 needm = np.zeros(pq.size)
@@ -404,6 +459,7 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
                     needm[ok] = np_[ok]
                     Em[ok] = Ep[ok]
                 found = pm > 0
+                cert[m] = (pm, needm, Em)
                 if m == DH:
                     c = (cnt_q[pq] * np.array([Dpow[p + 1] for p in pm])) * kw[0]
                 elif m == DL:
@@ -417,11 +473,35 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
                 best_need[better] = needm[better]
                 best_E[better] = Em[better]
             c_ex = ((float(D) * cnt_q[pq]) * cnt_r[pr]) * kw[3]
-            series = (~use_fd) & (best_m >= 0) & (best_c <= c_ex)   # ties favour the series method (Fig. 6)
-            method[series] = best_m[series]
-            porder[series] = best_p[series]
-            E[series] = best_E[series]
-            spent = np.where(series, best_need, spent)
+            if selector == SEL_RULE:
+                series = (~use_fd) & (best_m >= 0) & (best_c <= c_ex)   # ties favour the series method (Fig. 6)
+                method[series] = best_m[series]
+                porder[series] = best_p[series]
+                E[series] = best_E[series]
+                spent = np.where(series, best_need, spent)
+            else:
+                contested = (~use_fd) & ((cert[DH][0] > 0) | (cert[DL][0] > 0) | (cert[H2L][0] > 0))
+                consult = contested & (cnt_q[pq] * cnt_r[pr] >= MLP_MIN_WORK)
+                # small pairs keep Fig. 6's choice
+                series = contested & ~consult & (best_m >= 0) & (best_c <= c_ex)
+                method[series] = best_m[series]
+                porder[series] = best_p[series]
+                E[series] = best_E[series]
+                spent = np.where(series, best_need, spent)
+                idx = np.flatnonzero(consult)
+                out.consulted += idx.size
+                if idx.size:
+                    X = selector_features(qt, rt, pq[idx], pr[idx], pj[idx], kmin32[idx], kmax32[idx],
+                                          (share if tokens else np.zeros(ng))[gid[idx]], kappa[gid[idx]], inv_h,
+                                          W, diam, t, P, D, cnt_q, cnt_r)
+                    sc = _mlp.infer_f32(mlp_params, X)
+                    chosen = _argmax_certified(sc, [cert[a][0][idx] > 0 for a in (1, 2, 3)])
+                    for a in (1, 2, 3):
+                        sel = idx[chosen == a]
+                        method[sel] = a
+                        porder[sel] = cert[a][0][sel]
+                        E[sel] = cert[a][2][sel]
+                        spent[sel] = cert[a][1][sel]
         # Fig. 7's token update over the whole group: pruned pairs pay their
         # need (negative needs bank the excess), base cases bank W_R, splits
         # leave the token alone

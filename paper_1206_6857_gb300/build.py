@@ -26,7 +26,7 @@ def _nvcc():
 
 # translation units whose FP64 arithmetic must not be contracted into FMAs
 # (decisions there are reproduced bit for bit by a CPU evaluation)
-NO_FMA = {"gs_frontier.cu", "gs_tree.cu"}
+NO_FMA = {"gs_frontier.cu", "gs_tree.cu", "gs_mlp.cu"}
 
 
 def sources():

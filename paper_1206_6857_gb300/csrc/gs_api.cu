@@ -153,9 +153,11 @@ int gs_opts_default(gs_opts *o) {
     return GS_OK;
 }
 
-static int sum_impl(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
-                    int dtype, const double *h, int nh, double eps, double *out, const gs_opts *opts, void *stream,
-                    gs_stats *stats, TraceOut *trace) {
+}  // extern "C"
+
+int gs::sum_impl(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
+                 int dtype, const double *h, int nh, double eps, double *out, const gs_opts *opts, void *stream,
+                 gs_stats *stats, TraceOut *trace, PairLog *log) {
     g_err[0] = 0;
     int rc = check_common(queries, M, refs, weights, N, D, dtype, h, nh, eps, out);
     if (rc) return rc;
@@ -179,6 +181,10 @@ static int sum_impl(const void *queries, int64_t M, const void *refs, const floa
         }
     if (o.selector < GS_SEL_RULE || o.selector > GS_SEL_EXHAUSTIVE) {
         set_error("unknown selector %d", o.selector);
+        return GS_ERR_ARG;
+    }
+    if (o.selector == GS_SEL_MLP && !o.selector_params) {
+        set_error("GS_SEL_MLP needs gs_opts.selector_params (the trained network)");
         return GS_ERR_ARG;
     }
     if (o.floor_log2 < -1000 || o.floor_log2 > -1) {
@@ -213,13 +219,15 @@ static int sum_impl(const void *queries, int64_t M, const void *refs, const floa
         }
         if (rc == GS_OK && stats) stats->point_pairs_base = M * N * nh;
     } else {
-        rc = dualtree_sum(queries, M, refs, weights, N, D, dtype, h, nh, eps, out, o, cx, ing, trace, &status);
+        rc = dualtree_sum(queries, M, refs, weights, N, D, dtype, h, nh, eps, out, o, cx, ing, trace, &status, log);
     }
     cudaFreeAsync(ing, st);
     if (rc == GS_OK) rc = status_to_code(status);
     if (rc == GS_OK && stats) cx.finish();
     return rc;
 }
+
+extern "C" {
 
 int gs_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N,
            int D, int dtype, const double *h, int nh, double eps, double *out,

@@ -375,8 +375,7 @@ static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const Me
         const size_t ns = merged_x2(DP, Q) ? 2 * NT : NT;                                            \
         const size_t sm = (size_t)kMW * (2 * kBlk * (Q) * 32 + 2 * lmax * ns) * sizeof(float);     \
         if (sm > 220 * 1024) return GS_ERR_UNSUPPORTED;                                             \
-        cudaFuncSetAttribute(k_basecase_merged<DP, Q, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)sm);                                                              \
+        allow_max_smem((const void *)k_basecase_merged<DP, Q, A>);                                   \
         k_basecase_merged<DP, Q, A><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq, lmax);    \
     } while (0)
     if (anch) {

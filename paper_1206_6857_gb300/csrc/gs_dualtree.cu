@@ -118,7 +118,7 @@ static int alloc_bufs(FrontierBufs &fb, int64_t nodesQ, int nh, const double *h,
 
 int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
                  int dtype, const double *h, int nh, double eps, double *out, const gs_opts &o, CallCtx &cx,
-                 Ingest *ing, TraceOut *trace, unsigned *status_out) {
+                 Ingest *ing, TraceOut *trace, unsigned *status_out, PairLog *log) {
     cudaStream_t st = cx.st;
     const int L = o.leaf_size;
     if (L < 2 || L > 128) {
@@ -180,6 +180,8 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
     in.eps = eps;
 
     for (int k = 0; k < 4; ++k) in.cost_w[k] = o.cost_weight[k];
+    in.mlp = o.selector_params;
+    in.log = log;
     const int64_t lq = 1ll << qt.depth;
     FrontierBufs fb;
     fb.grid_warps = sm_count() * 64;

@@ -28,8 +28,11 @@
 // CPU evaluation of the same formulas.
 #include <math.h>
 
+#include <mutex>
+
 #include "gs_frontier.cuh"
 #include "gs_internal.h"
+#include "gs_mlp.cuh"
 #include "gs_tree.cuh"
 
 namespace gs {
@@ -85,6 +88,14 @@ struct FrontierParams {
     double cw[4];         // cost weights of c_DH, c_DL, c_H2L, c_Direct
     // weighted bestMethod costs of this iteration, for node sizes floor(n / 2^depth) + {0, 1}
     double cDH[2][17], cDL[2][17], cH2L[17], cex[2][2];
+    const float *mlp;     // selector network parameters (learned ordering)
+    // pair log (training data of the selector), indexed by global pair id
+    float *lfeat;
+    int8_t *lpc;
+    int32_t *lnq, *lnr;
+    int64_t *lpar;
+    const int64_t *pid;   // parent id of each pair of this iteration (null at the root)
+    int64_t log_base;     // id of this iteration's first pair
     float c32[64];        // log2(e) / 2h_j^2 rounded to FP32
 };
 
@@ -130,6 +141,9 @@ __device__ __forceinline__ KBounds kernel_bounds(const FrontierParams &fp, int64
 // ---------------------------------------------------------------------------
 // K1: decisions
 // ---------------------------------------------------------------------------
+// MODE 0: rule (Fig. 6) or FD only; MODE 1: learned ordering of the
+// certified actions; MODE 2: FD-only decisions with every pair logged.
+template <int MODE>
 __global__ void __launch_bounds__(256)
 k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ groups,
                const int32_t *__restrict__ pr, uint8_t *__restrict__ dec, int32_t *__restrict__ cnt,
@@ -140,6 +154,12 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t trace_base = fs->trace_count;
     __shared__ float s_tab[8][kTab];
+    __shared__ __align__(16) float s_w[MODE == 1 ? kMlpParams + 3 : 2];
+    if constexpr (MODE == 1) {
+        for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) s_w[i] = fp.mlp[i];
+        __syncthreads();
+    }
+    const double diam = fs->diam;
     for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < ng; g += warps) {
         const Group G = groups[g];
         const int64_t q = G.q;
@@ -188,10 +208,16 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         // above (1 + share)(1 + 2^-20) rejects only bounds the FP64 test
         // rejects.  Per group and order: hk = F_p kappa, gdl = hk r_Q^p (DL),
         // A = r_Q^p and B = C(D+p-1, D) tail_p (H2L).
-        const bool series = (fp.selector == GS_SEL_RULE || fp.selector == GS_SEL_MLP) && fp.P >= 1;
+        const bool series = (MODE == 2 ? fp.selector != GS_SEL_EXHAUSTIVE
+                                        : (fp.selector == GS_SEL_RULE || fp.selector == GS_SEL_MLP)) &&
+                            fp.P >= 1;
         const float thrL = __fmul_ru(__double2float_ru(1.0 + share_t), 0x1.00001p+0f);
         const float invhd = __double2float_rd(invh);
         float *tab = s_tab[threadIdx.x >> 5];
+        // per-group feature constants of the selector
+        const float hkf = (float)(0.5 * kappa < 1e37 ? 0.5 * kappa : 1e37);
+        const float thrf = (float)(1.0 + share_t);
+        const float lhd = plog2_f((float)(diam * invh));
         __syncwarp();
         if (series && lane >= 1 && lane <= fp.P) {
             const int p = lane;
@@ -234,13 +260,18 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     s_est = s_est + (WR * (kmin + kmax)) * 0.5;
                 }
             }
-            if (!decided && series) {
+            const int64_t crn = node_size(fp.rn, fp.r_depth, r);
+            // learned ordering: the network is consulted where the pair's
+            // exhaustive work is large enough to repay its inference; other
+            // pairs take the rule
+            const bool big = MODE == 1 && cq * crn >= (int64_t)GS_MLP_MIN_WORK;
+            if ((MODE == 0 || (MODE == 1 && !big)) && !decided && series) {
                 // bestMethod (Fig. 6).  Costs grow with p, so a method whose
                 // cost already reaches the best so far (or exceeds c_Direct)
                 // cannot be chosen and its remaining bounds are skipped; the
                 // choice is the same as evaluating every bound.  Costs are
                 // positive, so their order is that of their bit patterns.
-                const int ir = (int)(node_size(fp.rn, fp.r_depth, r) - (fp.rn >> fp.r_depth));
+                const int ir = (int)(crn - (fp.rn >> fp.r_depth));
                 const long long c_ex = __double_as_longlong(fp.cex[iq][ir]);
                 long long best_c = 0x7ff0000000000000ll;   // +inf
                 double best_need = 0.0;
@@ -298,6 +329,103 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     pord = best_p;
                     spent = best_need;
                     decided = true;
+                }
+            }
+            if (MODE == 2 || big) {
+                // smallest certified order of each series method (no cost cut-offs)
+                const bool fd_pruned = decided;
+                int pc3[3] = {0, 0, 0};
+                double need3[3] = {0.0, 0.0, 0.0};
+                if (!decided && series) {
+                    const float rRd = __fmul_rd(fp.rrad32[r], invhd);
+                    const float srd = __fmul_rd(rRd, 0x1.6a09e6p+0f);
+                    const double base = WR * (double)e4f;
+                    const double rR = fp.rrad[r] * invh;
+                    const double sr = kSqrt2 * rR;
+                    const double allot = fp.tokens ? WR * share : 0.0;
+                    for (int m = M_DH; m <= M_H2L; ++m) {
+                        float pw = 1.f;
+                        for (int p = 1; p <= fp.P; ++p) {
+                            float lb;
+                            if (m == M_DH) {
+                                pw = __fmul_rd(pw, rRd);
+                                lb = __fmul_rd(__fmul_rd(e4f, tab[p]), pw);
+                            } else if (m == M_DL) {
+                                lb = __fmul_rd(e4f, tab[17 + p]);
+                            } else {
+                                pw = __fmul_rd(pw, srd);
+                                lb = __fmul_rd(__fmul_rd(e4f, tab[p]), __fadd_rd(tab[34 + p], __fmul_rd(pw, tab[51 + p])));
+                            }
+                            if (lb > thrL) continue;
+                            double Ep;
+                            if (m == M_DH) {
+                                Ep = (base * fp.F[p]) * rpow(rR, p);
+                            } else if (m == M_DL) {
+                                Ep = (base * fp.F[p]) * rpow(rQ, p);
+                            } else {
+                                const double x2 = kSqrt2 * rQ;
+                                const double tail = (x2 <= 1.0) ? 1.0 : rpow(x2, p - 1);
+                                Ep = (base * fp.F[p]) * (rpow(rQ, p) + (rpow(sr, p) * fp.BT[p]) * tail);
+                            }
+                            const double np_ = Ep * kappa - WR;
+                            if (np_ <= allot) {
+                                pc3[m - 1] = p;
+                                need3[m - 1] = np_;
+                                break;
+                            }
+                        }
+                    }
+                }
+                const bool contested = (pc3[0] | pc3[1] | pc3[2]) != 0;
+                const int64_t cr = crn;
+                const bool consult = contested;
+                float xf[kMlpIn];
+                if (!fd_pruned && (MODE == 2 || consult)) {
+                    // pair features: kernel bounds, node sizes, D, FD budget ratio,
+                    // radii / h, W_R / W, level, diameter / h, PLIMIT
+                    xf[0] = plog2_f(kmin32);
+                    xf[1] = plog2_f(kmax32);
+                    xf[2] = plog2_f((float)cq);
+                    xf[3] = plog2_f((float)cr);
+                    xf[4] = (float)fp.D;
+                    xf[5] = plog2_f(__fdiv_rn(thrf, __fmul_rn(__fsub_rn(kmin32, kmax32), hkf)));
+                    xf[6] = plog2_f((float)rQ);
+                    xf[7] = plog2_f((float)(fp.rrad[r] * invh));
+                    xf[8] = plog2_f((float)(WR / Wtot));
+                    xf[9] = (float)fp.t;
+                    xf[10] = lhd;
+                    xf[11] = (float)fp.P;
+                }
+                if constexpr (MODE == 1) {
+                    int best = 4;
+                    if (consult) {
+                        // highest-scoring certified action; split / base case is always certified
+                        float o[kMlpOut];
+                        mlp_infer(s_w, xf, o);
+                        best = -1;
+                        for (int a = 1; a <= 4; ++a) {
+                            const bool cert = a == 4 || pc3[a - 1] > 0;
+                            if (cert && (best < 0 || o[a] > o[best])) best = a;
+                        }
+                    }
+                    if (best <= 3) {
+                        method = best;
+                        pord = pc3[best - 1];
+                        spent = need3[best - 1];
+                        decided = true;
+                    }
+                } else {
+                    const int64_t gid = fp.log_base + G.off + k;
+                    fp.lnq[gid] = (int32_t)cq;
+                    fp.lnr[gid] = (int32_t)cr;
+                    fp.lpar[gid] = fp.pid ? fp.pid[G.off + k] : -1;
+                    int8_t *pc = fp.lpc + 4 * gid;
+                    pc[0] = (int8_t)pc3[0];
+                    pc[1] = (int8_t)pc3[1];
+                    pc[2] = (int8_t)pc3[2];
+                    pc[3] = (int8_t)(fd_pruned ? LOG_FD : (method == M_BASE ? LOG_BASE : LOG_SPLIT));
+                    if (!fd_pruned)
+                        for (int i = 0; i < kMlpIn; ++i) fp.lfeat[kMlpIn * gid + i] = xf[i];
                 }
             }
             if (method == M_FD || (method >= M_DH && method <= M_H2L)) s_paid = s_paid + spent;
@@ -450,6 +578,8 @@ struct EmitOut {
     Group *base_groups;
     int32_t *base_r;
     SeriesEntry *series[3];
+    int64_t *pid_next;    // pair log: parent id of every child pair (null when not logging)
+    int64_t log_base;
 };
 
 __global__ void __launch_bounds__(256)
@@ -485,18 +615,25 @@ k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, const Group *__re
             const int32_t r = valid ? pr[G.off + k] : 0;
             if (isS) {
                 const int rank = run_s + __popc(bS & lt_mask);
+                const int64_t gid = eo.log_base + G.off + k;
                 if (!q_leaf && !r_leaf) {
                     for (int cc = 0; cc < 2; ++cc) {
                         const int64_t p = o_pairs + (int64_t)cc * per_child + 2 * rank;
                         eo.pr_next[p] = 2 * r + 1;
                         eo.pr_next[p + 1] = 2 * r + 2;
+                        if (eo.pid_next) eo.pid_next[p] = eo.pid_next[p + 1] = gid;
                     }
                 } else if (q_leaf) {
                     const int64_t p = o_pairs + 2 * rank;
                     eo.pr_next[p] = 2 * r + 1;
                     eo.pr_next[p + 1] = 2 * r + 2;
+                    if (eo.pid_next) eo.pid_next[p] = eo.pid_next[p + 1] = gid;
                 } else {
-                    for (int cc = 0; cc < 2; ++cc) eo.pr_next[o_pairs + (int64_t)cc * per_child + rank] = r;
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int64_t p = o_pairs + (int64_t)cc * per_child + rank;
+                        eo.pr_next[p] = r;
+                        if (eo.pid_next) eo.pid_next[p] = gid;
+                    }
                 }
             }
             if (isB) eo.base_r[o_base + run_b + __popc(bB & lt_mask)] = r;
@@ -551,7 +688,8 @@ __global__ void k_front_advance(FrontierState *fs, int t) {
 // initial frontier: one group (root, j) with the single pair (root, root) per
 // bandwidth; eps for the traversal after the FP32 base-case charge.
 __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int nh, const double *rW,
-                             Ingest *ing, int64_t N, int D, int floor_log2, double eps) {
+                             const double *rlo, const double *rhi, Ingest *ing, int64_t N, int D, int floor_log2,
+                             double eps) {
     const int j = threadIdx.x;
     if (j < nh) {
         Group g;
@@ -573,6 +711,9 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
         fs->floorW = W * ldexp(1.0, floor_log2);
         fs->ngroups[0] = nh;
         fs->npairs[0] = nh;
+        double d2 = 0.0;
+        for (int d = 0; d < D; ++d) d2 = d2 + (rhi[d] - rlo[d]) * (rhi[d] - rlo[d]);
+        fs->diam = sqrt(d2);
         if (!(fs->eps_t > 0.5 * eps)) atomicOr(&ing->status, ST_EPS);
     }
 }
@@ -581,12 +722,14 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
 // host driver
 // ---------------------------------------------------------------------------
 static bool g_consts_ready[64] = {false};
+static std::mutex g_consts_mu;
 
 // exp2 coefficients ln2^n / n! built in FP64 by repeated multiplication,
 // then rounded to FP32; uploaded once per device
 static int ensure_consts() {
     int dev = 0;
     cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_consts_mu);
     if (dev >= 0 && dev < 64 && g_consts_ready[dev]) return GS_OK;
     float c[8];
     double t = 1.0;
@@ -665,15 +808,17 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.Dpow[0] = 1.0;
     for (int k = 1; k < 34; ++k) fp.Dpow[k] = fp.Dpow[k - 1] * (double)D;
 
-    k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, (Ingest *)in.ing, in.rt->n,
-                                   in.D, in.floor_log2, in.eps);
+    k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, in.rt->lo, in.rt->hi,
+                                   (Ingest *)in.ing, in.rt->n, in.D, in.floor_log2, in.eps);
     cx.launches += 1;
     if ((rc = cx.check("k_front_init"))) return rc;
     const int T = in.qt->depth > in.rt->depth ? in.qt->depth : in.rt->depth;
     int cur = 0;
     int64_t ng = in.nh, npairs = in.nh;
     int64_t base_count = 0, bgroups = 0, ser_count[3] = {0, 0, 0};
+    int64_t log_base = 0;
     const int max_grid = fb.grid_warps / 8;
+    fp.mlp = in.mlp;
     for (int t = 0; t <= T && ng > 0; ++t) {
         fp.t = t;
         fp.q_depth = t < in.qt->depth ? t : in.qt->depth;
@@ -697,9 +842,39 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         if ((rc = grow(&fb.dec, &fb.cap_pairs, npairs, 0, st))) return rc;
         if ((rc = grow(&fb.geo, &fb.cap_geo, 3 * npairs, 0, st))) return rc;
         fp.geo = fb.geo;
+        PairLog *lg = in.log;
+        if (lg) {
+            // the pair log grows by this iteration's pairs
+            if (t + 1 >= 80) {
+                set_error("pair log: too many iterations");
+                return GS_ERR_ARG;
+            }
+            const int64_t need = log_base + npairs, keep = log_base;
+            if (need > lg->cap) {
+                const int64_t nc = need + need / 2 > 2 * lg->cap ? need + need / 2 : 2 * lg->cap;
+                int64_t c1 = lg->cap * kMlpIn, c2 = lg->cap * 4, c3 = lg->cap, c4 = lg->cap, c5 = lg->cap;
+                if ((rc = grow(&lg->feat, &c1, nc * kMlpIn, keep * kMlpIn, st))) return rc;
+                if ((rc = grow(&lg->pc, &c2, nc * 4, keep * 4, st))) return rc;
+                if ((rc = grow(&lg->nq, &c3, nc, keep, st))) return rc;
+                if ((rc = grow(&lg->nr, &c4, nc, keep, st))) return rc;
+                if ((rc = grow(&lg->par, &c5, nc, keep, st))) return rc;
+                lg->cap = c5;
+            }
+            lg->iter_off[t] = log_base;
+            fp.lfeat = lg->feat; fp.lpc = lg->pc; fp.lnq = lg->nq; fp.lnr = lg->nr; fp.lpar = lg->par;
+            fp.pid = t == 0 ? nullptr : lg->pid[cur];
+            fp.log_base = log_base;
+        }
         const int grid = (int)((ng + 7) / 8 < max_grid ? (ng + 7) / 8 : max_grid);
-        k_front_decide<<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
-                                             fb.trace_cap);
+        if (lg)
+            k_front_decide<2><<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
+                                                    fb.trace_cap);
+        else if (in.selector == GS_SEL_MLP)
+            k_front_decide<1><<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
+                                                    fb.trace_cap);
+        else
+            k_front_decide<0><<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
+                                                    fb.trace_cap);
         if ((rc = cx.check("k_front_decide"))) return rc;
         k_cols_partial<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial);
         k_cols_scan_partials<<<1, kColTB, 0, st>>>(fb.fs, fb.partial);
@@ -727,12 +902,23 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         eo.base_groups = fb.base_groups;
         eo.base_r = fb.base_r;
         for (int m = 0; m < 3; ++m) eo.series[m] = fb.series[m];
+        eo.pid_next = nullptr;
+        eo.log_base = log_base;
+        if (lg) {
+            if ((rc = grow(&lg->pid[cur ^ 1], &lg->cap_pid[cur ^ 1], tot[C_PAIRS], 0, st))) return rc;
+            eo.pid_next = lg->pid[cur ^ 1];
+        }
         k_front_emit<<<grid, 256, 0, st>>>(fb.fs, t, fp.q_leaf, fp.r_leaf, fb.groups[cur], fb.pr[cur], fb.dec,
                                            fb.cnt, fb.off, eo);
         k_front_advance<<<1, 1, 0, st>>>(fb.fs, t);
         cx.launches += 3;
         if ((rc = cx.check("k_front_emit"))) return rc;
         ng = tot[C_GROUPS];
+        log_base += npairs;
+        if (lg) {
+            lg->niter = t + 1;
+            lg->iter_off[t + 1] = log_base;
+        }
         npairs = tot[C_PAIRS];
         base_count += tot[C_BASE];
         bgroups += tot[C_BGROUPS];

@@ -39,6 +39,7 @@ struct FrontierState {
     unsigned long long method_count[6];
     double eps_t, rho, Wtot, floorW;
     unsigned long long work;    // tile counter of dynamically scheduled kernels (zeroed before each)
+    double diam;                // diagonal of the reference root box
     int32_t overflow;
     int32_t pad;
 };

@@ -58,6 +58,19 @@ struct CallCtx {
         open_phase = ph;
     }
     void end() { phase(-1); }
+    // Time one launch into stats->ms_series[slot]: mark(slot) before it,
+    // mark(-1) after.  No-op without stats.
+    static constexpr int kMaxTimers = 16;
+    cudaEvent_t tev[kMaxTimers];
+    int tslot[kMaxTimers];
+    int ntev = 0;
+    void mark(int slot) {
+        if (!stats || ntev >= kMaxTimers) return;
+        if (cudaEventCreate(&tev[ntev]) != cudaSuccess) return;
+        cudaEventRecord(tev[ntev], st);
+        tslot[ntev] = slot;
+        ++ntev;
+    }
     // After the stream has been synchronised: fold event pairs into stats.
     void finish() {
         if (!stats) return;
@@ -70,13 +83,33 @@ struct CallCtx {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, ev[0], ev[nev - 1]) == cudaSuccess) stats->ms_total = ms;
         }
+        for (int i = 0; i + 1 < ntev; ++i) {
+            if (tslot[i] < 0 || tslot[i] >= 3) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, tev[i], tev[i + 1]) == cudaSuccess) stats->ms_series[tslot[i]] += ms;
+        }
         stats->launches = launches;
         stats->launches_base = launches_base;
     }
     ~CallCtx() {
         for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+        for (int i = 0; i < ntev; ++i) cudaEventDestroy(tev[i]);
     }
 };
+
+// Let `fn` launch with up to the device's opt-in maximum of dynamic shared
+// memory.  The attribute is per function and shared by every host thread, so
+// it is always set to that same maximum (never to one launch's size, which a
+// concurrent caller could lower between another's set and launch).
+inline cudaError_t allow_max_smem(const void *fn) {
+    int dev = 0, mx = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+    return e;
+}
 
 // Host-side error reporting (thread-local message).
 void set_error(const char *fmt, ...);
@@ -101,6 +134,22 @@ int exhaustive_sum(const void *queries, int64_t M, const void *refs, const float
                    double *out, CallCtx &cx);
 
 // ---- dual-tree path -------------------------------------------------------
+// Per-pair record of a logged traversal (training data of the pair
+// selector), indexed by global pair id (iterations in order, pairs of an
+// iteration in frontier order).  Arrays grow between iterations.
+struct PairLog {
+    float *feat = nullptr;        // 12 features (pairs whose FD test failed)
+    int8_t *pc = nullptr;         // smallest certified order of DH, DL, H2L (0: none); kind
+    int32_t *nq = nullptr, *nr = nullptr;
+    int64_t *par = nullptr;       // parent pair id (-1 at the root iteration)
+    int64_t cap = 0;
+    int64_t *pid[2] = {nullptr, nullptr};   // parent id of each pair slot, per frontier buffer
+    int64_t cap_pid[2] = {0, 0};
+    int64_t iter_off[80] = {0};   // first pair id of each iteration; iter_off[niter] = total
+    int niter = 0;
+};
+enum : int { LOG_FD = 0, LOG_BASE = 1, LOG_SPLIT = 2 };
+
 struct TraversalIn {
     const TreeDev *qt = nullptr, *rt = nullptr;
     const Ingest *ing = nullptr;
@@ -109,6 +158,8 @@ struct TraversalIn {
     int D = 0, nh = 0, P = 0, selector = 0, tokens = 1, mono = 0, floor_log2 = -40;
     double eps = 0.0;
     double cost_w[4] = {GS_COST_DH, GS_COST_DL, GS_COST_H2L, GS_COST_DIRECT};
+    const float *mlp = nullptr;   // selector network (GS_SEL_MLP)
+    PairLog *log = nullptr;       // log every pair (FD-only decisions)
 };
 
 struct FrontierBufs {
@@ -166,7 +217,12 @@ struct TraceOut {
 
 int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
                  int dtype, const double *h, int nh, double eps, double *out, const gs_opts &o, CallCtx &cx,
-                 Ingest *ing, TraceOut *trace, unsigned *status_out);
+                 Ingest *ing, TraceOut *trace, unsigned *status_out, PairLog *log = nullptr);
+
+// gs_sum with its options checked; trace and log are optional.
+int sum_impl(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
+             int dtype, const double *h, int nh, double eps, double *out, const gs_opts *opts, void *stream,
+             gs_stats *stats, TraceOut *trace, PairLog *log = nullptr);
 
 // Instruction-rate probe (see gs_probe_rates).
 int probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, cudaStream_t st);

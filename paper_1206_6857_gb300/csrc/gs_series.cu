@@ -22,6 +22,10 @@ namespace gs {
 constexpr int kSerTB = 128;
 constexpr int kMaxT = 1024;      // series terms supported by the DL / H2L kernels
 constexpr int kMaxDP = 64;       // D * (orders) table entries per point
+constexpr int kLaneT = 20;       // H2L lane-per-action path: at most kLaneT terms
+constexpr int kDlLane = 32;      // DL lane-per-reference path: at most kDlLane coefficients
+constexpr int kDlStride = 33;    //   accumulator row stride (doubles)
+constexpr int kLaneH = 32;       //   and kLaneH Hermite values (D (2p - 1))
 
 struct SeriesParams {
     int D, nh, P, T;
@@ -162,9 +166,13 @@ __global__ void k_series_dh(SeriesParams sp, const SeriesEntry *__restrict__ ent
 }
 
 // ---------------------------------------------------------------------------
-// DL: one warp per piece of kChunk references, lanes over the coefficients b;
-// the piece's references in groups of 32 have their Hermite tables built
-// cooperatively in shared memory; partial coefficients are added atomically
+// DL: one warp per piece of kChunk references.  Up to kDlLane coefficients:
+// lanes over references, each adding its references' contributions to every
+// coefficient in its own row of a shared accumulator (row stride 33 doubles,
+// so both the row-wise adds and the column sums are conflict-free), then
+// lanes over coefficients sum the 32 rows.  More coefficients: lanes over the
+// coefficients b, the piece's references in groups of 32 with their Hermite
+// tables built cooperatively.  Partial coefficients are added atomically.
 // ---------------------------------------------------------------------------
 __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent, int64_t ne,
                             const long long *__restrict__ off, const long long *__restrict__ npieces) {
@@ -175,8 +183,9 @@ __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent
     load_tables(sp.tb, D, al_s, dg_s);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int DPp = D * P;
-    double *Hr = smem_d + table_bytes(T, D) / 8 + (size_t)w * (32 * DPp + 32);
+    double *Hr = smem_d + table_bytes(T, D) / 8 + (size_t)w * (32 * DPp + 32 + 32 * kDlStride);
     double *we = Hr + 32 * DPp;
+    double *acc_s = we + 32;   // [32 lanes][kDlStride]
     const long long C = *npieces;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (long long c = blockIdx.x * (int64_t)(blockDim.x >> 5) + w; c < C; c += warps) {
@@ -190,6 +199,35 @@ __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent
         const int64_t rb = level_begin(sp.rn, rd, ri) + (c - off[e]) * kChunk;
         const int64_t re = min(rb + kChunk, level_begin(sp.rn, rd, ri + 1));
         double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * T;
+        if (Tp <= kDlLane) {
+            double *row = acc_s + lane * kDlStride;
+            double *H = Hr + lane * DPp;
+            for (int bt = 0; bt < Tp; ++bt) row[bt] = 0.0;
+            for (int64_t pos = rb + lane; pos < re; pos += 32) {
+                double v2 = 0.0;
+                for (int d = 0; d < D; ++d) {
+                    const double v = (coord(sp.rxs, sp.dtype, pos, D, d) - cQ[d]) * is;
+                    hermite_polys(v, p, &H[d * p]);
+                    v2 += v * v;
+                }
+                const double wr = (double)sp.w[sp.rperm[pos]] * exp(-v2);
+                for (int bt = 0; bt < Tp; ++bt) {
+                    const uint8_t *be = al_s + bt * D;
+                    double pr = wr;
+                    for (int d = 0; d < D; ++d) pr *= H[d * p + be[d]];
+                    row[bt] += pr;
+                }
+            }
+            __syncwarp();
+            for (int bt = lane; bt < Tp; bt += 32) {
+                double sum = 0.0;
+                for (int l = 0; l < 32; ++l) sum += acc_s[l * kDlStride + bt];
+                atomicAdd(&Bq[bt], sum * sp.tb.inv_fact[bt]);
+            }
+            __syncwarp();
+            if (lane == 0) atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
+            continue;
+        }
         for (int b0 = 0; b0 < Tp; b0 += 32) {
             const int bt = b0 + lane;
             const uint8_t *be = al_s + (bt < Tp ? bt : 0) * D;
@@ -231,10 +269,11 @@ __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent
 //   b = 0:    s_0   = A_0 + sum_i A_{e_i} H_1(t_i),
 //   b = e_k:  s_e_k = H_1(t_k) (s_0 - A_{e_k} H_1(t_k)) + A_{e_k} H_2(t_k),
 // B_b += (-1)^|b| e^{-|t|^2} s_b.  When all 32 actions of a tile add into
-// the same (Q, h) they are summed across the warp first.  Higher orders are
-// done one at a time by the whole warp: lanes over b, loop over a, with A_a
-// and the 1-D Hermite polynomials of t = (x_Q - x_R)/s (orders 0 .. 2p-2)
-// in shared memory.
+// the same (Q, h) they are summed across the warp first.  Middle orders
+// (at most kLaneT terms) also take one lane each, with A_a and the 1-D
+// Hermite polynomials of t = (x_Q - x_R)/s (orders 0 .. 2p-2) in a
+// lane-interleaved shared buffer.  Higher orders are done one at a time by
+// the whole warp: lanes over b, loop over a.
 // ---------------------------------------------------------------------------
 __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
     extern __shared__ double smem_d[];
@@ -246,6 +285,8 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
     const int nHmax = 2 * P - 1;
     double *A = smem_d + table_bytes(T, D) / 8 + (size_t)w * (T + D * nHmax);
     double *Hs = A + T;
+    double *lanebuf = smem_d + table_bytes(T, D) / 8 + (size_t)(blockDim.x >> 5) * (T + D * nHmax) +
+                      (size_t)w * 32 * (kLaneT + kLaneH);
     const int64_t ne = fs->series_count[2];
     const unsigned full = 0xffffffffu;
     // tiles are taken in list order from a counter: the high-order actions
@@ -309,8 +350,50 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
                 }
             }
         }
+        // ---- middle orders (T_p <= kLaneT, D (2p-1) <= kLaneH): one lane per
+        // action, its A_a and Hermite values in a lane-interleaved buffer
+        const bool mid = E.p > 2 && sp.tb.Tp[E.p] <= kLaneT && D * (2 * E.p - 1) <= kLaneH;
+        if (mid) {
+            const int p = E.p, Tp = sp.tb.Tp[p], nH = 2 * p - 1;
+            const double ism = sp.inv_s[E.j];
+            double *Al = lanebuf + lane, *Hl = lanebuf + kLaneT * 32 + lane;
+            for (int a = 0; a < Tp; ++a) {
+                double v = mom[a];
+                for (int k = 0; k < dg_s[a]; ++k) v *= ism;
+                Al[a * 32] = v;
+            }
+            double t2 = 0.0;
+            for (int d = 0; d < D; ++d) {
+                const double tau = (cq[d] - cr[d]) * ism;
+                t2 += tau * tau;
+                double hm = 1.0, hc = 2.0 * tau;
+                Hl[(d * nH) * 32] = 1.0;
+                Hl[(d * nH + 1) * 32] = hc;
+                for (int k = 1; k + 1 < nH; ++k) {
+                    const double hn = 2.0 * tau * hc - 2.0 * k * hm;
+                    Hl[(d * nH + k + 1) * 32] = hn;
+                    hm = hc;
+                    hc = hn;
+                }
+            }
+            const double etm = exp(-t2);
+            double *Bm = sp.B + ((int64_t)E.q * sp.nh + E.j) * T;
+            for (int bt = 0; bt < Tp; ++bt) {
+                const uint8_t *be = al_s + bt * D;
+                double sacc = 0.0;
+                for (int a = 0; a < Tp; ++a) {
+                    const uint8_t *al = al_s + a * D;
+                    double pr = Al[a * 32];
+                    for (int d = 0; d < D; ++d) pr *= Hl[(d * nH + al[d] + be[d]) * 32];
+                    sacc += pr;
+                }
+                const double sign = (dg_s[bt] & 1) ? -1.0 : 1.0;
+                atomicAdd(&Bm[bt], sign * sp.tb.inv_fact[bt] * etm * sacc);
+            }
+            atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], p);
+        }
         // ---- higher orders: the whole warp per action
-        unsigned big = __ballot_sync(full, E.p > 2);
+        unsigned big = __ballot_sync(full, E.p > 2 && !mid);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
@@ -508,7 +591,7 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
             const unsigned grid = (unsigned)(fb.grid_warps / wpb);
             const void *fn = which == 0 ? (const void *)k_series_dh
                            : which == 1 ? (const void *)k_series_dl : (const void *)k_series_h2l;
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            allow_max_smem(fn);
             if (which == 0)
                 k_series_dh<<<grid, wpb * 32, sm, st>>>(sp, fb.series[0], n, pieces[0], pieces[0] + n);
             else if (which == 1)
@@ -522,9 +605,13 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
             cx.launches += 1;
             return cx.check(which == 0 ? "k_series_dh" : which == 1 ? "k_series_dl" : "k_series_h2l");
         };
+        cx.mark(0);
         rc = launch(0, fb.n_series[0], 8 * (size_t)(sp.T + sp.D * sp.P * 32));
-        if (!rc) rc = launch(1, fb.n_series[1], 8 * (size_t)(32 * sp.D * sp.P + 32));
-        if (!rc) rc = launch(2, fb.n_series[2], 8 * (size_t)(sp.T + sp.D * (2 * sp.P - 1)));
+        cx.mark(1);
+        if (!rc) rc = launch(1, fb.n_series[1], 8 * (size_t)(32 * sp.D * sp.P + 32 + 32 * kDlStride));
+        cx.mark(2);
+        if (!rc) rc = launch(2, fb.n_series[2], 8 * (size_t)(sp.T + sp.D * (2 * sp.P - 1) + 32 * (kLaneT + kLaneH)));
+        cx.mark(-1);
         for (int m = 0; m < 2; ++m)
             if (pieces[m]) cudaFreeAsync(pieces[m], st);
         if (rc) return rc;

@@ -798,9 +798,9 @@ int build_moments(TreeDev &t, const float *w, const SeriesTables &tb, CallCtx &c
     }
     if (sm > 48 * 1024) {
         if (t.dtype == GS_F64)
-            cudaFuncSetAttribute(k_leaf_moments<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            allow_max_smem((const void *)k_leaf_moments<double>);
         else
-            cudaFuncSetAttribute(k_leaf_moments<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            allow_max_smem((const void *)k_leaf_moments<float>);
     }
     if (t.dtype == GS_F64)
         k_leaf_moments<double><<<(unsigned)nl, 128, sm, st>>>((const double *)t.xs, t.perm, w, t.n, t.D, t.depth,
@@ -810,7 +810,7 @@ int build_moments(TreeDev &t, const float *w, const SeriesTables &tb, CallCtx &c
                                                              t.center, tb, t.moments);
     cx.launches += 1;
     const size_t sm2 = 2 * (size_t)tb.T * sizeof(double);
-    if (sm2 > 48 * 1024) cudaFuncSetAttribute(k_h2h_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    if (sm2 > 48 * 1024) allow_max_smem((const void *)k_h2h_moments);
     for (int k = t.depth - 1; k >= 0; --k) {
         k_h2h_moments<<<(unsigned)(1ll << k), 128, sm2, st>>>(t.D, k, t.center, tb, t.moments);
         cx.launches += 1;

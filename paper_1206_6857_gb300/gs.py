@@ -36,18 +36,29 @@ GS_SEL_EXHAUSTIVE = 3
 GS_COST_DEFAULT = (32.0, 32.0, 32.0, 1.0)     # c_DH, c_DL, c_H2L, c_Direct weights
 GS_FLAG_NO_MERGE = 1
 
+GS_MLP_NIN = 12
+GS_MLP_NOUT = 5
+GS_MLP_NPARAM = 5341
+
 
 class gs_opts(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int32), ("plimit", ctypes.c_int32),
                 ("selector", ctypes.c_int32), ("no_tokens", ctypes.c_int32),
                 ("floor_log2", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("pair_capacity", ctypes.c_int64), ("cost_weight", ctypes.c_double * 4),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("selector_params", ctypes.c_void_p), ("reserved", ctypes.c_int64 * 3)]
 
 
 GS_PH_INGEST, GS_PH_TREE, GS_PH_FRONTIER, GS_PH_SERIES, GS_PH_BASE, GS_PH_DOWN, GS_PH_OTHER = range(7)
 GS_NPHASE = 8
 PHASE_NAMES = ["ingest", "tree", "frontier", "series", "base", "down", "other", "spare"]
+
+
+class gs_problem(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_void_p), ("M", ctypes.c_int64), ("refs", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("N", ctypes.c_int64), ("D", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("h", ctypes.c_void_p), ("nh", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("out", ctypes.c_void_p)]
 
 
 class gs_stats(ctypes.Structure):
@@ -58,11 +69,13 @@ class gs_stats(ctypes.Structure):
                 ("launches_base", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("retries", ctypes.c_int32), ("fp32_rel_bound", ctypes.c_double),
                 ("eps_traversal", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("ms_phase", ctypes.c_double * GS_NPHASE), ("reserved", ctypes.c_double * 4)]
+                ("ms_phase", ctypes.c_double * GS_NPHASE), ("ms_series", ctypes.c_double * 3),
+                ("reserved", ctypes.c_double * 1)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "ms_phase")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "ms_phase", "ms_series")}
         d["ms_phase"] = {PHASE_NAMES[i]: self.ms_phase[i] for i in range(GS_NPHASE)}
+        d["ms_series"] = {"dh": self.ms_series[0], "dl": self.ms_series[1], "h2l": self.ms_series[2]}
         return d
 
 
@@ -91,6 +104,14 @@ SIGNATURES = {
                                                   ctypes.c_int, _VP, _VP]),
     "gs_lscv": (ctypes.c_int, [_VP, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                _VP, _VP, _VP, _VP, _VP]),
+    "gs_mlp_forward": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP]),
+    "gs_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    "gs_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_uint64, ctypes.c_int, _VP, _VP]),
+    "gs_sum_batched": (ctypes.c_int, [ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "gs_selector_samples": (ctypes.c_int, [_VP, _I64, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, _VP,
+                                           ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP, _VP, _I64, _VP,
+                                           _VP, _VP]),
 }
 
 
@@ -262,3 +283,85 @@ def gs_probe_rates(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().gs_probe_rates(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
     return a.value, b.value
+
+
+# ---------------------------------------------------------------------------
+# learned pair selector
+# ---------------------------------------------------------------------------
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def gs_mlp_forward(params, x, stream=None):
+    """Selector scores (n x 5 float32 CUDA tensor) of x (n x 12 float32)."""
+    import torch
+    assert params.is_cuda and params.dtype == torch.float32 and params.numel() == GS_MLP_NPARAM
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.shape[1] == GS_MLP_NIN
+    out = torch.empty((x.shape[0], GS_MLP_NOUT), dtype=torch.float32, device=x.device)
+    _check(load().gs_mlp_forward(_ptr(params), _ptr(x), x.shape[0], _ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def gs_mlp_loss_grad(params, x, y, s=None, stream=None):
+    """(loss, grad): mean weighted softmax cross entropy and its FP64 gradient (CUDA tensors)."""
+    import torch
+    grad = torch.empty(GS_MLP_NPARAM, dtype=torch.float64, device=x.device)
+    loss = torch.empty(1, dtype=torch.float64, device=x.device)
+    _check(load().gs_mlp_loss_grad(_ptr(params), _ptr(x), _ptr(y), _ptr(s), x.shape[0], _ptr(grad), _ptr(loss),
+                                   _stream_ptr(stream)))
+    return loss, grad
+
+
+def gs_mlp_train(params, x, y, s=None, epochs=10, batch=4096, lr=1e-3, seed=0, set_norm=True, stream=None):
+    """Adam training of params (updated in place); returns the per-epoch mean losses."""
+    losses = (ctypes.c_double * max(epochs, 1))()
+    _check(load().gs_mlp_train(_ptr(params), _ptr(x), _ptr(y), _ptr(s), x.shape[0], int(epochs), int(batch),
+                               float(lr), ctypes.c_uint64(seed), int(bool(set_norm)), losses, _stream_ptr(stream)))
+    return [losses[i] for i in range(epochs)]
+
+
+def gs_selector_samples(queries, refs, weights, h, eps, unit_cost, cap, opts: gs_opts | None = None, stream=None):
+    """Selector training samples of one problem: (x, y, s, model_cost) CUDA tensors
+    truncated to the sample count; model_cost = (cheapest policy, FD-only policy)."""
+    import torch
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    M, D = queries.shape
+    N = refs.shape[0]
+    dev = queries.device
+    x = torch.empty((max(cap, 1), GS_MLP_NIN), dtype=torch.float32, device=dev)
+    y = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    s = torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
+    assert len(unit_cost) == 6
+    uc = (ctypes.c_double * 6)(*[float(v) for v in unit_cost])
+    n = ctypes.c_int64(0)
+    mc = (ctypes.c_double * 2)()
+    _check(load().gs_selector_samples(_ptr(queries), M, _ptr(refs), _ptr(weights), N, D, _dtype_code(queries),
+                                      h.ctypes.data_as(_VP), len(h), float(eps),
+                                      ctypes.byref(opts) if opts is not None else None, uc, _ptr(x), _ptr(y),
+                                      _ptr(s), cap, ctypes.byref(n), mc, _stream_ptr(stream)))
+    k = n.value
+    return x[:k], y[:k], s[:k], (mc[0], mc[1])
+
+
+def gs_sum_batched(problems, opts: gs_opts | None = None, nworkers: int = 0, stream=None,
+                   stats: gs_stats | None = None, raise_on_error: bool = True):
+    """problems: sequence of (queries, refs, weights, h, eps) with torch CUDA
+    tensors (queries may be refs).  Returns the list of outputs (M x nh
+    float64 CUDA tensors) and the per-problem status codes."""
+    import torch
+    n = len(problems)
+    arr = (gs_problem * max(n, 1))()
+    outs, keep = [], []
+    for i, (q, r, w, h, eps) in enumerate(problems):
+        hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+        keep.append(hh)
+        out = torch.empty((q.shape[0], hh.size), dtype=torch.float64, device=q.device)
+        outs.append(out)
+        arr[i] = gs_problem(q.data_ptr(), q.shape[0], r.data_ptr(), w.data_ptr(), r.shape[0], q.shape[1],
+                            _dtype_code(q), hh.ctypes.data, hh.size, 0, float(eps), out.data_ptr())
+    status = (ctypes.c_int32 * max(n, 1))()
+    rc = load().gs_sum_batched(n, arr, ctypes.byref(opts) if opts is not None else None, int(nworkers),
+                               _stream_ptr(stream), ctypes.byref(stats) if stats is not None else None, status)
+    if raise_on_error:
+        _check(rc)
+    return outs, [status[i] for i in range(n)]

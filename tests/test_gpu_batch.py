@@ -1,0 +1,87 @@
+"""gs_sum_batched: many uneven problems in one call.
+
+Every problem's result is within its eps of the FP64 exhaustive oracle (the
+exhaustive ones to 1e-5), a failing problem reports its own status without
+stopping the others, and an empty batch is a no-op.
+"""
+import numpy as np
+import pytest
+
+from helpers import rel_err
+from oracle import exhaustive as oracle_ex
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+    from paper_1206_6857_gb300 import build, gs as _gs
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    _gs.load()
+    return _gs
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _problems():
+    out = []
+    # uneven batched KDE problems (the batched workload's generator, scaled down)
+    for i in (1, 5, 9, 13):
+        wl = synth.config5_problem(i, scale=0.1)
+        out.append((wl.queries, wl.refs, wl.weights, wl.h[::2], wl.eps))
+    q, r, w = synth.small_random(31, 1500, 4, m=700)
+    out.append((q, r, w, np.array([0.05, 0.2]), 1e-2))
+    q, r, w = synth.small_random(32, 900, 3)
+    out.append((q, q, w, np.array([0.02, 0.3]), 0.0))        # exhaustive
+    q, r, w = synth.small_random(33, 1200, 2, dtype=np.float64)
+    out.append((q, q, w, np.array([0.01, 0.1]), 1e-3))
+    return out
+
+
+def test_batched_problems_within_eps(gs):
+    probs = _problems()
+    dev = []
+    for q, r, w, h, eps in probs:
+        tq = _dev(q)
+        tr = tq if q is r else _dev(r)
+        dev.append((tq, tr, _dev(w), h, eps))
+    st = gs.gs_stats()
+    outs, status = gs.gs_sum_batched(dev, nworkers=3, stats=st)
+    assert status == [0] * len(probs)
+    assert st.ms_total > 0 and st.launches > 0
+    for (q, r, w, h, eps), out in zip(probs, outs):
+        exact = oracle_ex.gauss_sum(q, r, w, h)
+        err = rel_err(out.cpu().numpy(), exact, float(w.astype(np.float64).sum()))
+        assert err.max() <= (eps if eps > 0 else 1e-5), (q.shape, eps, err.max())
+
+
+def test_failing_problem_reports_its_status(gs):
+    probs = _problems()[:3]
+    dev = []
+    for k, (q, r, w, h, eps) in enumerate(probs):
+        w = w.copy()
+        if k == 1:
+            w[3] = -1.0                        # invalid weight in problem 1 only
+        tq = _dev(q)
+        tr = tq if q is r else _dev(r)
+        dev.append((tq, tr, _dev(w), h, eps))
+    with pytest.raises(gs.GSError) as ei:
+        gs.gs_sum_batched(dev, nworkers=2)
+    assert ei.value.code == gs.GS_ERR_WEIGHT and "problem 1" in str(ei.value)
+    outs, status = gs.gs_sum_batched(dev, nworkers=2, raise_on_error=False)
+    assert status[1] == gs.GS_ERR_WEIGHT and status[0] == 0 and status[2] == 0
+    q, r, w, h, eps = probs[0]
+    exact = oracle_ex.gauss_sum(q, r, w, h)
+    assert rel_err(outs[0].cpu().numpy(), exact, float(w.astype(np.float64).sum())).max() <= eps
+
+
+def test_empty_batch(gs):
+    outs, status = gs.gs_sum_batched([])
+    assert outs == [] and status == []
