@@ -47,6 +47,8 @@ def parse():
                     help="pair selector: Fig. 6's rule or the stored learned network")
     ap.add_argument("--count", type=int, default=256, help="problems in --mode batch")
     ap.add_argument("--workers", type=int, default=16, help="concurrent problems in --mode batch")
+    ap.add_argument("--no-small-exhaustive", action="store_true",
+                    help="--mode batch: dual tree even for problems whose exact sum is cheaper")
     ap.add_argument("--eps", type=float, default=None, help="override eps (0 = exhaustive)")
     ap.add_argument("--scale", type=float, default=1.0, help="workload size factor (1 = full)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -177,23 +179,31 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def source_sha():
+# sources of each kernel whose DRAM traffic profiles/traffic.json records
+KERNEL_SOURCES = {"k_basecase": ("gs_basemerge.cu", "gs_device.cuh"),
+                  "k_exhaustive": ("gs_exhaustive.cu", "gs_device.cuh")}
+
+
+def source_sha(kernel):
+    """Hash of the kernel's source files: a recorded traffic figure is used
+    only while the kernel is unchanged since its counters were taken."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1206_6857_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES.get(kernel, ()):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel, sha):
+def load_traffic(kernel, sha, workload):
+    """DRAM bytes per launch recorded for this kernel on this workload, if the
+    kernel's sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
     e = d.get(kernel)
-    if e and e.get("src_sha") == sha:
+    if e and e.get("src_sha") == sha and e.get("workload") == workload:
         return e.get("bytes_per_launch")
     return None
 
@@ -302,7 +312,8 @@ def run_gs(args):
     kname = "k_exhaustive" if eps == 0.0 else "k_basecase"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
             "frac": achieved / peak if peak else None,
-            "traffic": load_traffic(kname, source_sha()),
+            "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g" % (wl_config(wl, args.mode, eps)["workload"],
+                                                                                args.mode, args.scale)),
             "kernel": kname, "peak_basis": "measured %.1f ex2 lanes/SM/clk x %d SMs x %.0f MHz (median SM clock under load)"
             % (ex2_rate, props.multi_processor_count, sm_mhz),
             "ffma_lanes_per_sm_clk": ffma_rate, "kernel_ms_per_launch": base_ms}
@@ -392,8 +403,12 @@ def run_batch(args):
     for wl in wls:
         q = torch.from_numpy(wl.queries).to(dev)
         probs.append((q, q, torch.from_numpy(wl.weights).to(dev), wl.h, eps))
-    opts, keep = selector_opts(args, None)
+    opts = gs.gs_opts_default()
+    if not args.no_small_exhaustive:
+        opts.flags |= gs.GS_FLAG_SMALL_EXHAUSTIVE     # small problems: the exact sum is cheaper
+    opts, keep = selector_opts(args, opts)
     units = float(sum(float(wl.M) * wl.N * wl.h.size for wl in wls))
+    n_small = sum(1 for wl in wls if float(wl.M) * wl.N * wl.h.size <= gs.GS_SMALL_WORK)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -461,6 +476,8 @@ def run_batch(args):
                "sample": "20 seeded queries x all refs x 8 bandwidths of each of the first 16 problems (%.1f s)" % tot}
     cfg = {"workload": "kde_batch_%d_problems_d2-8_n1e3-2e5_8h" % len(wls), "problems": len(wls),
            "sum_M_N_nh": units, "eps": eps, "mode": "batch", "workers": args.workers, "selector": args.selector,
+           "small_exhaustive": (not args.no_small_exhaustive), "problems_summed_exhaustively":
+           (0 if args.no_small_exhaustive else n_small),
            "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"}
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -83,6 +83,14 @@ typedef struct gs_opts {
 /* gs_opts.flags */
 #define GS_FLAG_NO_MERGE 1  /* base case per bandwidth, without merging the leaf pairs
                                that several bandwidths share                           */
+#define GS_FLAG_SMALL_EXHAUSTIVE 2  /* eps > 0 problems whose exhaustive work M N nh is at
+                               most GS_SMALL_WORK are summed exhaustively (their error,
+                               about 1e-5, is within eps).  GS_SMALL_WORK = 2^39 is the
+                               crossover measured on GB300 for D = 3: 1e5 points x 16
+                               bandwidths (1.6e11 terms) take 21 ms exhaustively and 35 ms
+                               by the dual tree; 1e6 points x 16 (1.6e13) take 2.1 s and
+                               1.1 s.  In higher D the crossover is later still.        */
+#define GS_SMALL_WORK 549755813888.0
 
 /* Default cost weights: a series action runs in FP64 on the GPU while a
  * direct (base-case) term is an FP32 exponential, so on GB300 one unit of

@@ -193,7 +193,8 @@ int gs::sum_impl(const void *queries, int64_t M, const void *refs, const float *
     }
     if (stats) memset(stats, 0, sizeof(*stats));
     cudaStream_t st = (cudaStream_t)stream;
-    const bool exhaustive = eps == 0.0;
+    const bool exhaustive = eps == 0.0 || ((o.flags & GS_FLAG_SMALL_EXHAUSTIVE) && !trace && !log &&
+                                           (double)M * (double)N * (double)nh <= GS_SMALL_WORK);
 
     CallCtx cx;
     cx.st = st;

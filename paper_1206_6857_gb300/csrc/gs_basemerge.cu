@@ -172,7 +172,7 @@ __device__ __forceinline__ void leaf_terms_x2(const f2_t (&xq)[QPL / 2][DP], con
     for (int s = 0; s < QPL / 2; ++s)
 #pragma unroll
         for (int k = 0; k < NJ; ++k) part[s][k] = 0ull;
-#pragma unroll 2
+#pragma unroll 4
     for (int i = 0; i < nr; ++i) {
         f2_t rv[NT];
 #pragma unroll

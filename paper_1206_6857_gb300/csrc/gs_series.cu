@@ -78,9 +78,13 @@ __device__ __forceinline__ void load_tables(const SeriesTables &tb, int D, uint8
 __host__ __device__ inline int table_bytes(int T, int D) { return ((T * D + 7) / 8 + (T + 7) / 8) * 8; }
 
 // Work chunks: a DH action over a large query node or a DL action over a
-// large reference node is split into pieces of kChunk points; piece counts
+// large reference node is split into pieces of kChunk (DH) or kChunkDL (DL)
+// points -- DL pieces are larger because each piece ends with one atomic add
+// per coefficient into the query node's expansion, which all pieces of an
+// action share; piece counts
 // are prefix-summed and warps take pieces from the flattened list.
 constexpr int kChunk = 64;
+constexpr int kChunkDL = 512;
 
 __global__ void k_chunk_count(const SeriesEntry *__restrict__ ent, int64_t ne, int use_q, int64_t nq, int64_t nr,
                               long long *cnt) {
@@ -90,7 +94,8 @@ __global__ void k_chunk_count(const SeriesEntry *__restrict__ ent, int64_t ne, i
         const int64_t ii = node - ((1ll << dd) - 1);
         const int64_t n = use_q ? nq : nr;
         const int64_t c = level_begin(n, dd, ii + 1) - level_begin(n, dd, ii);
-        cnt[e] = (c + kChunk - 1) / kChunk;
+        const int chunk = use_q ? kChunk : kChunkDL;
+        cnt[e] = (c + chunk - 1) / chunk;
     }
 }
 
@@ -166,7 +171,7 @@ __global__ void k_series_dh(SeriesParams sp, const SeriesEntry *__restrict__ ent
 }
 
 // ---------------------------------------------------------------------------
-// DL: one warp per piece of kChunk references.  Up to kDlLane coefficients:
+// DL: one warp per piece of kChunkDL references.  Up to kDlLane coefficients:
 // lanes over references, each adding its references' contributions to every
 // coefficient in its own row of a shared accumulator (row stride 33 doubles,
 // so both the row-wise adds and the column sums are conflict-free), then
@@ -196,8 +201,8 @@ __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent
         const double *cQ = sp.qcenter + (int64_t)E.q * D;
         const int rd = node_depth(E.r);
         const int64_t ri = E.r - ((1ll << rd) - 1);
-        const int64_t rb = level_begin(sp.rn, rd, ri) + (c - off[e]) * kChunk;
-        const int64_t re = min(rb + kChunk, level_begin(sp.rn, rd, ri + 1));
+        const int64_t rb = level_begin(sp.rn, rd, ri) + (c - off[e]) * kChunkDL;
+        const int64_t re = min(rb + kChunkDL, level_begin(sp.rn, rd, ri + 1));
         double *Bq = sp.B + ((int64_t)E.q * sp.nh + E.j) * T;
         if (Tp <= kDlLane) {
             double *row = acc_s + lane * kDlStride;

@@ -172,7 +172,7 @@ def _training_problems():
     yield synth.config1()
     yield synth.config2(scale=0.03)
     yield synth.config2(scale=0.1)
-    yield synth.config2(scale=0.3)
+    yield synth.config2(scale=0.1, nh=8)
     yield synth.config3(scale=0.04, eps=1e-3)
     yield synth.config3(scale=0.1, eps=1e-2)
     for i in range(0, 40, 8):

@@ -85,3 +85,22 @@ def test_failing_problem_reports_its_status(gs):
 def test_empty_batch(gs):
     outs, status = gs.gs_sum_batched([])
     assert outs == [] and status == []
+
+
+def test_small_problems_summed_exactly_with_the_flag(gs):
+    probs = _problems()[:5]
+    dev = []
+    for q, r, w, h, eps in probs:
+        tq = _dev(q)
+        tr = tq if q is r else _dev(r)
+        dev.append((tq, tr, _dev(w), h, eps))
+    o = gs.gs_opts_default()
+    o.flags |= gs.GS_FLAG_SMALL_EXHAUSTIVE
+    st = gs.gs_stats()
+    outs, status = gs.gs_sum_batched(dev, opts=o, stats=st)
+    assert status == [0] * len(probs)
+    assert st.pairs_split == 0 and st.pairs_fd == 0          # no traversal ran
+    for (q, r, w, h, eps), out in zip(probs, outs):
+        assert float(q.shape[0]) * r.shape[0] * len(h) <= gs.GS_SMALL_WORK
+        exact = oracle_ex.gauss_sum(q, r, w, h)
+        assert rel_err(out.cpu().numpy(), exact, float(w.astype(np.float64).sum())).max() <= 1e-5

@@ -160,3 +160,43 @@ def test_selector_samples(gs):
     with pytest.raises(gs.GSError) as ei:
         gs.gs_selector_samples(p, p, _dev(wl.weights), wl.h, wl.eps, selector.UNIT_COSTS, 10, opts=o)
     assert ei.value.code == gs.GS_ERR_CAPACITY
+
+
+def test_trained_selector_against_the_rule(gs, capsys):
+    """The stored network (trained on the GPU by selector.main) on problems it
+    was not trained on: both orderings stay within eps of the oracle; the
+    test reports the wall time of each (the gain or loss of the network)."""
+    import time
+    import torch
+    from paper_1206_6857_gb300 import selector
+    params = selector.load()
+    rows = []
+    for wl in (synth.config2(scale=0.05), synth.config5_problem(3, scale=0.5)):
+        p = _dev(wl.refs)
+        w = _dev(wl.weights)
+        res = {}
+        for name in ("rule", "mlp"):
+            o = gs.gs_opts_default()
+            o.leaf_size = wl.leaf_size
+            if name == "mlp":
+                o = selector.options(params, o)
+            gs.gs_sum(p, p, w, wl.h, wl.eps, opts=o)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(3):
+                st = gs.gs_stats()
+                t0 = time.perf_counter()
+                out = gs.gs_sum(p, p, w, wl.h, wl.eps, opts=o, stats=st)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            idx = np.sort(np.random.default_rng(0).choice(wl.M, 300, replace=False))
+            exact = oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, wl.h)
+            err = rel_err(out.cpu().numpy()[idx], exact, float(wl.weights.astype(np.float64).sum()))
+            assert err.max() <= wl.eps, (wl.name, name, err.max())
+            res[name] = (best, st.pairs_dh + st.pairs_dl + st.pairs_h2l, st.pairs_base)
+        assert res["mlp"][1:] != res["rule"][1:]       # the network changed decisions
+        rows.append("%s: rule %.2f ms, learned %.2f ms (x%.2f)" % (wl.name, 1e3 * res["rule"][0],
+                                                                 1e3 * res["mlp"][0], res["rule"][0] / res["mlp"][0]))
+    with capsys.disabled():
+        print("\n" + "\n".join(rows))
