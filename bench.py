@@ -56,12 +56,15 @@ def parse():
     ap.add_argument("--leaf", type=int, default=0, help="fixed leaf size (skips the autotuner)")
     ap.add_argument("--cost", default="", help="fixed cost weights c_DH,c_DL,c_H2L,c_Direct (skips the autotuner)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+                    help="workload for --mode sum: 1 (D=2, 1e4), 2 (D=3 sweep, 1e6), 3 (D=5, 5e5, eps 1e-3), "
+                         "4 (D=16 bichromatic, 2e6 refs x 2e5 queries)")
     return ap.parse_args()
 
 
-def workload(scale):
+def workload(scale, config=2):
     from workloads import synth
-    return synth.config2(scale)
+    return {1: synth.config1, 2: synth.config2, 3: synth.config3, 4: synth.config4}[config](scale)
 
 
 def sum_bandwidths(wl, mode):
@@ -71,11 +74,13 @@ def sum_bandwidths(wl, mode):
 
 
 def wl_config(wl, mode, eps):
-    return {"workload": "kde_sweep_d3_n%d_mono_16h" % wl.N, "M": wl.M, "N": wl.N, "D": wl.D,
+    name = "kde_sweep_d3_n%d_mono_16h" % wl.N if wl.D == 3 and wl.mono and wl.h.size == 16 else wl.name
+    return {"workload": name, "M": wl.M, "N": wl.N, "D": wl.D,
             "nh": int(wl.h.size), "gaussian_sums": int(sum_bandwidths(wl, mode).size), "eps": eps,
             "mode": mode, "leaf_size": wl.leaf_size,
             "h_range_x_diameter": [1e-3, 1.0], "diameter": round(wl.diameter, 6),
-            "input_dtype": "f32", "l2": "flushed before every timed step (256 MB write)",
+            "input_dtype": "f32" if wl.refs.dtype == np.float32 else "f64",
+            "l2": "flushed before every timed step (256 MB write)",
             "parallelism": "replicas"}
 
 
@@ -151,7 +156,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = workload(args.scale)
+    wl = workload(args.scale, args.config)
     from oracle import build as ob
     ob.build()
     hs = sum_bandwidths(wl, args.mode)
@@ -227,11 +232,14 @@ def run_gs(args):
         dist.barrier()
     gs.load()
 
-    wl = workload(args.scale)
+    wl = workload(args.scale, args.config)
+    if not wl.mono and args.mode == "lscv":
+        args.mode = "sum"                 # LSCV needs monochromatic data
     eps = wl.eps if args.eps is None else args.eps
     hs = sum_bandwidths(wl, args.mode)
     dev = torch.device("cuda", local)
     tq = torch.from_numpy(wl.queries).to(dev)
+    tr = tq if wl.mono else torch.from_numpy(wl.refs).to(dev)
     tw = torch.from_numpy(wl.weights).to(dev)
     out = torch.empty((wl.M, wl.h.size), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -249,7 +257,7 @@ def run_gs(args):
     elif eps > 0 and not args.no_tune:
         from paper_1206_6857_gb300 import autotune
         t0 = time.perf_counter()
-        tuned, _table = autotune.tune(tq, tw, hs, eps)
+        tuned, _table = autotune.tune(tr, tw, hs, eps, queries=None if wl.mono else tq)
         tuned["tuning_seconds"] = time.perf_counter() - t0
         opts = autotune.options(tuned)
 
@@ -261,7 +269,7 @@ def run_gs(args):
         if args.mode == "lscv":
             scores["lscv"] = gs.gs_lscv(tq, tw, wl.h, eps, opts=opts, stream=stream, stats=stats)
         else:
-            gs.gs_sum(tq, tq, tw, wl.h, eps, out=out, opts=opts, stream=stream, stats=stats)
+            gs.gs_sum(tq, tr, tw, wl.h, eps, out=out, opts=opts, stream=stream, stats=stats)
 
     for _ in range(args.warmup):
         step()
@@ -334,8 +342,11 @@ def run_gs(args):
         else:
             hout = torch.empty((wl.M, wl.h.size), dtype=torch.float64).pin_memory().numpy()
 
+            hqn = hq.numpy()
+            hrn = hqn if wl.mono else torch.from_numpy(wl.refs).pin_memory().numpy()   # same object: monochromatic
+
             def e2e_step():
-                gs.gs_sum_host(hq.numpy(), hq.numpy(), hw.numpy(), wl.h, eps, out=hout, opts=opts)
+                gs.gs_sum_host(hqn, hrn, hw.numpy(), wl.h, eps, out=hout, opts=opts)
             d2h = int(hout.nbytes)
         e2e_step()
         torch.cuda.synchronize()
@@ -344,7 +355,8 @@ def run_gs(args):
             e2e_step()
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / n_e2e
-        e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": int(hq.numel() * 4 + hw.numel() * 4),
+        h2d = int(hq.numel() * hq.element_size() + hw.numel() * 4 + (0 if wl.mono else wl.refs.nbytes))
+        e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
 
     cpu = None

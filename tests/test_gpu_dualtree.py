@@ -154,6 +154,21 @@ def test_config2_full_size_sampled(gs):
     assert st.point_pairs_base < 1e12 * 16      # the tree pruned something
 
 
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_config3_full_size_sampled(gs, eps):
+    # D = 5, 5e5 points, 8 bandwidths: every query of a seeded sample checked
+    wl = synth.config3(eps=eps)
+    st = _check_eps(gs, wl, eps=eps, sample=64)
+    assert st.pairs_fd > 0
+
+
+def test_config4_full_size_sampled(gs):
+    # D = 16 bichromatic: 2e6 references, 2e5 queries, 8 bandwidths
+    wl = synth.config4()
+    st = _check_eps(gs, wl, sample=32)
+    assert st.point_pairs_base <= float(wl.M) * wl.N * wl.h.size
+
+
 @pytest.mark.parametrize("n,m,D", [(1, 1, 2), (5, 3, 1), (40, 1, 3), (1, 50, 2), (64, 64, 32)])
 def test_degenerate_sizes(gs, n, m, D):
     q, r, w = synth.small_random(n * 31 + m, n, D, m=m)
