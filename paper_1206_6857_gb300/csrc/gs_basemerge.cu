@@ -162,16 +162,17 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
 // leaf_terms for two query slots per register pair: the staged reference
 // records hold every float twice, (x_0, x_0, x_1, x_1, ..., l, l, ...), so a
 // 16-byte shared load gives two broadcast pairs.  Same operations, in the
-// same order, as the scalar version.
+// same order, as the scalar version; up to 8 bandwidths share one squared
+// distance (the scalar version takes 4 at a time).
 template <int DP, int QPL, bool ANCH, int NJ>
 __device__ __forceinline__ void leaf_terms_x2(const f2_t (&xq)[QPL / 2][DP], const f2_t (&dc)[DP],
-                                              const ulonglong2 *rp, int nr, const f2_t (&c)[4],
-                                              f2_t (&part)[QPL / 2][4]) {
+                                              const ulonglong2 *rp, int nr, const f2_t (&c)[8],
+                                              f2_t (&part)[QPL / 2][8]) {
     constexpr int NT = RefRec<float, DP>::NT;   // pairs per staged record
 #pragma unroll
     for (int s = 0; s < QPL / 2; ++s)
 #pragma unroll
-        for (int k = 0; k < NJ; ++k) part[s][k] = 0ull;
+        for (int k = 0; k < 8; ++k) part[s][k] = 0ull;
 #pragma unroll 4
     for (int i = 0; i < nr; ++i) {
         f2_t rv[NT];
@@ -293,7 +294,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                 int ks[8];
                 float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 int nj = 0;
-                while (m && nj < 4) {
+                while (m && nj < (X2 ? 8 : 4)) {
                     const int k = __ffs(m) - 1;
                     m &= m - 1;
                     ks[nj] = k;
@@ -303,7 +304,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                 float part[QPL][8];
                 if constexpr (X2) {
                     constexpr int QH = QPL / 2 > 0 ? QPL / 2 : 1;
-                    f2_t xq2[QH][DP], dc2[DP], c2[4], part2[QH][4];
+                    f2_t xq2[QH][DP], dc2[DP], c2[8], part2[QH][8];
 #pragma unroll
                     for (int h2 = 0; h2 < QH; ++h2)
 #pragma unroll
@@ -311,18 +312,22 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
 #pragma unroll
                     for (int d = 0; d < DP; ++d) dc2[d] = f2_pack(dc[d], dc[d]);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) c2[k] = f2_pack(c[k], c[k]);
+                    for (int k = 0; k < 8; ++k) c2[k] = f2_pack(c[k], c[k]);
                     const ulonglong2 *rp2 = reinterpret_cast<const ulonglong2 *>(rp);
                     switch (nj) {
                         case 1: leaf_terms_x2<DP, QPL, ANCH, 1>(xq2, dc2, rp2, nr, c2, part2); break;
                         case 2: leaf_terms_x2<DP, QPL, ANCH, 2>(xq2, dc2, rp2, nr, c2, part2); break;
                         case 3: leaf_terms_x2<DP, QPL, ANCH, 3>(xq2, dc2, rp2, nr, c2, part2); break;
-                        default: leaf_terms_x2<DP, QPL, ANCH, 4>(xq2, dc2, rp2, nr, c2, part2); break;
+                        case 4: leaf_terms_x2<DP, QPL, ANCH, 4>(xq2, dc2, rp2, nr, c2, part2); break;
+                        case 5: leaf_terms_x2<DP, QPL, ANCH, 5>(xq2, dc2, rp2, nr, c2, part2); break;
+                        case 6: leaf_terms_x2<DP, QPL, ANCH, 6>(xq2, dc2, rp2, nr, c2, part2); break;
+                        case 7: leaf_terms_x2<DP, QPL, ANCH, 7>(xq2, dc2, rp2, nr, c2, part2); break;
+                        default: leaf_terms_x2<DP, QPL, ANCH, 8>(xq2, dc2, rp2, nr, c2, part2); break;
                     }
 #pragma unroll
                     for (int h2 = 0; h2 < QH; ++h2)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) f2_unpack(part2[h2][k], part[2 * h2][k], part[2 * h2 + 1][k]);
+                        for (int k = 0; k < 8; ++k) f2_unpack(part2[h2][k], part[2 * h2][k], part[2 * h2 + 1][k]);
                 } else {
                     const float4 *rp4 = reinterpret_cast<const float4 *>(rp);
                     switch (nj) {

@@ -179,17 +179,19 @@ def _training_problems():
         yield synth.config5_problem(i)
 
 
-def main(epochs=40, out=PARAMS_FILE):
-    """Collect samples from the training problems, train, store the network."""
+def _collect(problems, factors=(1.0, 1.0, 1.0)):
+    """Samples of every problem; series unit costs from a rule run of the
+    problem, multiplied by per-method factors (DH, DL, H2L)."""
     import torch
     xs, ys, ss, info = [], [], [], []
-    for wl in _training_problems():
+    for wl in problems:
         p = torch.from_numpy(np.ascontiguousarray(wl.refs)).cuda()
         w = torch.from_numpy(np.ascontiguousarray(wl.weights)).cuda()
         q = None if wl.mono else torch.from_numpy(np.ascontiguousarray(wl.queries)).cuda()
         o = gs.gs_opts_default()
         o.leaf_size = wl.leaf_size
         units, _ = calibrate(p, w, wl.h, wl.eps, queries=q, opts=o)
+        units = tuple(units[:2]) + tuple(u * f for u, f in zip(units[2:5], factors)) + (units[5],)
         x, y, s, mc = samples(p, w, wl.h, wl.eps, queries=q, opts=o, units=units)
         xs.append(x)
         ys.append(y)
@@ -198,13 +200,45 @@ def main(epochs=40, out=PARAMS_FILE):
         info.append({"workload": wl.name, "samples": int(x.shape[0]), "labels": counts, "unit_costs": units,
                      "model_cost_best": mc[0], "model_cost_fd_only": mc[1]})
         print(info[-1], flush=True)
-    x = torch.cat(xs)
-    y = torch.cat(ys)
-    s = torch.cat(ss)
-    params, losses = train(x, y, s, epochs=epochs)
-    scores = gs.gs_mlp_forward(params, x)
-    acc = float((scores[:, 1:].argmax(dim=1) + 1 == y).float().mean())
-    meta = {"problems": info, "epochs": epochs, "loss": losses, "train_accuracy": acc}
+    return torch.cat(xs), torch.cat(ys), torch.cat(ss), info
+
+
+def main(epochs=40, rounds=2, out=PARAMS_FILE):
+    """Collect samples from the training problems, train, store the network.
+
+    Round 1 takes the series unit costs measured on the rule's own actions.
+    The learned policy then picks other actions (larger nodes, higher orders),
+    so each further round measures the unit costs again on a run of the
+    current network over a calibration problem, scales every problem's series
+    costs by the ratio to the rule's, relabels and retrains."""
+    import sys
+    import torch
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from workloads import synth
+    factors = (1.0, 1.0, 1.0)
+    history = []
+    params = None
+    for rnd in range(rounds):
+        x, y, s, info = _collect(_training_problems(), factors)
+        params, losses = train(x, y, s, epochs=epochs)
+        scores = gs.gs_mlp_forward(params, x)
+        acc = float((scores[:, 1:].argmax(dim=1) + 1 == y).float().mean())
+        history.append({"round": rnd, "factors": factors, "samples": int(x.shape[0]), "loss": losses[-1],
+                        "train_accuracy": acc})
+        print("round %d: %d samples, loss %.4f, accuracy %.3f, factors %s" % (rnd, x.shape[0], losses[-1], acc,
+                                                                            factors), flush=True)
+        if rnd + 1 < rounds:
+            wl = synth.config2(scale=0.1)
+            p = torch.from_numpy(np.ascontiguousarray(wl.refs)).cuda()
+            w = torch.from_numpy(np.ascontiguousarray(wl.weights)).cuda()
+            o = gs.gs_opts_default()
+            o.leaf_size = wl.leaf_size
+            u_rule, _ = calibrate(p, w, wl.h, wl.eps, opts=o)
+            u_mlp, _ = calibrate(p, w, wl.h, wl.eps, opts=options(params, o))
+            factors = tuple(max(1.0, f * um / ur) for f, um, ur in zip(factors, u_mlp[2:5], u_rule[2:5]))
+    meta = {"problems": info, "epochs": epochs, "rounds": history, "loss": losses, "train_accuracy": acc}
     save(params, meta, out)
     print("trained on %d samples, final loss %.4f, accuracy %.3f" % (x.shape[0], losses[-1], acc))
     return params, meta
