@@ -256,6 +256,40 @@ int gs_sum_exhaustive_noalloc(const void *queries, int64_t M, const void *refs, 
                               int64_t N, int D, int dtype, const double *h, int nh, double *out,
                               void *stream);
 
+/* ---- trees built once, summed many times ---------------------------------
+ *
+ * A gs_tree holds the kd-tree of one point set (Section 5: the node boxes,
+ * weight sums and the packed point records, in the library's own device
+ * memory) so that several sums over the same data -- other bandwidths, other
+ * eps, other query sets -- do not rebuild it.  A reference tree (built with
+ * weights) also keeps a copy of the weights and the weight range. */
+typedef struct gs_tree gs_tree;
+
+/*
+ * gs_build_tree -- build the tree of n points (DEVICE, n x D, dtype) with
+ * optional weights (DEVICE, n floats; NULL for a query-only tree).  The
+ * leaf size is opts->leaf_size (0 or NULL opts -> 32).  The inputs are
+ * copied; the caller may free them afterwards.  *out receives the handle.
+ * Returns GS_OK, GS_ERR_ARG, GS_ERR_NONFINITE, GS_ERR_WEIGHT, GS_ERR_OOM or
+ * GS_ERR_CUDA; synchronises the stream.
+ */
+int gs_build_tree(const void *pts, int dtype, int64_t n, int D, const float *weights, const gs_opts *opts,
+                  void *stream, gs_tree **out);
+
+/* gs_tree_free -- release a tree (waits for the device to be idle); NULL is a no-op. */
+void gs_tree_free(gs_tree *tree);
+
+/*
+ * gs_sum_trees -- gs_sum on built trees: queries from q, references and
+ * weights from r (q == r: monochromatic), same D, dtype and leaf size.
+ * h HOST (1 <= nh <= 64), 0 < eps < 1 (the exhaustive sum needs no tree:
+ * use gs_sum), out DEVICE M x nh in the query tree's caller order.  opts as
+ * for gs_sum except leaf_size, which the trees fix.  Same results and
+ * errors as gs_sum on the same data and options.
+ */
+int gs_sum_trees(const gs_tree *q, const gs_tree *r, const double *h, int nh, double eps, double *out,
+                 const gs_opts *opts, void *stream, gs_stats *stats);
+
 /* ---- many problems in one call ------------------------------------------
  *
  * One independent Gaussian-sum problem (the arguments of gs_sum). */

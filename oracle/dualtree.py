@@ -117,6 +117,50 @@ def kernel_bounds(qt, rt, pq, pr, c32):
 # --------------------------------------------------------------------------
 # Fixed-order group reduction: 32 strided partials, then xor butterfly.
 # --------------------------------------------------------------------------
+def f32_mul_dir(a, b, up: bool):
+    """a * b for FP32 arrays, rounded to FP32 toward -inf (up=False) or +inf.
+    The FP64 product of two FP32 values is exact."""
+    p = np.asarray(a, np.float32).astype(np.float64) * np.asarray(b, np.float32).astype(np.float64)
+    return f32_up(p) if up else f32_down(p)
+
+
+def f32_add_dir(a, b, up: bool):
+    """a + b for FP32 arrays rounded to FP32 toward -inf / +inf: the exact
+    sum is s + e with s the FP64 sum and e its error (Knuth's two-sum)."""
+    a = np.asarray(a, np.float32).astype(np.float64)
+    b = np.asarray(b, np.float32).astype(np.float64)
+    s = a + b
+    bv = s - a
+    e = (a - (s - bv)) + (b - bv)
+    r = s.astype(np.float32)
+    rd = r.astype(np.float64)
+    if up:
+        fix = (rd < s) | ((rd == s) & (e > 0))
+        r[fix] = np.nextafter(r[fix], np.float32(np.inf))
+    else:
+        fix = (rd > s) | ((rd == s) & (e < 0))
+        r[fix] = np.nextafter(r[fix], np.float32(-np.inf))
+    return r
+
+
+def group_reduce_f32(values, group_of, pos_in_group, ngroups: int, up: bool):
+    """Per group: 32 lane-strided FP32 partial sums, every addition rounded
+    in one direction, then the partials widened to FP64 and combined by the
+    xor butterfly (the frontier kernel's order)."""
+    values = np.asarray(values, np.float32)
+    acc = np.zeros((ngroups, 32), np.float32)
+    lane = pos_in_group % 32
+    rnd = pos_in_group // 32
+    for k in range(int(rnd.max()) + 1 if rnd.size else 0):
+        sel = rnd == k
+        g, l = group_of[sel], lane[sel]
+        acc[g, l] = f32_add_dir(acc[g, l], values[sel], up)
+    acc = acc.astype(np.float64)
+    for m in (16, 8, 4, 2, 1):
+        acc = acc + acc[:, np.arange(32) ^ m]
+    return acc[:, 0]
+
+
 def group_reduce(values: np.ndarray, group_of: np.ndarray, pos_in_group: np.ndarray, ngroups: int):
     acc = np.zeros((ngroups, 32))
     lane = pos_in_group % 32
@@ -163,6 +207,12 @@ class Tree:
     @property
     def nodes(self):
         return (1 << (self.depth + 1)) - 1
+    W32d: np.ndarray = None   # W rounded down / up to FP32
+    W32u: np.ndarray = None
+
+    def __post_init__(self):
+        self.W32d = f32_down(self.W)
+        self.W32u = f32_up(self.W)
 
 
 def build_tree(x: np.ndarray, w: np.ndarray, L: int) -> Tree:
@@ -401,9 +451,10 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
         kmax = kmax32.astype(np.float64)
         kmin = kmin32.astype(np.float64)
         WR = rt.W[pr]
-        dl = WR * kmax
-        front = group_reduce(dl, gid, pos, ng)
-        Wg = group_reduce(WR, gid, pos, ng)
+        # the lower bound sum and the weight sum in FP32, rounded down and up
+        dl32 = f32_mul_dir(rt.W32d[pr], kmax32, up=False)
+        front = group_reduce_f32(dl32, gid, pos, ng, up=False)
+        Wg = group_reduce_f32(rt.W32u[pr], gid, pos, ng, up=True)
         G = fin[gq, gj] + front
         if mono:
             G = np.maximum(G, qt.wmin[gq])
@@ -507,12 +558,13 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
         # leave the token alone
         finished = method != SPLIT
         if tokens:
-            banked = group_reduce(np.where(method == BASE, WR, 0.0), gid, pos, ng)
+            banked = group_reduce_f32(np.where(method == BASE, rt.W32d[pr], np.float32(0)), gid, pos, ng, up=False)
             paid = group_reduce(spent, gid, pos, ng)
             tok_new = np.maximum(0.0, (tok[gq, gj] + banked) - paid)
         else:
             tok_new = np.zeros(ng)
-        fin_add = group_reduce(np.where(finished, dl, 0.0), gid, pos, ng)
+        fin_add = front if (q_leaf and r_leaf) else \
+            group_reduce_f32(np.where(finished, dl32, np.float32(0)), gid, pos, ng, up=False)
         est_add = group_reduce(np.where(method == FD, est_fd, 0.0), gid, pos, ng)
         fin[gq, gj] = fin[gq, gj] + fin_add
         tok[gq, gj] = tok_new

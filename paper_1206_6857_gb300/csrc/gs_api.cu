@@ -76,7 +76,7 @@ static int check_common(const void *queries, int64_t M, const void *refs, const 
     return GS_OK;
 }
 
-static int status_to_code(unsigned st) {
+int status_to_code(unsigned st) {
     if (st & ST_NONFINITE) {
         set_error("non-finite coordinate or weight");
         return GS_ERR_NONFINITE;

@@ -127,7 +127,7 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
     }
     const bool mono = queries == refs && M == N;
     const int DP = dp_for(D);
-    const int stride = (((DP + 1) * 4 + 15) / 16) * 4;   // floats per packed record (16-byte units)
+    const int stride = record_stride(D);
     int rc;
     TreeDev rt, qt;
     cx.phase(GS_PH_TREE);
@@ -142,6 +142,23 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
             return rc;
         }
     }
+    rc = dualtree_run(qt, rt, mono, weights, D, h, nh, eps, out, o, cx, ing, trace, status_out, log);
+    free_tree(rt, st);
+    if (!mono) free_tree(qt, st);
+    return rc;
+}
+
+int dualtree_run(const TreeDev &qt_in, const TreeDev &rt_in, bool mono, const float *weights, int D,
+                 const double *h, int nh, double eps, double *out, const gs_opts &o, CallCtx &cx, Ingest *ing,
+                 TraceOut *trace, unsigned *status_out, PairLog *log) {
+    cudaStream_t st = cx.st;
+    const int DP = dp_for(D);
+    int rc = GS_OK;
+    // shallow copies: this call's moments live in rt and are freed here
+    TreeDev rt = rt_in;
+    TreeDev qt = mono ? rt_in : qt_in;
+    rt.moments = nullptr;
+    rt.mom_terms = 0;
     int P = o.plimit > 0 ? o.plimit : plimit_for(D);
     if (P > 16) P = 16;
     const bool series = (o.selector == GS_SEL_RULE || o.selector == GS_SEL_MLP) && P >= 1;
@@ -159,8 +176,7 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
         if (!rc) rc = build_moments(rt, weights, tb, cx);
         if (rc) {
             free_series_tables(&tb, st);
-            free_tree(rt, st);
-            if (!mono) free_tree(qt, st);
+            if (rt.moments) cudaFreeAsync(rt.moments, st);
             return rc;
         }
     }
@@ -251,8 +267,7 @@ int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *
     if (pL) cudaFreeAsync(pL, st);
     free_bufs(fb, st);
     if (series) free_series_tables(&tb, st);
-    free_tree(rt, st);
-    if (!mono) free_tree(qt, st);
+    if (rt.moments) cudaFreeAsync(rt.moments, st);
     if (rc) return rc;
     *status_out = hing.status;
     return GS_OK;

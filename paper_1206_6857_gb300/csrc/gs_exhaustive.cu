@@ -101,7 +101,7 @@ cudaError_t launch_ingest(Ingest *ing, const void *queries, int64_t M, const voi
         if (queries != refs)
             k_ingest_points<float><<<grid_for(nq, 256), 256, 0, st>>>((const float *)queries, nq, ing);
     }
-    k_ingest_weights<<<grid_for(N, 256), 256, 0, st>>>(weights, N, ing);
+    if (weights) k_ingest_weights<<<grid_for(N, 256), 256, 0, st>>>(weights, N, ing);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ struct FrontierParams {
     const float *qwmin;
     const double *rrad, *rW;
     const float *rrad32;  // reference radii rounded down to FP32
+    const float *rW32d, *rW32u;   // reference weight sums rounded down / up to FP32
     const double *inv_h;
     double *fin, *tok, *est;
     float *geo;           // per pair cache: K(delta_max) lower, K(delta_min) upper, e^{-dmin^2/4h^2} upper
@@ -166,8 +167,13 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const int j = G.j;
         const double invh = fp.inv_h[j];
         const float c32 = fp.c32[j];
-        // pass 1: kernel bounds of every pair, lower bound over the group
-        double s_dl = 0.0, s_W = 0.0;
+        // pass 1: kernel bounds of every pair, lower bound over the group.
+        // The lane sums run in FP32 rounded towards -inf (the lower bound,
+        // from W_R rounded down) and +inf (the weight sum the token is
+        // shared by, from W_R rounded up), then widen to FP64 for the
+        // butterfly: a smaller lower bound and a larger weight sum keep
+        // every budget valid.
+        float s_dl = 0.f, s_W = 0.f;
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
             const KBounds kb = kernel_bounds(fp, q, r, c32);
@@ -175,11 +181,10 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             gc[0] = kb.kmax;
             gc[1] = kb.kmin;
             gc[2] = kb.e4;
-            const double WR = fp.rW[r];
-            s_dl = s_dl + WR * (double)kb.kmax;
-            s_W = s_W + WR;
+            s_dl = __fadd_rd(s_dl, __fmul_rd(fp.rW32d[r], kb.kmax));
+            s_W = __fadd_ru(s_W, fp.rW32u[r]);
         }
-        const double front = warp_sum(s_dl), Wg = warp_sum(s_W);
+        const double front = warp_sum((double)s_dl), Wg = warp_sum((double)s_W);
         const int64_t qj = q * fp.nh + j;
         const double fin0 = fp.fin[qj], tok0 = fp.tok[qj];
         double Gb = fin0 + front;
@@ -191,7 +196,8 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const double share = tok0 / Wg;
         const double kappa = Wtot / (eps_t * Gb);
         // pass 2: decisions
-        double s_bank = 0.0, s_paid = 0.0, s_fin = 0.0, s_est = 0.0;
+        float s_bank = 0.f, s_fin = 0.f;   // FP32 rounded down, like the lower bound
+        double s_paid = 0.0, s_est = 0.0;
         int n_fd = 0, n_dh = 0, n_dl = 0, n_h2l = 0, n_base = 0, n_split = 0;
         const double share_t = fp.tokens ? share : 0.0;
         // FP32 screen of the FD test (n_fd <= allot  <=>  (K(dmin)-K(dmax)) kappa/2 <= 1 + share):
@@ -429,9 +435,10 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                 }
             }
             if (method == M_FD || (method >= M_DH && method <= M_H2L)) s_paid = s_paid + spent;
-            if (method == M_BASE) s_bank = s_bank + WR;
+            if (method == M_BASE) s_bank = __fadd_rd(s_bank, fp.rW32d[r]);
             // at a leaf-leaf iteration no pair splits, so this sum equals pass 1's s_dl
-            if (method != M_SPLIT && !(fp.q_leaf && fp.r_leaf)) s_fin = s_fin + WR * (double)kmax32;
+            if (method != M_SPLIT && !(fp.q_leaf && fp.r_leaf))
+                s_fin = __fadd_rd(s_fin, __fmul_rd(fp.rW32d[r], kmax32));
             n_fd += method == M_FD;
             n_dh += method == M_DH;
             n_dl += method == M_DL;
@@ -446,8 +453,8 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             }
         }
         if (fp.q_leaf && fp.r_leaf) s_fin = s_dl;
-        const double banked = warp_sum(s_bank), paid = warp_sum(s_paid);
-        const double fin_add = warp_sum(s_fin), est_add = warp_sum(s_est);
+        const double banked = warp_sum((double)s_bank), paid = warp_sum(s_paid);
+        const double fin_add = warp_sum((double)s_fin), est_add = warp_sum(s_est);
         // Fig. 7's token update over the whole group: pruned pairs pay their
         // need, base cases bank W_R, splits leave the token alone
         const double tok_new = fp.tokens ? fmax(0.0, (tok0 + banked) - paid) : 0.0;
@@ -790,6 +797,8 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.qlo32 = in.qt->lo32; fp.qhi32 = in.qt->hi32; fp.qrad = in.qt->rad; fp.qwmin = in.qt->wmin;
     fp.rlo32 = in.rt->lo32; fp.rhi32 = in.rt->hi32; fp.rrad = in.rt->rad; fp.rW = in.rt->W;
     fp.rrad32 = in.rt->rad32;
+    fp.rW32d = in.rt->W32d;
+    fp.rW32u = in.rt->W32u;
     fp.inv_h = fb.inv_h;
     for (int j = 0; j < in.nh; ++j) fp.c32[j] = (float)(1.4426950408889634 / ((2.0 * in.h[j]) * in.h[j]));
     fp.fin = fb.fin; fp.tok = fb.tok; fp.est = fb.est;

@@ -111,6 +111,9 @@ inline cudaError_t allow_max_smem(const void *fn) {
     return e;
 }
 
+// Device status bits -> GS_ERR_* code (and message); GS_OK when clear.
+int status_to_code(unsigned st);
+
 // Host-side error reporting (thread-local message).
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
@@ -218,6 +221,14 @@ struct TraceOut {
 int dualtree_sum(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
                  int dtype, const double *h, int nh, double eps, double *out, const gs_opts &o, CallCtx &cx,
                  Ingest *ing, TraceOut *trace, unsigned *status_out, PairLog *log = nullptr);
+// The traversal, series, base case and downward pass on trees already built
+// (qt ignored when mono); `weights` are the references' weights in caller
+// order (for the moments).  The trees are not modified.
+int dualtree_run(const TreeDev &qt, const TreeDev &rt, bool mono, const float *weights, int D,
+                 const double *h, int nh, double eps, double *out, const gs_opts &o, CallCtx &cx, Ingest *ing,
+                 TraceOut *trace, unsigned *status_out, PairLog *log = nullptr);
+// floats per packed FP32 record (dimension bucket + log2 weight, 16-byte units)
+inline int record_stride(int D) { return (((dp_for(D) + 1) * 4 + 15) / 16) * 4; }
 
 // gs_sum with its options checked; trace and log are optional.
 int sum_impl(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,

@@ -381,7 +381,8 @@ __global__ void k_internal_stats(int D, int k, double *lo, double *hi, double *W
 }
 
 __global__ void k_center_rad(int64_t nodes, int D, const double *lo, const double *hi, double *center,
-                             double *rad, float *rad32, float *lo32, float *hi32) {
+                             double *rad, float *rad32, float *lo32, float *hi32, const double *W, float *W32d,
+                             float *W32u) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nodes; i += (int64_t)gridDim.x * blockDim.x) {
         double r = 0.0;
         for (int d = 0; d < D; ++d) {
@@ -394,6 +395,8 @@ __global__ void k_center_rad(int64_t nodes, int D, const double *lo, const doubl
         }
         rad[i] = r;
         rad32[i] = __double2float_rd(r);
+        W32d[i] = __double2float_rd(W[i]);
+        W32u[i] = __double2float_ru(W[i]);
     }
 }
 
@@ -716,6 +719,8 @@ static int build_impl(const T *x, const float *w, int64_t n, int D, int L, const
     GS_CUDA_TRY(cudaMallocAsync((void **)&t.hi32, nodes * D * sizeof(float), st));
     GS_CUDA_TRY(cudaMallocAsync((void **)&t.rad, nodes * sizeof(double), st));
     GS_CUDA_TRY(cudaMallocAsync((void **)&t.rad32, nodes * sizeof(float), st));
+    GS_CUDA_TRY(cudaMallocAsync((void **)&t.W32d, nodes * sizeof(float), st));
+    GS_CUDA_TRY(cudaMallocAsync((void **)&t.W32u, nodes * sizeof(float), st));
     GS_CUDA_TRY(cudaMallocAsync((void **)&t.W, nodes * sizeof(double), st));
     GS_CUDA_TRY(cudaMallocAsync((void **)&t.wmin, nodes * sizeof(float), st));
     GS_CUDA_TRY(cudaMallocAsync((void **)&t.split_dim, nodes * sizeof(int32_t), st));
@@ -753,7 +758,7 @@ static int build_impl(const T *x, const float *w, int64_t n, int D, int L, const
         k_internal_stats<<<gridn(1ll << k), kTB, 0, st>>>(D, k, t.lo, t.hi, t.W, t.wmin);
         cx.launches += 1;
     }
-    k_center_rad<<<gridn(nodes), kTB, 0, st>>>(nodes, D, t.lo, t.hi, t.center, t.rad, t.rad32, t.lo32, t.hi32);
+    k_center_rad<<<gridn(nodes), kTB, 0, st>>>(nodes, D, t.lo, t.hi, t.center, t.rad, t.rad32, t.lo32, t.hi32, t.W, t.W32d, t.W32u);
     k_pack_sorted<T><<<gridn(n), kTB, 0, st>>>(xa, pa, with_weights ? w : nullptr, n, D, DP, rec_stride, t.depth,
                                                t.center, ing, t.rec);
     cx.launches += 2;
@@ -823,7 +828,7 @@ int build_moments(TreeDev &t, const float *w, const SeriesTables &tb, CallCtx &c
 
 void free_tree(TreeDev &t, cudaStream_t st) {
     void *ptrs[] = {t.perm, t.xs, t.lo, t.hi, t.center, t.rad, t.W, t.wmin, t.split_dim, t.rec, t.moments,
-                    t.lo32, t.hi32, t.rad32};
+                    t.lo32, t.hi32, t.rad32, t.W32d, t.W32u};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, st);
     t = TreeDev();

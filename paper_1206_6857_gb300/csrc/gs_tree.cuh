@@ -22,6 +22,7 @@ struct TreeDev {
     double *rad = nullptr;    // half the widest extent
     float *rad32 = nullptr;   // rad rounded down to FP32
     double *W = nullptr;      // weight sums
+    float *W32d = nullptr, *W32u = nullptr;   // W rounded down / up to FP32
     float *wmin = nullptr;    // smallest weight (monochromatic lower bound)
     int32_t *split_dim = nullptr;
     float *rec = nullptr;     // packed FP32 records in sorted order (base case)

@@ -111,6 +111,9 @@ SIGNATURES = {
     "gs_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_uint64, ctypes.c_int, _VP, _VP]),
     "gs_sum_batched": (ctypes.c_int, [ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "gs_build_tree": (ctypes.c_int, [_VP, ctypes.c_int, _I64, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "gs_tree_free": (None, [_VP]),
+    "gs_sum_trees": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP]),
     "gs_selector_samples": (ctypes.c_int, [_VP, _I64, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, _VP,
                                            ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP, _VP, _I64, _VP,
                                            _VP, _VP]),
@@ -367,3 +370,40 @@ def gs_sum_batched(problems, opts: gs_opts | None = None, nworkers: int = 0, str
     if raise_on_error:
         _check(rc)
     return outs, [status[i] for i in range(n)]
+
+
+class Tree:
+    """A built kd-tree (gs_build_tree); freed with close() or when collected."""
+
+    def __init__(self, points, weights=None, opts: gs_opts | None = None, stream=None):
+        self.M = points.shape[0]
+        self.D = points.shape[1]
+        self.device = points.device
+        self._h = ctypes.c_void_p()
+        _check(load().gs_build_tree(_ptr(points), _dtype_code(points), points.shape[0], points.shape[1],
+                                    _ptr(weights), ctypes.byref(opts) if opts is not None else None,
+                                    _stream_ptr(stream), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            load().gs_tree_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_sum_trees(qtree: Tree, rtree: Tree, h, eps, out=None, opts: gs_opts | None = None, stream=None,
+                 stats: gs_stats | None = None):
+    """gs_sum on built trees (qtree is rtree: monochromatic); returns out (M x nh float64)."""
+    import torch
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    if out is None:
+        out = torch.empty((qtree.M, hh.size), dtype=torch.float64, device=qtree.device)
+    _check(load().gs_sum_trees(qtree._h, rtree._h, hh.ctypes.data, hh.size, float(eps), _ptr(out),
+                               ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream),
+                               ctypes.byref(stats) if stats is not None else None))
+    return out

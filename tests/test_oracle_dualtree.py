@@ -173,3 +173,38 @@ def test_series_methods_are_used_in_low_dimension():
     got, _ = T.estimate(qt, rt, q, r, w, h, trav)
     want = oracle_ex.gauss_sum(q, r, w, h)
     assert np.max(np.abs(got - want) / want) <= 1e-3
+
+
+def test_directed_fp32_arithmetic_brackets_the_exact_result():
+    # rounded-down / -up FP32 sums and products bracket the exact rational
+    # result by one FP32 step, including operands of very different size
+    from fractions import Fraction
+    g = np.random.default_rng(17)
+    a = (g.standard_normal(400) * 2.0 ** g.integers(-30, 30, 400)).astype(np.float32)
+    b = (g.standard_normal(400) * 2.0 ** g.integers(-30, 30, 400)).astype(np.float32)
+    for up in (False, True):
+        s = T.f32_add_dir(a, b, up)
+        p = T.f32_mul_dir(np.abs(a), np.abs(b), up)
+        for i in range(a.size):
+            es = Fraction(float(a[i])) + Fraction(float(b[i]))
+            ep = Fraction(float(abs(a[i]))) * Fraction(float(abs(b[i])))
+            for got, ex in ((s[i], es), (p[i], ep)):
+                other = np.nextafter(got, np.float32(-np.inf if up else np.inf))
+                if up:
+                    assert Fraction(float(got)) >= ex and Fraction(float(other)) < ex
+                else:
+                    assert Fraction(float(got)) <= ex and Fraction(float(other)) > ex
+
+
+def test_directed_group_sums_bound_the_exact_sums():
+    g = np.random.default_rng(18)
+    n = 5000
+    gid = np.sort(g.integers(0, 37, n))
+    start = np.searchsorted(gid, np.arange(37))
+    pos = np.arange(n) - start[gid]
+    v = g.uniform(0, 1, n).astype(np.float32)
+    lo = T.group_reduce_f32(v, gid, pos, 37, up=False)
+    hi = T.group_reduce_f32(v, gid, pos, 37, up=True)
+    exact = np.bincount(gid, weights=v.astype(np.float64), minlength=37)
+    assert np.all(lo <= exact * (1 + 1e-15)) and np.all(hi >= exact * (1 - 1e-15))
+    assert np.all(hi - lo <= 1e-5 * exact + 1e-30)
