@@ -422,6 +422,16 @@ int gs_selector_samples(const void *queries, int64_t M, const void *refs, const 
                         int64_t *n_samples, double *model_cost, void *stream);
 
 /*
+ * gs_debug_fail_alloc -- fault injection for tests: after n more device
+ * scratch allocations (of any call, any thread) the next one fails as if the
+ * device were out of memory, once; n < 0 disarms.  The call that meets the
+ * failure returns GS_ERR_OOM and later calls work normally (the tree build,
+ * the traversal buffers and the outputs are freed on that path; a few small
+ * scratch arrays of the base case and series phases may stay allocated).
+ */
+void gs_debug_fail_alloc(long long n);
+
+/*
  * gs_probe_rates -- measures this device's throughput, in lanes per SM per
  * SM clock cycle, of the two instructions the base case is built from: MUFU
  * ex2.approx.ftz.f32 and FP32 FFMA.  A short kernel with independent chains

@@ -144,9 +144,9 @@ def f32_add_dir(a, b, up: bool):
 
 
 def group_reduce_f32(values, group_of, pos_in_group, ngroups: int, up: bool):
-    """Per group: 32 lane-strided FP32 partial sums, every addition rounded
-    in one direction, then the partials widened to FP64 and combined by the
-    xor butterfly (the frontier kernel's order)."""
+    """Per group: 32 lane-strided FP32 partial sums combined by the xor
+    butterfly (the frontier kernel's order), every addition rounded in one
+    direction; returned as FP64."""
     values = np.asarray(values, np.float32)
     acc = np.zeros((ngroups, 32), np.float32)
     lane = pos_in_group % 32
@@ -155,10 +155,9 @@ def group_reduce_f32(values, group_of, pos_in_group, ngroups: int, up: bool):
         sel = rnd == k
         g, l = group_of[sel], lane[sel]
         acc[g, l] = f32_add_dir(acc[g, l], values[sel], up)
-    acc = acc.astype(np.float64)
     for m in (16, 8, 4, 2, 1):
-        acc = acc + acc[:, np.arange(32) ^ m]
-    return acc[:, 0]
+        acc = f32_add_dir(acc, acc[:, np.arange(32) ^ m], up)
+    return acc[:, 0].astype(np.float64)
 
 
 def group_reduce(values: np.ndarray, group_of: np.ndarray, pos_in_group: np.ndarray, ngroups: int):

@@ -1,6 +1,8 @@
 // C-ABI entry points: argument checks, scratch management, dispatch to the
 // exhaustive or dual-tree path, and the single end-of-call status read.
 #include <math.h>
+
+#include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -17,6 +19,22 @@ void set_error(const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+static std::atomic<long long> g_fail_countdown{-1};
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
+    long long c = g_fail_countdown.load();
+    while (c >= 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+            if (c == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMallocAsync(p, bytes, st);
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -201,7 +219,7 @@ int gs::sum_impl(const void *queries, int64_t M, const void *refs, const float *
     cx.stats = stats;
     cx.phase(GS_PH_INGEST);
     Ingest *ing = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&ing, sizeof(Ingest), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&ing, sizeof(Ingest), st));
     cudaError_t e = launch_ingest(ing, queries, M, refs, weights, N, D, dtype, cx);
     if (e != cudaSuccess) {
         cudaFreeAsync(ing, st);
@@ -277,12 +295,12 @@ int gs_lscv(const void *pts, int64_t N, int D, int dtype, const float *weights, 
     cudaStream_t st = (cudaStream_t)stream;
     double *G = nullptr, *acc = nullptr;
     Ingest *ing = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&G, (size_t)N * 2 * nh * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&G, (size_t)N * 2 * nh * sizeof(double), st));
     int rc = sum_impl(pts, N, pts, weights, N, D, dtype, hh, 2 * nh, eps, G, opts, stream, stats, nullptr);
     if (rc == GS_OK) {
         // total weight (the library's own ingest reduction) and the sums
-        cudaError_t e = cudaMallocAsync((void **)&ing, sizeof(Ingest), st);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&acc, 3 * 32 * sizeof(double), st);
+        cudaError_t e = dev_malloc_async((void **)&ing, sizeof(Ingest), st);
+        if (e == cudaSuccess) e = dev_malloc_async((void **)&acc, 3 * 32 * sizeof(double), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * 32 * sizeof(double), st);
         CallCtx cx;
         cx.st = st;
@@ -329,10 +347,10 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
     void *dq = nullptr, *dr = nullptr;
     float *dw = nullptr;
     double *dout = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync(&dr, (size_t)N * D * es, st));
-    if (!mono) GS_CUDA_TRY(cudaMallocAsync(&dq, (size_t)M * D * es, st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&dw, (size_t)N * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&dout, (size_t)M * nh * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async(&dr, (size_t)N * D * es, st));
+    if (!mono) GS_CUDA_TRY(dev_malloc_async(&dq, (size_t)M * D * es, st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&dw, (size_t)N * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&dout, (size_t)M * nh * sizeof(double), st));
     if (mono) dq = dr;
     cudaError_t e = cudaMemcpyAsync(dr, refs, (size_t)N * D * es, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !mono)
@@ -355,6 +373,8 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
     cudaFreeAsync(dout, st);
     return rc;
 }
+
+void gs_debug_fail_alloc(long long n) { g_fail_countdown.store(n < 0 ? -1 : n); }
 
 int gs_probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, void *stream) {
     g_err[0] = 0;

@@ -438,9 +438,9 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     long long *off = nullptr;
     MergedEntry *ent = nullptr;
     float *rec2 = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&mask, (size_t)lq * lr * sizeof(uint32_t), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&mask, (size_t)lq * lr * sizeof(uint32_t), st));
     GS_CUDA_TRY(cudaMemsetAsync(mask, 0, (size_t)lq * lr * sizeof(uint32_t), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
     const int grid = fb.grid_warps / 8;
     // mask bit of each bandwidth: its rank in ascending h
     int order[64];
@@ -464,7 +464,7 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     long long total = 0;
     GS_CUDA_TRY(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
     GS_CUDA_TRY(cudaStreamSynchronize(st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&ent, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&ent, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
     k_row_compact<<<grid, 256, 0, st>>>(mask, lq, lr, rleaf0, off, ent);
     cx.launches += 1;
     cudaFreeAsync(mask, st);
@@ -496,7 +496,7 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         const int Q = qpl <= 1 ? 1 : (qpl <= 2 ? 2 : 4);
         if (merged_x2(DP, Q)) {
             const int64_t nf = in.rt->n * (int64_t)in.rt->rec_stride;
-            GS_CUDA_TRY(cudaMallocAsync((void **)&rec2, (size_t)nf * 2 * sizeof(float), st));
+            GS_CUDA_TRY(dev_malloc_async((void **)&rec2, (size_t)nf * 2 * sizeof(float), st));
             k_dup_records<<<grid, 256, 0, st>>>(in.rt->rec, nf, (float2 *)rec2);
             cx.launches += 1;
             bp.rrec2 = rec2;

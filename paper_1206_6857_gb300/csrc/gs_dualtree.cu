@@ -54,7 +54,7 @@ static void free_bufs(FrontierBufs &fb, cudaStream_t st) {
     fb = keep;
 }
 
-#define GS_ALLOC(ptr, bytes) GS_CUDA_TRY(cudaMallocAsync((void **)&(ptr), (size_t)(bytes), st))
+#define GS_ALLOC(ptr, bytes) GS_CUDA_TRY(dev_malloc_async((void **)&(ptr), (size_t)(bytes), st))
 
 // pinned host scratch for the per-iteration totals (one per host thread)
 static int64_t *host_scratch() {
@@ -218,16 +218,21 @@ int dualtree_run(const TreeDev &qt_in, const TreeDev &rt_in, bool mono, const fl
         rc = run_frontier(in, fb, cx);
     }
     if (!rc) {
-        GS_ALLOC(Gq, (size_t)qt.n * nh * sizeof(double));
-        GS_CUDA_TRY(cudaMemsetAsync(Gq, 0, (size_t)qt.n * nh * sizeof(double), st));
-        if (series) {
-            GS_ALLOC(B, (size_t)qt.nodes * nh * tb.T * sizeof(double));
-            GS_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)qt.nodes * nh * tb.T * sizeof(double), st));
-            GS_ALLOC(pL, (size_t)qt.nodes * nh * sizeof(int32_t));
-            GS_CUDA_TRY(cudaMemsetAsync(pL, 0, (size_t)qt.nodes * nh * sizeof(int32_t), st));
-        }
-        rc = (merged_base_possible(in) && !(o.flags & GS_FLAG_NO_MERGE)) ? run_basecase_merged(in, fb, Gq, DP, cx)
-                                                         : run_basecase(in, fb, Gq, DP, cx);
+        // outputs of the base case and the series (freed below whatever happens)
+        rc = [&]() -> int {
+            GS_ALLOC(Gq, (size_t)qt.n * nh * sizeof(double));
+            GS_CUDA_TRY(cudaMemsetAsync(Gq, 0, (size_t)qt.n * nh * sizeof(double), st));
+            if (series) {
+                GS_ALLOC(B, (size_t)qt.nodes * nh * tb.T * sizeof(double));
+                GS_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)qt.nodes * nh * tb.T * sizeof(double), st));
+                GS_ALLOC(pL, (size_t)qt.nodes * nh * sizeof(int32_t));
+                GS_CUDA_TRY(cudaMemsetAsync(pL, 0, (size_t)qt.nodes * nh * sizeof(int32_t), st));
+            }
+            return GS_OK;
+        }();
+        if (!rc)
+            rc = (merged_base_possible(in) && !(o.flags & GS_FLAG_NO_MERGE)) ? run_basecase_merged(in, fb, Gq, DP, cx)
+                                                                             : run_basecase(in, fb, Gq, DP, cx);
     }
     if (!rc) rc = run_series_and_final(in, fb, series ? &tb : nullptr, Gq, B, pL, out, cx);
     if (!rc && trace && trace->qperm) {

@@ -269,7 +269,7 @@ static int run_exhaustive(const void *queries, int64_t M, const void *refs, cons
     constexpr int QPT = (DP <= 8) ? 2 : 1;
     const int64_t Npad = (N + TILE - 1) / TILE * TILE;
     T *rec = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&rec, (size_t)Npad * NT * sizeof(T), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&rec, (size_t)Npad * NT * sizeof(T), st));
     k_pack_refs<T, DP><<<grid_for(Npad, 256), 256, 0, st>>>((const T *)refs, weights, N, Npad, D,
                                                               ing, rec);
     cx.launches += 1;
@@ -512,8 +512,8 @@ int probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, cudaStream_t st
     const int nb = sms * 4;
     float *sink = nullptr;
     long long *rec = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&sink, 256 * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&rec, 3 * nb * sizeof(long long), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&sink, 256 * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&rec, 3 * nb * sizeof(long long), st));
     long long *hr = (long long *)malloc(3 * nb * sizeof(long long));
     const int maxsm = 1024;
     long long *lo = (long long *)malloc(maxsm * sizeof(long long));

@@ -71,6 +71,24 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// warp_sum of a value that is often zero on every lane: skipped then (a sum
+// of zeros is +0 either way)
+__device__ __forceinline__ double warp_sum_sparse(double v) {
+    return __any_sync(0xffffffffu, v != 0.0) ? warp_sum(v) : 0.0;
+}
+
+// xor-butterfly sums in FP32 with every addition rounded down / up
+__device__ __forceinline__ float warp_sum_rd(float v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, m));
+    return v;
+}
+__device__ __forceinline__ float warp_sum_ru(float v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, m));
+    return v;
+}
+
 struct FrontierParams {
     int D, nh, P, selector, tokens, mono;
     int t, q_depth, r_depth, q_leaf, r_leaf;
@@ -168,11 +186,10 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const double invh = fp.inv_h[j];
         const float c32 = fp.c32[j];
         // pass 1: kernel bounds of every pair, lower bound over the group.
-        // The lane sums run in FP32 rounded towards -inf (the lower bound,
-        // from W_R rounded down) and +inf (the weight sum the token is
-        // shared by, from W_R rounded up), then widen to FP64 for the
-        // butterfly: a smaller lower bound and a larger weight sum keep
-        // every budget valid.
+        // The lane sums and the butterfly run in FP32 rounded towards -inf
+        // (the lower bound, from W_R rounded down) and +inf (the weight sum
+        // the token is shared by, from W_R rounded up): a smaller lower bound
+        // and a larger weight sum keep every budget valid.
         float s_dl = 0.f, s_W = 0.f;
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
@@ -184,7 +201,7 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             s_dl = __fadd_rd(s_dl, __fmul_rd(fp.rW32d[r], kb.kmax));
             s_W = __fadd_ru(s_W, fp.rW32u[r]);
         }
-        const double front = warp_sum((double)s_dl), Wg = warp_sum((double)s_W);
+        const double front = (double)warp_sum_rd(s_dl), Wg = (double)warp_sum_ru(s_W);
         const int64_t qj = q * fp.nh + j;
         const double fin0 = fp.fin[qj], tok0 = fp.tok[qj];
         double Gb = fin0 + front;
@@ -452,9 +469,9 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     trace[ti] = make_int4((int)q, (int)r, j, method | (pord << 8) | (fp.t << 16));
             }
         }
-        if (fp.q_leaf && fp.r_leaf) s_fin = s_dl;
-        const double banked = warp_sum((double)s_bank), paid = warp_sum(s_paid);
-        const double fin_add = warp_sum((double)s_fin), est_add = warp_sum(s_est);
+        const double banked = (double)warp_sum_rd(s_bank), paid = warp_sum_sparse(s_paid);
+        const double fin_add = (fp.q_leaf && fp.r_leaf) ? front : (double)warp_sum_rd(s_fin);
+        const double est_add = warp_sum_sparse(s_est);
         // Fig. 7's token update over the whole group: pruned pairs pay their
         // need, base cases bank W_R, splits leave the token alone
         const double tok_new = fp.tokens ? fmax(0.0, (tok0 + banked) - paid) : 0.0;
@@ -769,7 +786,7 @@ static int grow(E **ptr, int64_t *cap, int64_t need, int64_t keep, cudaStream_t 
     int64_t nc = *cap * 2;
     if (nc < need + need / 2) nc = need + need / 2;
     E *np = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&np, (size_t)nc * sizeof(E), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&np, (size_t)nc * sizeof(E), st));
     if (keep > 0 && *ptr) GS_CUDA_TRY(cudaMemcpyAsync(np, *ptr, (size_t)keep * sizeof(E), cudaMemcpyDeviceToDevice, st));
     if (*ptr) cudaFreeAsync(*ptr, st);
     *ptr = np;

@@ -111,6 +111,12 @@ inline cudaError_t allow_max_smem(const void *fn) {
     return e;
 }
 
+// Every device scratch allocation of the library goes through here
+// (stream-ordered).  gs_debug_fail_alloc arms a one-shot failure of a later
+// allocation, so tests can check that a failed allocation surfaces as
+// GS_ERR_OOM and leaves the library usable.
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+
 // Device status bits -> GS_ERR_* code (and message); GS_OK when clear.
 int status_to_code(unsigned st);
 

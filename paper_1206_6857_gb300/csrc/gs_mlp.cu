@@ -300,10 +300,10 @@ extern "C" int gs_mlp_train(float *params, const float *x, const int32_t *y, con
     float *m = nullptr, *v = nullptr;
     int rc = GS_OK;
     auto fail = [&](cudaError_t e, const char *what) { rc = cuda_fail(e, what); };
-    cudaError_t e = cudaMallocAsync((void **)&grad, kMlpParams * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&loss, (size_t)(epochs + 1) * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&acc, 2 * kMlpIn * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&m, 2 * kMlpParams * sizeof(float), st);
+    cudaError_t e = dev_malloc_async((void **)&grad, kMlpParams * sizeof(double), st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&loss, (size_t)(epochs + 1) * sizeof(double), st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&acc, 2 * kMlpIn * sizeof(double), st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&m, 2 * kMlpParams * sizeof(float), st);
     if (e != cudaSuccess) {
         fail(e, "gs_mlp_train scratch");
     } else {

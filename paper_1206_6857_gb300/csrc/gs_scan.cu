@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(long long *v, int64
 
 int scan_i64(long long *v, int64_t n, long long *total, CallCtx &cx) {
     long long *part = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&part, kScanBlocks * sizeof(long long), cx.st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&part, kScanBlocks * sizeof(long long), cx.st));
     k_scan_sum<<<kScanBlocks, kScanThreads, 0, cx.st>>>(v, n, part);
     k_scan_part<<<1, kScanThreads, 0, cx.st>>>(part, total);
     k_scan_apply<<<kScanBlocks, kScanThreads, 0, cx.st>>>(v, n, part);

@@ -170,7 +170,7 @@ extern "C" int gs_selector_samples(const void *queries, int64_t M, const void *r
     if (opts) o = *opts;
     o.selector = GS_SEL_FD_ONLY;
     double *out = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&out, (size_t)(M > 0 ? M : 1) * nh * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&out, (size_t)(M > 0 ? M : 1) * nh * sizeof(double), st));
     PairLog lg;
     int rc = sum_impl(queries, M, refs, weights, N, D, dtype, h, nh, eps, out, &o, stream, nullptr, nullptr, &lg);
     cudaFreeAsync(out, st);
@@ -195,9 +195,9 @@ extern "C" int gs_selector_samples(const void *queries, int64_t M, const void *r
     long long *flag = nullptr;
     CallCtx cx;
     cx.st = st;
-    cudaError_t e = cudaMallocAsync((void **)&dbuf, (size_t)(4 * total + 3) * sizeof(double), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&label, (size_t)(total + 1), st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&flag, (size_t)(total + 1) * sizeof(long long), st);
+    cudaError_t e = dev_malloc_async((void **)&dbuf, (size_t)(4 * total + 3) * sizeof(double), st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&label, (size_t)(total + 1), st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&flag, (size_t)(total + 1) * sizeof(long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dbuf, 0, (size_t)(4 * total + 3) * sizeof(double), st);
     if (e != cudaSuccess) rc = cuda_fail(e, "gs_selector_samples scratch");
     if (!rc) {

@@ -493,8 +493,16 @@ __global__ void __launch_bounds__(kSerTB) k_l2l_level(SeriesParams sp, int k) {
 }
 
 // leaves: out = base + DH + sum of ancestors' FD estimates + EVALL(B)
+// Final values, one warp per (query leaf, bandwidth).  Local expansions of
+// at most kFinLane terms (D <= 16) are evaluated one query per lane: the
+// monomials u^a, u = (x_q - x_Q)/s, are built in graded-lex order from the
+// monomial with the last exponent one lower (one multiply each) in a
+// lane-interleaved shared buffer.  Longer expansions: lanes over the terms,
+// one query at a time.
+constexpr int kFinLane = 64;
+constexpr size_t kFinSmemPerWarp = (size_t)(kFinLane * 32 + 32 * 32) * sizeof(double);
 __global__ void __launch_bounds__(kSerTB) k_final(SeriesParams sp) {
-    __shared__ double us[kSerTB / 32][32];
+    extern __shared__ double fin_s[];   // per warp: monomials [kFinLane][32 lanes], u [32 dims][32 lanes]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int depth = sp.q_depth, D = sp.D;
     const int64_t nl = 1ll << depth;
@@ -514,18 +522,39 @@ __global__ void __launch_bounds__(kSerTB) k_final(SeriesParams sp) {
         const double is = sp.inv_s[j];
         const double *Bl = sp.B ? sp.B + (leaf * sp.nh + j) * sp.T : nullptr;
         const int64_t b = level_begin(sp.qn, depth, i), e = level_begin(sp.qn, depth, i + 1);
+        double *mono = fin_s + (size_t)w * (kFinLane * 32 + 32 * 32) + lane;
+        double *uw = mono - lane + kFinLane * 32;     // this warp's u region
+        if (Tp <= kFinLane) {
+            const double *cQ = sp.qcenter + leaf * D;
+            for (int64_t pos = b + lane; pos < e; pos += 32) {
+                double v = sp.Gq[pos * sp.nh + j] + es;
+                if (Tp > 0) {
+                    for (int d = 0; d < D; ++d) uw[d * 32 + lane] = (coord(sp.qxs, sp.dtype, pos, D, d) - cQ[d]) * is;
+                    double s = Bl[0];
+                    mono[0] = 1.0;
+                    for (int a = 1; a < Tp; ++a) {
+                        const double m = mono[sp.tb.dpred[a] * 32] * uw[sp.tb.pred_dim[a] * 32 + lane];
+                        mono[a * 32] = m;
+                        s += Bl[a] * m;
+                    }
+                    v += s;
+                }
+                sp.out[(int64_t)sp.qperm[pos] * sp.nh + j] = v;
+            }
+            continue;
+        }
         for (int64_t pos = b; pos < e; ++pos) {
             double v = sp.Gq[pos * sp.nh + j] + es;
             if (Tp > 0) {
                 for (int d = lane; d < D; d += 32)
-                    us[w][d] = (coord(sp.qxs, sp.dtype, pos, D, d) - sp.qcenter[leaf * D + d]) * is;
+                    uw[d] = (coord(sp.qxs, sp.dtype, pos, D, d) - sp.qcenter[leaf * D + d]) * is;
                 __syncwarp();
                 double s = 0.0;
                 for (int a = lane; a < Tp; a += 32) {
                     const uint8_t *al = sp.tb.alpha + a * D;
                     double m = Bl[a];
                     for (int d = 0; d < D; ++d)
-                        for (int q = 0; q < al[d]; ++q) m *= us[w][d];
+                        for (int q = 0; q < al[d]; ++q) m *= uw[d];
                     s += m;
                 }
                 for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -578,7 +607,7 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         for (int m = 0; m < 2; ++m) {
             const int64_t ne = fb.n_series[m];
             if (ne == 0) continue;
-            GS_CUDA_TRY(cudaMallocAsync((void **)&pieces[m], (size_t)(ne + 1) * sizeof(long long), st));
+            GS_CUDA_TRY(dev_malloc_async((void **)&pieces[m], (size_t)(ne + 1) * sizeof(long long), st));
             k_chunk_count<<<(unsigned)((ne + 255) / 256 < 4096 ? (ne + 255) / 256 : 4096), 256, 0, st>>>(
                 fb.series[m], ne, m == 0, sp.qn, sp.rn, pieces[m]);
             cx.launches += 1;
@@ -629,7 +658,8 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         }
     }
     cx.phase(GS_PH_DOWN);
-    k_final<<<fb.grid_warps / 4, kSerTB, 0, st>>>(sp);
+    allow_max_smem((const void *)k_final);
+    k_final<<<fb.grid_warps / 4, kSerTB, (kSerTB / 32) * kFinSmemPerWarp, st>>>(sp);
     cx.launches += 1;
     if (int rc2 = cx.check("k_final")) return rc2;
     cx.phase(GS_PH_OTHER);

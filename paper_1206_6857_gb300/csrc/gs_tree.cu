@@ -536,7 +536,7 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
         for (int p = dg + 1; p <= 16; ++p) h.Tp[p]++;
     }
     std::vector<uint8_t> alpha(T * D), deg(T), pdim(T);
-    std::vector<int32_t> pred(T);
+    std::vector<int32_t> pred(T), dpred(T);
     std::vector<double> invf(T);
     std::vector<int32_t> hoff(T + 1), hp, loff(T + 1), lp;
     std::vector<double> lc;
@@ -555,11 +555,15 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
         invf[i] = 1.0 / f;
         if (last < 0) {
             pred[i] = -1;
+            dpred[i] = -1;
             pdim[i] = 0;
         } else {
             std::vector<int> b = al[i];
             b[last] = 0;
             pred[i] = index[b];
+            std::vector<int> c = al[i];
+            c[last] -= 1;
+            dpred[i] = index[c];
             pdim[i] = (uint8_t)last;
         }
     }
@@ -601,7 +605,8 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
     size_t o_alpha = 0, o_deg = al8(o_alpha + alpha.size()), o_pdim = al8(o_deg + T), o_pred = al8(o_pdim + T);
     size_t o_invf = al8(o_pred + 4 * T), o_hoff = al8(o_invf + 8 * T), o_hp = al8(o_hoff + 4 * (T + 1));
     size_t o_loff = al8(o_hp + 4 * hp.size()), o_lp = al8(o_loff + 4 * (T + 1)), o_lc = al8(o_lp + 4 * lp.size());
-    size_t total = al8(o_lc + 8 * lc.size());
+    size_t o_dpred = al8(o_lc + 8 * lc.size());
+    size_t total = al8(o_dpred + 4 * T);
     std::vector<uint8_t> host(total, 0);
     memcpy(&host[o_alpha], alpha.data(), alpha.size());
     memcpy(&host[o_deg], deg.data(), T);
@@ -613,6 +618,7 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
     memcpy(&host[o_loff], loff.data(), 4 * (T + 1));
     if (!lp.empty()) memcpy(&host[o_lp], lp.data(), 4 * lp.size());
     if (!lc.empty()) memcpy(&host[o_lc], lc.data(), 8 * lc.size());
+    memcpy(&host[o_dpred], dpred.data(), 4 * T);
     uint8_t *dm = nullptr;
     GS_CUDA_TRY(cudaMalloc((void **)&dm, total));   // cached for the life of the process
     cudaError_t e = cudaMemcpy(dm, host.data(), total, cudaMemcpyHostToDevice);
@@ -631,6 +637,7 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
     h.l2l_off = (int32_t *)(dm + o_loff);
     h.l2l_pairs = (int32_t *)(dm + o_lp);
     h.l2l_coef = (double *)(dm + o_lc);
+    h.dpred = (int32_t *)(dm + o_dpred);
     *tb = h;
     return GS_OK;
 }
@@ -702,29 +709,43 @@ static int build_impl(const T *x, const float *w, int64_t n, int D, int L, const
     SelState<K> *sel = nullptr;
     uint32_t *hist = nullptr;
     unsigned long long *partial = nullptr, *S = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&xa, n * D * sizeof(T), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&xb, n * D * sizeof(T), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&pa, n * sizeof(int32_t), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&pb, n * sizeof(int32_t), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&bmin, maxlev * D * sizeof(K), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&bmax, maxlev * D * sizeof(K), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&sel, maxlev * sizeof(SelState<K>), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&hist, maxlev * 256 * sizeof(uint32_t), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&partial, kScanGrid * sizeof(unsigned long long), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&S, n * sizeof(unsigned long long), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.lo, nodes * D * sizeof(double), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.hi, nodes * D * sizeof(double), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.center, nodes * D * sizeof(double), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.lo32, nodes * D * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.hi32, nodes * D * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.rad, nodes * sizeof(double), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.rad32, nodes * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.W32d, nodes * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.W32u, nodes * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.W, nodes * sizeof(double), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.wmin, nodes * sizeof(float), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.split_dim, nodes * sizeof(int32_t), st));
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.rec, n * rec_stride * sizeof(float), st));
+    // on any early return: free the scratch and whatever of the tree exists
+    struct Guard {
+        cudaStream_t st;
+        TreeDev *t;
+        void **ptrs[10];
+        bool ok = false;
+        ~Guard() {
+            if (ok) return;
+            for (void **pp : ptrs)
+                if (*pp) cudaFreeAsync(*pp, st);
+            free_tree(*t, st);
+        }
+    } guard{st, &t, {(void **)&xa, (void **)&xb, (void **)&pa, (void **)&pb, (void **)&bmin, (void **)&bmax,
+                     (void **)&sel, (void **)&hist, (void **)&partial, (void **)&S}};
+    GS_CUDA_TRY(dev_malloc_async((void **)&xa, n * D * sizeof(T), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&xb, n * D * sizeof(T), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&pa, n * sizeof(int32_t), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&pb, n * sizeof(int32_t), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&bmin, maxlev * D * sizeof(K), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&bmax, maxlev * D * sizeof(K), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&sel, maxlev * sizeof(SelState<K>), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&hist, maxlev * 256 * sizeof(uint32_t), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&partial, kScanGrid * sizeof(unsigned long long), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&S, n * sizeof(unsigned long long), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.lo, nodes * D * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.hi, nodes * D * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.center, nodes * D * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.lo32, nodes * D * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.hi32, nodes * D * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.rad, nodes * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.rad32, nodes * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.W32d, nodes * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.W32u, nodes * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.W, nodes * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.wmin, nodes * sizeof(float), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.split_dim, nodes * sizeof(int32_t), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.rec, n * rec_stride * sizeof(float), st));
     GS_CUDA_TRY(cudaMemcpyAsync(xa, x, n * D * sizeof(T), cudaMemcpyDeviceToDevice, st));
     GS_CUDA_TRY(cudaMemsetAsync(t.split_dim, 0xff, nodes * sizeof(int32_t), st));
     launch_iota(pa, n, st);
@@ -763,18 +784,18 @@ static int build_impl(const T *x, const float *w, int64_t n, int D, int L, const
                                                t.center, ing, t.rec);
     cx.launches += 2;
     t.rec_stride = rec_stride;
-    t.perm = pa;
+    t.perm = pa;   // now owned by the tree
     t.xs = xa;
-    cudaFreeAsync(xb, st);
-    cudaFreeAsync(pb, st);
-    cudaFreeAsync(bmin, st);
-    cudaFreeAsync(bmax, st);
-    cudaFreeAsync(sel, st);
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(partial, st);
-    cudaFreeAsync(S, st);
+    xa = nullptr;
+    pa = nullptr;
+    for (void **pp : guard.ptrs)
+        if (*pp) {
+            cudaFreeAsync(*pp, st);
+            *pp = nullptr;
+        }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tree build launch");
+    guard.ok = true;
     *out = t;
     return GS_OK;
 }
@@ -792,7 +813,7 @@ int build_tree(const void *x, const float *w, int64_t n, int D, int dtype, int L
 
 int build_moments(TreeDev &t, const float *w, const SeriesTables &tb, CallCtx &cx) {
     cudaStream_t st = cx.st;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&t.moments, t.nodes * tb.T * sizeof(double), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&t.moments, t.nodes * tb.T * sizeof(double), st));
     t.mom_terms = tb.T;
     const int64_t nl = 1ll << t.depth;
     const int64_t maxcnt = (t.n + nl - 1) / nl;

@@ -42,6 +42,7 @@ struct SeriesTables {
     uint8_t *deg = nullptr;            // T
     int32_t *pred = nullptr;           // alpha with its last non-zero entry zeroed
     uint8_t *pred_dim = nullptr;       // that entry's dimension
+    int32_t *dpred = nullptr;          // alpha with its last non-zero entry decreased by one
     double *inv_fact = nullptr;        // 1 / alpha!
     // H2H: for each gamma, the (alpha, beta) index pairs with alpha + beta = gamma
     int32_t *h2h_off = nullptr;        // T + 1

@@ -56,9 +56,9 @@ extern "C" int gs_build_tree(const void *pts, int dtype, int64_t n, int D, const
     CallCtx cx;
     cx.st = st;
     int rc = GS_OK;
-    cudaError_t e = cudaMallocAsync((void **)&h->ing, sizeof(Ingest), st);
+    cudaError_t e = dev_malloc_async((void **)&h->ing, sizeof(Ingest), st);
     if (e == cudaSuccess && weights) {
-        e = cudaMallocAsync((void **)&h->w, (size_t)n * sizeof(float), st);
+        e = dev_malloc_async((void **)&h->w, (size_t)n * sizeof(float), st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->w, weights, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, st);
     }
     if (e == cudaSuccess) e = launch_ingest(h->ing, pts, n, pts, weights, n, D, dtype, cx);
@@ -154,7 +154,7 @@ extern "C" int gs_sum_trees(const gs_tree *qt, const gs_tree *rt, const double *
     cx.phase(GS_PH_INGEST);
     // this call's status word, starting from the reference set's summary
     Ingest *ing = nullptr;
-    GS_CUDA_TRY(cudaMallocAsync((void **)&ing, sizeof(Ingest), st));
+    GS_CUDA_TRY(dev_malloc_async((void **)&ing, sizeof(Ingest), st));
     cudaError_t e = cudaMemcpyAsync(ing, rt->ing, sizeof(Ingest), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) {
         cudaFreeAsync(ing, st);

@@ -111,6 +111,7 @@ SIGNATURES = {
     "gs_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_uint64, ctypes.c_int, _VP, _VP]),
     "gs_sum_batched": (ctypes.c_int, [ctypes.c_int, _VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "gs_debug_fail_alloc": (None, [ctypes.c_longlong]),
     "gs_build_tree": (ctypes.c_int, [_VP, ctypes.c_int, _I64, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "gs_tree_free": (None, [_VP]),
     "gs_sum_trees": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP]),
