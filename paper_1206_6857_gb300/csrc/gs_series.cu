@@ -270,9 +270,10 @@ __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent
 // ---------------------------------------------------------------------------
 // H2L.  Warps take tiles of 32 consecutive actions.  Orders 1 and 2 (the
 // bulk of the actions: one and 1 + D coefficients) take one lane each, with
-// the Lemma 1 sums written out:
+// the Lemma 1 sums written out (H_1(t) = 2t, H_2(t) = 4t^2 - 2):
 //   b = 0:    s_0   = A_0 + sum_i A_{e_i} H_1(t_i),
-//   b = e_k:  s_e_k = H_1(t_k) (s_0 - A_{e_k} H_1(t_k)) + A_{e_k} H_2(t_k),
+//   b = e_k:  s_e_k = H_1(t_k) (s_0 - A_{e_k} H_1(t_k)) + A_{e_k} H_2(t_k)
+//                   = 2 (t_k s_0 - A_{e_k}),
 // B_b += (-1)^|b| e^{-|t|^2} s_b.  When all 32 actions of a tile add into
 // the same (Q, h) they are summed across the warp first.  Middle orders
 // (at most kLaneT terms) also take one lane each, with A_a and the 1-D
@@ -333,13 +334,10 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
                 atomicMax(&sp.pL[key], pmax);
             }
             if (pmax == 2) {
+                const double m2et = -2.0 * et;
                 for (int k = 0; k < D; ++k) {
                     double u = 0.0;
-                    if (E.p == 2) {
-                        const double t = (cq[k] - cr[k]) * is, ak = mom[1 + k] * is;
-                        const double h1 = 2.0 * t, h2 = 4.0 * t * t - 2.0;
-                        u = -et * (h1 * (s0 - ak * h1) + ak * h2);
-                    }
+                    if (E.p == 2) u = m2et * ((cq[k] - cr[k]) * is * s0 - mom[1 + k] * is);
                     u = warp_sum_d(u);
                     if (lane == 0) atomicAdd(&Bq[1 + k], u);
                 }
@@ -348,11 +346,8 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
             atomicAdd(&Bq[0], et * s0);
             atomicMax(&sp.pL[key], (int)E.p);
             if (E.p == 2) {
-                for (int k = 0; k < D; ++k) {
-                    const double t = (cq[k] - cr[k]) * is, ak = mom[1 + k] * is;
-                    const double h1 = 2.0 * t, h2 = 4.0 * t * t - 2.0;
-                    atomicAdd(&Bq[1 + k], -et * (h1 * (s0 - ak * h1) + ak * h2));
-                }
+                const double m2et = -2.0 * et;
+                for (int k = 0; k < D; ++k) atomicAdd(&Bq[1 + k], m2et * ((cq[k] - cr[k]) * is * s0 - mom[1 + k] * is));
             }
         }
         // ---- middle orders (T_p <= kLaneT, D (2p-1) <= kLaneH): one lane per
