@@ -25,6 +25,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -94,7 +95,7 @@ class ClockSampler:
 
     def __init__(self, bus_id):
         self.bus_id = (bus_id or "").lower()
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "gs_clocks_%d.csv" % os.getpid())
         self.proc = None
 
     def start(self):
@@ -257,7 +258,9 @@ def run_gs(args):
     elif eps > 0 and not args.no_tune:
         from paper_1206_6857_gb300 import autotune
         t0 = time.perf_counter()
-        tuned, _table = autotune.tune(tr, tw, hs, eps, queries=None if wl.mono else tq)
+        # every bandwidth of the step: the merged base case handles them in
+        # blocks of 8, so a subset would favour the wrong leaf size
+        tuned, _table = autotune.tune(tr, tw, hs, eps, h_subset=0, queries=None if wl.mono else tq)
         tuned["tuning_seconds"] = time.perf_counter() - t0
         opts = autotune.options(tuned)
 
@@ -320,8 +323,9 @@ def run_gs(args):
     kname = "k_exhaustive" if eps == 0.0 else "k_basecase"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
             "frac": achieved / peak if peak else None,
-            "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g" % (wl_config(wl, args.mode, eps)["workload"],
-                                                                                args.mode, args.scale)),
+            "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d" % (
+                wl_config(wl, args.mode, eps)["workload"], args.mode, args.scale,
+                (tuned or {}).get("leaf_size", wl.leaf_size))),
             "kernel": kname, "peak_basis": "measured %.1f ex2 lanes/SM/clk x %d SMs x %.0f MHz (median SM clock under load)"
             % (ex2_rate, props.multi_processor_count, sm_mhz),
             "ffma_lanes_per_sm_clk": ffma_rate, "kernel_ms_per_launch": base_ms}

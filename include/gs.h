@@ -47,7 +47,7 @@ extern "C" {
 #define GS_ERR_CAPACITY    -5   /* a device work list outgrew its capacity (see gs_opts)   */
 #define GS_ERR_TIMEOUT     -6   /* a bounded device wait gave up                           */
 #define GS_ERR_CUDA        -7   /* a CUDA runtime call or kernel launch failed             */
-#define GS_ERR_UNSUPPORTED -8   /* valid request this build does not implement             */
+#define GS_ERR_UNSUPPORTED -8   /* valid request the library does not implement            */
 
 /* ---- element types ---------------------------------------------------- */
 #define GS_F32 0

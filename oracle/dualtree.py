@@ -14,8 +14,8 @@ The traversal follows the paper's DITO procedure (Fig. 7) and its pieces:
 FD pruning (Section 5), bestMethod (Fig. 6) over DH / DL / H2L with the Lemma
 4-6 bounds, the Theorem 2 rule with the W_T token scheme, exhaustive leaf-leaf
 base cases (DITOBase) and recursion into child pairs, and the breadth-first
-post-pass (Fig. 8).  Where the paper is silent this reference takes the
-readings listed in the design doc; in short:
+post-pass (Fig. 8).  Where the paper is silent this reference takes these
+readings:
 
   * kd-tree: complete binary tree of depth d = min{k : ceil(n/2^k) <= L};
     node (k, i) holds sorted positions [floor(i n/2^k), floor((i+1) n/2^k));

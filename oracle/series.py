@@ -5,7 +5,7 @@ the paper's definitions in the paper's order; nothing here is blocked, fused or
 reordered.  Notation: s = sqrt(2 h^2); "order p" keeps the multi-indices with
 |alpha| < p (Section 2: C(D+p-1, D) terms; D=2, p=2 gives 3).
 
-Readings taken where the paper is silent or garbled (each listed in the design doc):
+Readings taken where the paper is silent or garbled:
   * graded lexicographic order: |alpha| ascending; inside one degree,
     lexicographically descending in (alpha_1, ..., alpha_D), so degree 1 is
     e_1, e_2, ..., e_D as in the Section 2 worked example;

@@ -24,7 +24,7 @@ import numpy as np
 
 from . import gs
 
-DEFAULT_LEAVES = (32, 64)
+DEFAULT_LEAVES = (32, 64, 128)
 DEFAULT_COSTS = ((32.0, 32.0, 32.0, 1.0), (128.0, 128.0, 16.0, 1.0), (128.0, 128.0, 64.0, 1.0),
                  (512.0, 512.0, 64.0, 1.0), (512.0, 512.0, 256.0, 1.0), (2048.0, 2048.0, 256.0, 1.0))
 

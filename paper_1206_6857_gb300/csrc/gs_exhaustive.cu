@@ -391,7 +391,7 @@ static int run_exhaustive_noalloc(const void *queries, int64_t M, const void *re
     const int64_t Npad = (N + TILE - 1) / TILE * TILE;
     const int64_t max_pad = (int64_t)((kNoAllocBytes - kNoAllocHeader) / (NT * sizeof(T))) / TILE * TILE;
     if (Npad > max_pad) {
-        set_error("gs_sum_exhaustive_noalloc: N=%lld references exceed the %lld this build's fixed "
+        set_error("gs_sum_exhaustive_noalloc: N=%lld references exceed the %lld the library's fixed "
                   "16 MiB scratch holds for D=%d", (long long)N, (long long)max_pad, D);
         return GS_ERR_ARG;
     }

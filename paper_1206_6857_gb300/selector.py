@@ -206,9 +206,9 @@ def _collect(problems, factors=(1.0, 1.0, 1.0)):
 def main(epochs=40, rounds=2, out=PARAMS_FILE):
     """Collect samples from the training problems, train, store the network.
 
-    Round 1 takes the series unit costs measured on the rule's own actions.
+    The first pass takes the series unit costs measured on the rule's own actions.
     The learned policy then picks other actions (larger nodes, higher orders),
-    so each further round measures the unit costs again on a run of the
+    so each further pass measures the unit costs again on a run of the
     current network over a calibration problem, scales every problem's series
     costs by the ratio to the rule's, relabels and retrains."""
     import sys
