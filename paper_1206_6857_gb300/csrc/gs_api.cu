@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <atomic>
+#include <mutex>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -34,7 +35,49 @@ cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
             break;
         }
     }
-    return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = scratch_pool(&pool);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+// The library's own stream-ordered pool, one per device.  The device's
+// default pool returns freed memory to the driver at every synchronisation,
+// so a traversal that synchronises once per frontier iteration would map
+// its lists afresh each time; this pool keeps freed memory until
+// gs_trim_memory releases it.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+cudaError_t scratch_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
@@ -375,6 +418,28 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
 }
 
 void gs_debug_fail_alloc(long long n) { g_fail_countdown.store(n < 0 ? -1 : n); }
+
+int gs_trim_memory(size_t keep_bytes) {
+    g_err[0] = 0;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(&pool);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, keep_bytes);
+    return e == cudaSuccess ? GS_OK : cuda_fail(e, "gs_trim_memory");
+}
+
+int gs_pool_bytes(uint64_t *reserved, uint64_t *used) {
+    g_err[0] = 0;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(&pool);
+    uint64_t r = 0, u = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u);
+    if (e != cudaSuccess) return cuda_fail(e, "gs_pool_bytes");
+    if (reserved) *reserved = r;
+    if (used) *used = u;
+    return GS_OK;
+}
 
 int gs_probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, void *stream) {
     g_err[0] = 0;

@@ -112,10 +112,15 @@ inline cudaError_t allow_max_smem(const void *fn) {
 }
 
 // Every device scratch allocation of the library goes through here
-// (stream-ordered).  gs_debug_fail_alloc arms a one-shot failure of a later
-// allocation, so tests can check that a failed allocation surfaces as
-// GS_ERR_OOM and leaves the library usable.
+// (stream-ordered, from the library's pool of the current device).
+// gs_debug_fail_alloc arms a one-shot failure of a later allocation, so
+// tests can check that a failed allocation surfaces as GS_ERR_OOM and leaves
+// the library usable.
 cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+
+// The library's memory pool of the current device (created on first use;
+// freed memory stays in it until gs_trim_memory).
+cudaError_t scratch_pool(cudaMemPool_t *out);
 
 // Device status bits -> GS_ERR_* code (and message); GS_OK when clear.
 int status_to_code(unsigned st);

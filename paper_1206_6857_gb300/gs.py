@@ -101,6 +101,8 @@ SIGNATURES = {
     "gs_sum": (ctypes.c_int, _SUM_ARGS),
     "gs_sum_host": (ctypes.c_int, _SUM_ARGS),
     "gs_probe_rates": (ctypes.c_int, [_VP, _VP, _VP]),
+    "gs_trim_memory": (ctypes.c_int, [ctypes.c_size_t]),
+    "gs_pool_bytes": (ctypes.c_int, [_VP, _VP]),
     "gs_sum_trace": (ctypes.c_int, _SUM_ARGS + [_VP, _I64, _VP, _VP, _VP]),
     "gs_sum_exhaustive_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, _VP,
                                                   ctypes.c_int, _VP, _VP]),
@@ -289,6 +291,18 @@ def gs_probe_rates(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().gs_probe_rates(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
     return a.value, b.value
+
+
+def gs_trim_memory(keep_bytes=0):
+    """Return all but keep_bytes of the library's device pool to the driver."""
+    _check(load().gs_trim_memory(int(keep_bytes)))
+
+
+def gs_pool_bytes():
+    """(reserved, used) bytes of the library's device pool."""
+    r, u = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().gs_pool_bytes(ctypes.byref(r), ctypes.byref(u)))
+    return r.value, u.value
 
 
 # ---------------------------------------------------------------------------
