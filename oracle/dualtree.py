@@ -289,15 +289,17 @@ def plimit_for(D: int) -> int:
     return DEFAULT_PLIMIT.get(D, 1)
 
 
-def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int) -> float:
+def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int, run: int) -> float:
     """A-priori relative error of the FP32 base case: per-term argument
     rounding for exponents down to 2^-64 (ln2 * 64 * (D+4) u), the ex2.approx
-    bound 2^-21, FP32 accumulation over 64-term runs (64 u); terms below
+    bound 2^-21, FP32 recursive summation of positive terms over a run of at
+    most `run` terms (one reference leaf: (run - 1) u) followed by the
+    compensated sum across leaves (2 u), together (run + 1) u; terms below
     2^-64 w_max are charged absolutely against the floor."""
     u = 2.0 ** -24
     rho = 0.6931471805599453 * 64.0 * (D + 4) * u
     rho = rho + 2.0 ** -21
-    rho = rho + 64.0 * u
+    rho = rho + float(run + 1) * u
     rho = rho + 2.0 ** (-63 - floor_log2) * ((N * w_max) / W)
     return rho
 
@@ -406,7 +408,8 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
     P = plimit_for(D) if not plimit else plimit
     W = float(rt.W[0])
     floorW = W * 2.0 ** floor_log2
-    rho = fp32_rho(D, rt.n, w_max, W, floor_log2)
+    run = -(-rt.n // (1 << rt.depth))          # largest reference leaf
+    rho = fp32_rho(D, rt.n, w_max, W, floor_log2, run)
     eps_t = eps - rho
     F, BT = bound_factor_table(D, P)
     Dpow = [1.0]

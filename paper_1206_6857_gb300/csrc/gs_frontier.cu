@@ -713,7 +713,7 @@ __global__ void k_front_advance(FrontierState *fs, int t) {
 // bandwidth; eps for the traversal after the FP32 base-case charge.
 __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int nh, const double *rW,
                              const double *rlo, const double *rhi, Ingest *ing, int64_t N, int D, int floor_log2,
-                             double eps) {
+                             double eps, int64_t run) {
     const int j = threadIdx.x;
     if (j < nh) {
         Group g;
@@ -727,7 +727,7 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
         const double u = 5.9604644775390625e-08;   // 2^-24
         double rho = 0.6931471805599453 * 64.0 * (double)(D + 4) * u;
         rho = rho + 4.76837158203125e-07;          // 2^-21
-        rho = rho + 64.0 * u;
+        rho = rho + (double)(run + 1) * u;      // FP32 sums over one reference leaf, then compensated
         rho = rho + ldexp(1.0, -63 - floor_log2) * (((double)N * wmax) / W);
         fs->rho = rho;
         fs->eps_t = eps - rho;
@@ -835,7 +835,8 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     for (int k = 1; k < 34; ++k) fp.Dpow[k] = fp.Dpow[k - 1] * (double)D;
 
     k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, in.rt->lo, in.rt->hi,
-                                   (Ingest *)in.ing, in.rt->n, in.D, in.floor_log2, in.eps);
+                                   (Ingest *)in.ing, in.rt->n, in.D, in.floor_log2, in.eps,
+                                   (in.rt->n + (1ll << in.rt->depth) - 1) >> in.rt->depth);
     cx.launches += 1;
     if ((rc = cx.check("k_front_init"))) return rc;
     const int T = in.qt->depth > in.rt->depth ? in.qt->depth : in.rt->depth;

@@ -208,3 +208,47 @@ def test_directed_group_sums_bound_the_exact_sums():
     exact = np.bincount(gid, weights=v.astype(np.float64), minlength=37)
     assert np.all(lo <= exact) and np.all(hi >= exact)
     assert np.all(hi - lo <= 1e-5 * exact + 1e-30)
+
+
+def _run_then_kahan_f32(terms):
+    """The base case's accumulation order: an FP32 running sum over each
+    reference leaf (a row of `terms`), then a compensated FP32 sum of the
+    leaf sums."""
+    s = np.float32(0.0)
+    c = np.float32(0.0)
+    for row in terms:
+        part = np.float32(0.0)
+        for v in row:
+            part = np.float32(part + v)
+        y = np.float32(part - c)
+        t = np.float32(s + y)
+        c = np.float32(np.float32(t - s) - y)
+        s = t
+    return float(s)
+
+
+@pytest.mark.parametrize("run", [16, 64, 128])
+def test_summation_charge_covers_adversarial_runs(run):
+    """Positive terms built so that every FP32 addition of a leaf run rounds
+    up by almost a full unit: the relative error of the run-then-compensated
+    sum approaches (run - 1) u, which the charge's run-length term covers —
+    and for runs of 128 (leaf size 128) it exceeds 64 u."""
+    u = 2.0 ** -24
+    rows = []
+    for leaf in range(4):
+        s = np.float32(1.0 + leaf)
+        row = [s]
+        for _ in range(run - 1):
+            # just above half an ulp of the running sum: rounds up to the next float
+            ulp = float(np.spacing(np.float32(s)))
+            t = np.float32(ulp * 0.5 * (1.0 + 2.0 ** -8))
+            row.append(t)
+            s = np.float32(s + t)
+        rows.append(row)
+    exact = math.fsum(float(v) for row in rows for v in row)
+    got = _run_then_kahan_f32(rows)
+    rel = abs(got - exact) / exact
+    charge = T.fp32_rho(1, 1, 0.0, 1.0, -40, run) - T.fp32_rho(1, 1, 0.0, 1.0, -40, 0) + u
+    assert rel <= charge
+    if run == 128:
+        assert rel > 64.0 * u
