@@ -248,7 +248,8 @@ def run_gs(args):
     scores = {}
 
     # autotuner (setup, not timed): leaf size, PLIMIT and bestMethod cost
-    # weights chosen by timing the library on the data with 8 of the bandwidths
+    # weights chosen by timing the library on the data with every bandwidth
+    # of the step
     tuned, opts = None, None
     if args.leaf or args.cost:
         from paper_1206_6857_gb300 import autotune
@@ -262,6 +263,8 @@ def run_gs(args):
         # blocks of 8, so a subset would favour the wrong leaf size
         tuned, _table = autotune.tune(tr, tw, hs, eps, h_subset=0, queries=None if wl.mono else tq)
         tuned["tuning_seconds"] = time.perf_counter() - t0
+        tuned["candidates"] = [[r["leaf_size"]] + list(r["cost_weight"]) + [round(r["seconds"] * 1e3, 1)]
+                               for r in _table]     # leaf, c_DH, c_DL, c_H2L, c_Direct, ms
         opts = autotune.options(tuned)
 
     opts, _sel_params = selector_opts(args, opts)
