@@ -326,9 +326,10 @@ def run_gs(args):
     kname = "k_exhaustive" if eps == 0.0 else "k_basecase"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
             "frac": achieved / peak if peak else None,
-            "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d" % (
+            "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d/cw%s" % (
                 wl_config(wl, args.mode, eps)["workload"], args.mode, args.scale,
-                (tuned or {}).get("leaf_size", wl.leaf_size))),
+                (tuned or {}).get("leaf_size", wl.leaf_size),
+                ",".join("%g" % v for v in (tuned or {}).get("cost_weight", gs.GS_COST_DEFAULT)))),
             "kernel": kname, "peak_basis": "measured %.1f ex2 lanes/SM/clk x %d SMs x %.0f MHz (median SM clock under load)"
             % (ex2_rate, props.multi_processor_count, sm_mhz),
             "ffma_lanes_per_sm_clk": ffma_rate, "kernel_ms_per_launch": base_ms}
