@@ -281,7 +281,8 @@ __global__ void k_series_dl(SeriesParams sp, const SeriesEntry *__restrict__ ent
 // lane-interleaved shared buffer.  Higher orders are done one at a time by
 // the whole warp: lanes over b, loop over a.
 // ---------------------------------------------------------------------------
-__global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent) {
+__global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, const SeriesEntry *__restrict__ ent,
+                             const unsigned long long *__restrict__ ne_end) {
     extern __shared__ double smem_d[];
     const int D = sp.D, T = sp.T, P = sp.P;
     uint8_t *al_s = (uint8_t *)smem_d;
@@ -293,7 +294,8 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
     double *Hs = A + T;
     double *lanebuf = smem_d + table_bytes(T, D) / 8 + (size_t)(blockDim.x >> 5) * (T + D * nHmax) +
                       (size_t)w * 32 * (kLaneT + kLaneH);
-    const int64_t ne = fs->series_count[2];
+    // the whole list, or the general bucket of a bucketed list
+    const int64_t ne = ne_end ? (int64_t)*ne_end : fs->series_count[2];
     const unsigned full = 0xffffffffu;
     // tiles are taken in list order from a counter: the high-order actions
     // of the upper levels come first and the cheap leaf-level ones fill in
@@ -432,6 +434,154 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
             }
             if (lane == 0) atomicMax(&sp.pL[(int64_t)Eb.q * sp.nh + Eb.j], p);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// H2L in three dimensions, one lane per action.  The translation
+//   C_beta = sum_{|alpha| < p} A_alpha prod_d h_{alpha_d + beta_d}(tau_d)
+// separates over the dimensions, so it is summed one dimension at a time,
+//   X1[a1,a2,b3] = sum_a3 A[a1,a2,a3] H3[a3+b3]
+//   X2[a1,b2,b3] = sum_a2 X1[a1,a2,b3] H2[a2+b2]
+//   C[b1,b2,b3]  = sum_a1 X2[a1,b2,b3] H1[a1+b1],
+// every range cut to total degree < p: 2 p T_p + (p(p+1)/2)^2 multiply-adds
+// instead of T_p^2 (D + 1) for the double sum (order 4: 260 against 1600).
+// The same terms as k_series_h2l, added in another order.
+// ---------------------------------------------------------------------------
+constexpr int kH2lBuckets = 3;   // 0: k_series_h2l; 1, 2: k_series_h2l_d3 at orders 3, 4
+
+__device__ __forceinline__ int h2l_bucket(int D, int p) { return (D == 3 && (p == 3 || p == 4)) ? p - 2 : 0; }
+
+template <int P>
+__global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const SeriesEntry *__restrict__ ent,
+                                                       const unsigned long long *__restrict__ bounds) {
+    constexpr int TP = P * (P + 1) * (P + 2) / 6;   // C(P + 2, 3) terms of total degree < P
+    constexpr int NH = 2 * P - 1;                   // Hermite orders 0 .. 2P - 2
+    __shared__ uint8_t idx3[P * P * P];             // (a1, a2, a3) -> graded-lex position
+    for (int a = threadIdx.x; a < TP; a += blockDim.x) {
+        const uint8_t *al = sp.tb.alpha + 3 * a;
+        idx3[(al[0] * P + al[1]) * P + al[2]] = (uint8_t)a;
+    }
+    __syncthreads();
+    const int64_t b0 = (int64_t)bounds[0], b1 = (int64_t)bounds[1];
+    for (int64_t e = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < b1;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const SeriesEntry E = ent[e];
+        const double is = sp.inv_s[E.j];
+        const double *mom = sp.rmom + (int64_t)E.r * sp.T;
+        const double *cq = sp.qcenter + (int64_t)E.q * 3, *cr = sp.rcenter + (int64_t)E.r * 3;
+        double H[3][NH];
+        double t2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double tau = (cq[d] - cr[d]) * is;
+            t2 += tau * tau;
+            H[d][0] = 1.0;
+            H[d][1] = 2.0 * tau;
+#pragma unroll
+            for (int k = 1; k + 1 < NH; ++k) H[d][k + 1] = 2.0 * tau * H[d][k] - 2.0 * k * H[d][k - 1];
+        }
+        const double et = exp(-t2);
+        double ip[P];   // s^-k
+        ip[0] = 1.0;
+#pragma unroll
+        for (int k = 1; k < P; ++k) ip[k] = ip[k - 1] * is;
+        double X1[P][P][P];   // [a1][a2][b3], a1 + a2 < P
+#pragma unroll
+        for (int a1 = 0; a1 < P; ++a1)
+#pragma unroll
+            for (int a2 = 0; a1 + a2 < P; ++a2) {
+                double A[P];   // A_alpha = M_alpha s^-|alpha| along a3
+#pragma unroll
+                for (int a3 = 0; a1 + a2 + a3 < P; ++a3)
+                    A[a3] = mom[idx3[(a1 * P + a2) * P + a3]] * ip[a1 + a2 + a3];
+#pragma unroll
+                for (int b3 = 0; b3 < P; ++b3) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int a3 = 0; a1 + a2 + a3 < P; ++a3) s = fma(A[a3], H[2][a3 + b3], s);
+                    X1[a1][a2][b3] = s;
+                }
+            }
+        double X2[P][P][P];   // [a1][b2][b3], b2 + b3 < P
+#pragma unroll
+        for (int a1 = 0; a1 < P; ++a1)
+#pragma unroll
+            for (int b2 = 0; b2 < P; ++b2)
+#pragma unroll
+                for (int b3 = 0; b2 + b3 < P; ++b3) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int a2 = 0; a1 + a2 < P; ++a2) s = fma(X1[a1][a2][b3], H[1][a2 + b2], s);
+                    X2[a1][b2][b3] = s;
+                }
+        double *Bm = sp.B + ((int64_t)E.q * sp.nh + E.j) * sp.T;
+#pragma unroll
+        for (int c1 = 0; c1 < P; ++c1)
+#pragma unroll
+            for (int c2 = 0; c1 + c2 < P; ++c2)
+#pragma unroll
+                for (int c3 = 0; c1 + c2 + c3 < P; ++c3) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int a1 = 0; a1 < P; ++a1) s = fma(X2[a1][c2][c3], H[0][a1 + c1], s);
+                    const int k = idx3[(c1 * P + c2) * P + c3];
+                    const double sign = ((c1 + c2 + c3) & 1) ? -1.0 : 1.0;
+                    atomicAdd(&Bm[k], sign * sp.tb.inv_fact[k] * et * s);
+                }
+        atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], P);
+    }
+}
+
+// Bucket the H2L list by kernel: warp-aggregated counts, then the start of
+// each bucket, then a scatter (the order inside a bucket is free: every
+// action adds into B with atomics)
+__global__ void k_h2l_count(const SeriesEntry *__restrict__ ent, const FrontierState *__restrict__ fs, int D,
+                            int64_t cap, unsigned long long *cnt) {
+    const int64_t ne = fs->series_count[2] < cap ? fs->series_count[2] : cap;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps step together, so every shuffle has all 32 lanes
+    for (int64_t w0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); w0 < ne; w0 += stride) {
+        const int64_t e = w0 + lane;
+        const int b = e < ne ? h2l_bucket(D, ent[e].p) : -1;
+        const unsigned m = __match_any_sync(0xffffffffu, b);
+        if (b >= 0 && lane == __ffs(m) - 1) atomicAdd(&cnt[b], (unsigned long long)__popc(m));
+    }
+}
+
+__global__ void k_h2l_starts(const unsigned long long *cnt, unsigned long long *cur, unsigned long long *bounds) {
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int b = 0; b < kH2lBuckets; ++b) {
+            cur[b] = s;
+            bounds[b] = s;
+            s += cnt[b];
+        }
+        bounds[kH2lBuckets] = s;
+    }
+}
+
+__global__ void k_h2l_scatter(const SeriesEntry *__restrict__ ent, const FrontierState *__restrict__ fs, int D,
+                              int64_t cap, unsigned long long *cur, SeriesEntry *out) {
+    const int64_t ne = fs->series_count[2] < cap ? fs->series_count[2] : cap;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); w0 < ne; w0 += stride) {
+        const int64_t e = w0 + lane;
+        SeriesEntry E;
+        int b = -1;
+        if (e < ne) {
+            E = ent[e];
+            b = h2l_bucket(D, E.p);
+        }
+        const unsigned m = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (b >= 0 && lane == leader) base = atomicAdd(&cur[b], (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (b >= 0) out[base + __popc(m & lt)] = E;
     }
 }
 
@@ -599,6 +749,8 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         const int tbytes = table_bytes(sp.T, sp.D);
         // pieces of the DH (queries) and DL (references) actions
         long long *pieces[2] = {nullptr, nullptr};
+        SeriesEntry *h2l_sorted = nullptr;          // the H2L list bucketed by kernel (D = 3)
+        unsigned long long *h2l_ctl = nullptr;
         for (int m = 0; m < 2; ++m) {
             const int64_t ne = fb.n_series[m];
             if (ne == 0) continue;
@@ -629,7 +781,17 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
                 GS_CUDA_TRY(cudaMemsetAsync(&fb.fs->work, 0, sizeof(unsigned long long), st));
                 int64_t g = ((n + 31) / 32 + wpb - 1) / wpb;
                 const int64_t mx = fb.grid_warps / wpb;
-                k_series_h2l<<<(unsigned)(g < 1 ? 1 : (g > mx ? mx : g)), wpb * 32, sm, st>>>(sp, fb.fs, fb.series[2]);
+                const unsigned grid_h = (unsigned)(g < 1 ? 1 : (g > mx ? mx : g));
+                if (!h2l_sorted) {
+                    k_series_h2l<<<grid_h, wpb * 32, sm, st>>>(sp, fb.fs, fb.series[2], nullptr);
+                } else {
+                    // three-dimensional orders 3 and 4 in their own kernels,
+                    // everything else in the general one
+                    k_series_h2l<<<grid_h, wpb * 32, sm, st>>>(sp, fb.fs, h2l_sorted, h2l_ctl + 7);
+                    k_series_h2l_d3<3><<<(unsigned)(fb.grid_warps / 4), 128, 0, st>>>(sp, h2l_sorted, h2l_ctl + 7);
+                    k_series_h2l_d3<4><<<(unsigned)(fb.grid_warps / 4), 128, 0, st>>>(sp, h2l_sorted, h2l_ctl + 8);
+                    cx.launches += 2;
+                }
             }
             cx.launches += 1;
             return cx.check(which == 0 ? "k_series_dh" : which == 1 ? "k_series_dl" : "k_series_h2l");
@@ -639,7 +801,27 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         cx.mark(1);
         if (!rc) rc = launch(1, fb.n_series[1], 8 * (size_t)(32 * sp.D * sp.P + 32 + 32 * kDlStride));
         cx.mark(2);
+        if (!rc && sp.D == 3 && sp.P >= 3 && fb.n_series[2] > 0) {
+            // bucket the H2L list: ctl = counts[3], cursors[3], bounds[4]
+            cudaError_t e = dev_malloc_async((void **)&h2l_ctl, 10 * sizeof(unsigned long long), st);
+            if (e == cudaSuccess)
+                e = dev_malloc_async((void **)&h2l_sorted, (size_t)fb.n_series[2] * sizeof(SeriesEntry), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h2l_ctl, 0, 10 * sizeof(unsigned long long), st);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "H2L buckets");
+            } else {
+                const int64_t blocks = (fb.n_series[2] + 255) / 256;
+                const unsigned gb = (unsigned)(blocks < 4096 ? blocks : 4096);
+                k_h2l_count<<<gb, 256, 0, st>>>(fb.series[2], fb.fs, sp.D, fb.n_series[2], h2l_ctl);
+                k_h2l_starts<<<1, 32, 0, st>>>(h2l_ctl, h2l_ctl + 3, h2l_ctl + 6);
+                k_h2l_scatter<<<gb, 256, 0, st>>>(fb.series[2], fb.fs, sp.D, fb.n_series[2], h2l_ctl + 3, h2l_sorted);
+                cx.launches += 3;
+                rc = cx.check("H2L buckets");
+            }
+        }
         if (!rc) rc = launch(2, fb.n_series[2], 8 * (size_t)(sp.T + sp.D * (2 * sp.P - 1) + 32 * (kLaneT + kLaneH)));
+        if (h2l_sorted) cudaFreeAsync(h2l_sorted, st);
+        if (h2l_ctl) cudaFreeAsync(h2l_ctl, st);
         cx.mark(-1);
         for (int m = 0; m < 2; ++m)
             if (pieces[m]) cudaFreeAsync(pieces[m], st);

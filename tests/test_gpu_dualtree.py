@@ -233,3 +233,36 @@ def test_autotuner_picks_a_certified_configuration(gs, tmp_path):
     path = str(tmp_path / "tuned.json")
     autotune.cache(path, key, best)
     assert autotune.cache(path, key) == best
+
+
+def test_h2l_orders_3_and_4_in_three_dimensions(gs):
+    """H2L-heavy traversal in D = 3 (cost weights that make H2L the cheapest
+    method wherever it is certified, PLIMIT 4): the actions at orders 3 and
+    4 run in their own dimension-by-dimension kernel.  Bit-exact decisions,
+    and every query's error stays under the bounds charged to it (the sum of
+    E over the approximations that cover it) plus the FP32 base-case charge,
+    which is far tighter than eps."""
+    q, _, w = synth.small_random(33, 3000, 3)
+    h = np.array([0.05, 0.12, 0.3])
+    eps, leaf, P, cw = 3e-2, 16, 4, (1e6, 1e6, 1e-3, 1.0)
+    tq = _dev(q)
+    st = gs.gs_stats()
+    out, trace, _, _ = gs.gs_sum_trace(tq, tq, _dev(w), h, eps, opts=_opts(gs, leaf, 0, True, P, cw), stats=st)
+    qt, rt, want, trav = _cpu_trace(q, q, w, True, h, eps, leaf, 0, True, P, cw)
+    got = trace.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, want)
+    act, p = got[:, 3] & 0xff, (got[:, 3] >> 8) & 0xff
+    assert np.sum((act == T.H2L) & (p == 3)) > 100 and np.sum((act == T.H2L) & (p == 4)) > 1000
+    charged = np.zeros((qt.n, h.size))
+    for it in trav.iters:
+        for qn, j, m, e in zip(it["q"], it["j"], it["method"], it["E"]):
+            if m in (T.FD, T.DH, T.DL, T.H2L):
+                charged[qt.begin[qn]:qt.end[qn], j] += e
+    bound = np.empty_like(charged)
+    bound[qt.perm] = charged
+    exact = oracle_ex.gauss_sum(q, q, w, h)
+    W = float(w.astype(np.float64).sum())
+    err = np.abs(out.cpu().numpy() - exact)
+    slack = bound + 2.0 * st.fp32_rel_bound * exact + 1e-12 * W
+    assert np.all(err <= slack), np.max(err / slack)
+    assert np.max(bound / exact) < eps
