@@ -440,17 +440,30 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
 // ---------------------------------------------------------------------------
 // H2L in three dimensions, one lane per action.  The translation
 //   C_beta = sum_{|alpha| < p} A_alpha prod_d h_{alpha_d + beta_d}(tau_d)
-// separates over the dimensions, so it is summed one dimension at a time,
-//   X1[a1,a2,b3] = sum_a3 A[a1,a2,a3] H3[a3+b3]
-//   X2[a1,b2,b3] = sum_a2 X1[a1,a2,b3] H2[a2+b2]
-//   C[b1,b2,b3]  = sum_a1 X2[a1,b2,b3] H1[a1+b1],
+// separates over the dimensions, so it is summed one dimension at a time:
+// for each a1,
+//   X1[a2,b3] = sum_a3 A[a1,a2,a3] H3[a3+b3]
+//   X2[b2,b3] = sum_a2 X1[a2,b3] H2[a2+b2]
+//   C[c1,c2,c3] += X2[c2,c3] H1[a1+c1],
 // every range cut to total degree < p: 2 p T_p + (p(p+1)/2)^2 multiply-adds
 // instead of T_p^2 (D + 1) for the double sum (order 4: 260 against 1600).
-// The same terms as k_series_h2l, added in another order.
+// Only one a1 slice of X1 and X2 is live at a time.  e^{-|tau|^2} is folded
+// into the scaled moments and (-1)^{|beta|} / beta! comes from a table, so
+// each coefficient costs one multiply on the way out.  The same terms as
+// k_series_h2l, added in another order.
 // ---------------------------------------------------------------------------
-constexpr int kH2lBuckets = 3;   // 0: k_series_h2l; 1, 2: k_series_h2l_d3 at orders 3, 4
+constexpr int kH2lBuckets = 4;   // 0: k_series_h2l; 1, 2, 3: k_series_h2l_d3 at orders 3, 4, 5
 
-__device__ __forceinline__ int h2l_bucket(int D, int p) { return (D == 3 && (p == 3 || p == 4)) ? p - 2 : 0; }
+__device__ __forceinline__ int h2l_bucket(int D, int p) { return (D == 3 && p >= 3 && p <= 5) ? p - 2 : 0; }
+
+// dense register slot of (c1, c2, c3), c1 + c2 + c3 < P (c1 outermost)
+template <int P>
+__host__ __device__ constexpr int slot_of(int c1, int c2, int c3) {
+    int s = 0;
+    for (int i = 0; i < c1; ++i) s += (P - i) * (P - i + 1) / 2;
+    for (int j = 0; j < c2; ++j) s += P - c1 - j;
+    return s + c3;
+}
 
 template <int P>
 __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const SeriesEntry *__restrict__ ent,
@@ -458,9 +471,11 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
     constexpr int TP = P * (P + 1) * (P + 2) / 6;   // C(P + 2, 3) terms of total degree < P
     constexpr int NH = 2 * P - 1;                   // Hermite orders 0 .. 2P - 2
     __shared__ uint8_t idx3[P * P * P];             // (a1, a2, a3) -> graded-lex position
+    __shared__ double sif[TP];                      // (-1)^{|beta|} / beta!
     for (int a = threadIdx.x; a < TP; a += blockDim.x) {
         const uint8_t *al = sp.tb.alpha + 3 * a;
         idx3[(al[0] * P + al[1]) * P + al[2]] = (uint8_t)a;
+        sif[a] = ((al[0] + al[1] + al[2]) & 1) ? -sp.tb.inv_fact[a] : sp.tb.inv_fact[a];
     }
     __syncthreads();
     const int64_t b0 = (int64_t)bounds[0], b1 = (int64_t)bounds[1];
@@ -481,40 +496,43 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
 #pragma unroll
             for (int k = 1; k + 1 < NH; ++k) H[d][k + 1] = 2.0 * tau * H[d][k] - 2.0 * k * H[d][k - 1];
         }
-        const double et = exp(-t2);
-        double ip[P];   // s^-k
-        ip[0] = 1.0;
+        double ip[P];   // e^{-|tau|^2} s^-k
+        ip[0] = exp(-t2);
 #pragma unroll
         for (int k = 1; k < P; ++k) ip[k] = ip[k - 1] * is;
-        double X1[P][P][P];   // [a1][a2][b3], a1 + a2 < P
+        double C[TP];
 #pragma unroll
-        for (int a1 = 0; a1 < P; ++a1)
+        for (int k = 0; k < TP; ++k) C[k] = 0.0;
+#pragma unroll
+        for (int a1 = 0; a1 < P; ++a1) {
+            double X1[P][P];   // [a2][b3], a1 + a2 < P
 #pragma unroll
             for (int a2 = 0; a1 + a2 < P; ++a2) {
-                double A[P];   // A_alpha = M_alpha s^-|alpha| along a3
+                double A[P];
 #pragma unroll
                 for (int a3 = 0; a1 + a2 + a3 < P; ++a3)
                     A[a3] = mom[idx3[(a1 * P + a2) * P + a3]] * ip[a1 + a2 + a3];
 #pragma unroll
                 for (int b3 = 0; b3 < P; ++b3) {
-                    double s = 0.0;
+                    double acc = 0.0;
 #pragma unroll
-                    for (int a3 = 0; a1 + a2 + a3 < P; ++a3) s = fma(A[a3], H[2][a3 + b3], s);
-                    X1[a1][a2][b3] = s;
+                    for (int a3 = 0; a1 + a2 + a3 < P; ++a3) acc = fma(A[a3], H[2][a3 + b3], acc);
+                    X1[a2][b3] = acc;
                 }
             }
-        double X2[P][P][P];   // [a1][b2][b3], b2 + b3 < P
 #pragma unroll
-        for (int a1 = 0; a1 < P; ++a1)
+            for (int c2 = 0; c2 < P; ++c2)
 #pragma unroll
-            for (int b2 = 0; b2 < P; ++b2)
+                for (int c3 = 0; c2 + c3 < P; ++c3) {
+                    double x2 = 0.0;   // X2[c2, c3] of this slice
 #pragma unroll
-                for (int b3 = 0; b2 + b3 < P; ++b3) {
-                    double s = 0.0;
+                    for (int a2 = 0; a1 + a2 < P; ++a2) x2 = fma(X1[a2][c3], H[1][a2 + c2], x2);
 #pragma unroll
-                    for (int a2 = 0; a1 + a2 < P; ++a2) s = fma(X1[a1][a2][b3], H[1][a2 + b2], s);
-                    X2[a1][b2][b3] = s;
+                    for (int c1 = 0; c1 + c2 + c3 < P; ++c1) {
+                        C[slot_of<P>(c1, c2, c3)] = fma(x2, H[0][a1 + c1], C[slot_of<P>(c1, c2, c3)]);
+                    }
                 }
+        }
         double *Bm = sp.B + ((int64_t)E.q * sp.nh + E.j) * sp.T;
 #pragma unroll
         for (int c1 = 0; c1 < P; ++c1)
@@ -522,12 +540,8 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
             for (int c2 = 0; c1 + c2 < P; ++c2)
 #pragma unroll
                 for (int c3 = 0; c1 + c2 + c3 < P; ++c3) {
-                    double s = 0.0;
-#pragma unroll
-                    for (int a1 = 0; a1 < P; ++a1) s = fma(X2[a1][c2][c3], H[0][a1 + c1], s);
                     const int k = idx3[(c1 * P + c2) * P + c3];
-                    const double sign = ((c1 + c2 + c3) & 1) ? -1.0 : 1.0;
-                    atomicAdd(&Bm[k], sign * sp.tb.inv_fact[k] * et * s);
+                    atomicAdd(&Bm[k], sif[k] * C[slot_of<P>(c1, c2, c3)]);
                 }
         atomicMax(&sp.pL[(int64_t)E.q * sp.nh + E.j], P);
     }
@@ -787,10 +801,13 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
                 } else {
                     // three-dimensional orders 3 and 4 in their own kernels,
                     // everything else in the general one
-                    k_series_h2l<<<grid_h, wpb * 32, sm, st>>>(sp, fb.fs, h2l_sorted, h2l_ctl + 7);
-                    k_series_h2l_d3<3><<<(unsigned)(fb.grid_warps / 4), 128, 0, st>>>(sp, h2l_sorted, h2l_ctl + 7);
-                    k_series_h2l_d3<4><<<(unsigned)(fb.grid_warps / 4), 128, 0, st>>>(sp, h2l_sorted, h2l_ctl + 8);
-                    cx.launches += 2;
+                    const unsigned long long *bnd = h2l_ctl + 2 * kH2lBuckets;
+                    const unsigned gd = (unsigned)(fb.grid_warps / 4);
+                    k_series_h2l<<<grid_h, wpb * 32, sm, st>>>(sp, fb.fs, h2l_sorted, bnd + 1);
+                    k_series_h2l_d3<3><<<gd, 128, 0, st>>>(sp, h2l_sorted, bnd + 1);
+                    if (sp.P >= 4) k_series_h2l_d3<4><<<gd, 128, 0, st>>>(sp, h2l_sorted, bnd + 2);
+                    if (sp.P >= 5) k_series_h2l_d3<5><<<gd, 128, 0, st>>>(sp, h2l_sorted, bnd + 3);
+                    cx.launches += 1 + (sp.P >= 4) + (sp.P >= 5);
                 }
             }
             cx.launches += 1;
@@ -802,19 +819,21 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         if (!rc) rc = launch(1, fb.n_series[1], 8 * (size_t)(32 * sp.D * sp.P + 32 + 32 * kDlStride));
         cx.mark(2);
         if (!rc && sp.D == 3 && sp.P >= 3 && fb.n_series[2] > 0) {
-            // bucket the H2L list: ctl = counts[3], cursors[3], bounds[4]
-            cudaError_t e = dev_malloc_async((void **)&h2l_ctl, 10 * sizeof(unsigned long long), st);
+            // bucket the H2L list: ctl = counts, cursors, bounds (kH2lBuckets + 1)
+            constexpr int kCtl = 3 * kH2lBuckets + 1;
+            cudaError_t e = dev_malloc_async((void **)&h2l_ctl, kCtl * sizeof(unsigned long long), st);
             if (e == cudaSuccess)
                 e = dev_malloc_async((void **)&h2l_sorted, (size_t)fb.n_series[2] * sizeof(SeriesEntry), st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(h2l_ctl, 0, 10 * sizeof(unsigned long long), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h2l_ctl, 0, kCtl * sizeof(unsigned long long), st);
             if (e != cudaSuccess) {
                 rc = cuda_fail(e, "H2L buckets");
             } else {
                 const int64_t blocks = (fb.n_series[2] + 255) / 256;
                 const unsigned gb = (unsigned)(blocks < 4096 ? blocks : 4096);
                 k_h2l_count<<<gb, 256, 0, st>>>(fb.series[2], fb.fs, sp.D, fb.n_series[2], h2l_ctl);
-                k_h2l_starts<<<1, 32, 0, st>>>(h2l_ctl, h2l_ctl + 3, h2l_ctl + 6);
-                k_h2l_scatter<<<gb, 256, 0, st>>>(fb.series[2], fb.fs, sp.D, fb.n_series[2], h2l_ctl + 3, h2l_sorted);
+                k_h2l_starts<<<1, 32, 0, st>>>(h2l_ctl, h2l_ctl + kH2lBuckets, h2l_ctl + 2 * kH2lBuckets);
+                k_h2l_scatter<<<gb, 256, 0, st>>>(fb.series[2], fb.fs, sp.D, fb.n_series[2], h2l_ctl + kH2lBuckets,
+                                                  h2l_sorted);
                 cx.launches += 3;
                 rc = cx.check("H2L buckets");
             }

@@ -235,16 +235,25 @@ def test_autotuner_picks_a_certified_configuration(gs, tmp_path):
     assert autotune.cache(path, key) == best
 
 
-def test_h2l_orders_3_and_4_in_three_dimensions(gs):
-    """H2L-heavy traversal in D = 3 (cost weights that make H2L the cheapest
-    method wherever it is certified, PLIMIT 4): the actions at orders 3 and
-    4 run in their own dimension-by-dimension kernel.  Bit-exact decisions,
-    and every query's error stays under the bounds charged to it (the sum of
-    E over the approximations that cover it) plus the FP32 base-case charge,
-    which is far tighter than eps."""
-    q, _, w = synth.small_random(33, 3000, 3)
-    h = np.array([0.05, 0.12, 0.3])
-    eps, leaf, P, cw = 3e-2, 16, 4, (1e6, 1e6, 1e-3, 1.0)
+H2L_CASES = [
+    # seed, n, h, eps, PLIMIT, the orders that must occur (at least that many actions)
+    (33, 3000, [0.05, 0.12, 0.3], 3e-2, 4, {3: 100, 4: 1000}),
+    (35, 6000, [0.04, 0.1, 0.25], 1e-2, 6, {4: 1000, 5: 10000, 6: 1000}),
+]
+
+
+@pytest.mark.parametrize("case", H2L_CASES, ids=lambda c: "s%d_P%d" % (c[0], c[4]))
+def test_h2l_orders_3_to_5_in_three_dimensions(gs, case):
+    """H2L-heavy traversals in D = 3 (cost weights that make H2L the cheapest
+    method wherever it is certified): the actions at orders 3 to 5 run in
+    their own dimension-by-dimension kernel, the others in the general one.
+    Bit-exact decisions, and every query's error stays under the bounds
+    charged to it (the sum of E over the approximations that cover it) plus
+    the FP32 base-case charge, which is far tighter than eps."""
+    seed, n, h, eps, P, orders = case
+    q, _, w = synth.small_random(seed, n, 3)
+    h = np.asarray(h)
+    leaf, cw = 16, (1e6, 1e6, 1e-3, 1.0)
     tq = _dev(q)
     st = gs.gs_stats()
     out, trace, _, _ = gs.gs_sum_trace(tq, tq, _dev(w), h, eps, opts=_opts(gs, leaf, 0, True, P, cw), stats=st)
@@ -252,7 +261,8 @@ def test_h2l_orders_3_and_4_in_three_dimensions(gs):
     got = trace.cpu().numpy().astype(np.int64)
     assert np.array_equal(got, want)
     act, p = got[:, 3] & 0xff, (got[:, 3] >> 8) & 0xff
-    assert np.sum((act == T.H2L) & (p == 3)) > 100 and np.sum((act == T.H2L) & (p == 4)) > 1000
+    for order, least in orders.items():
+        assert np.sum((act == T.H2L) & (p == order)) >= least, (order, np.bincount(p[act == T.H2L]))
     charged = np.zeros((qt.n, h.size))
     for it in trav.iters:
         for qn, j, m, e in zip(it["q"], it["j"], it["method"], it["E"]):
