@@ -49,14 +49,22 @@ static const double kSqrt2 = 1.4142135623730951;
 
 // 2^x in FP32 for -125 <= x <= 0: k = rint(x), f = x - k, 2^f by Horner on
 // its degree-7 Taylor polynomial, times 2^k built exactly.  Relative error
-// below 2^-20 (covered by the bound margins).
+// below 2^-20 (covered by the bound margins).  rint comes from one FP32 add
+// of 1.5 * 2^23 (in [2^23, 2^24) the spacing is 1, and round-to-nearest-even
+// of the sum is 1.5 * 2^23 + rint(x) because 1.5 * 2^23 is even); the
+// integer k is then the difference of the bit patterns.  The same values as
+// rintf and a float-to-int conversion, without conversion instructions
+// (they share the slow FP64 pipe on this GPU).
 __device__ __forceinline__ float exp2_f32(float x) {
-    const float k = rintf(x);
+    const float magic = 0x1.8p+23f;
+    const float t = __fadd_rn(x, magic);
+    const float k = __fsub_rn(t, magic);
+    const int ki = __float_as_int(t) - __float_as_int(magic);
     const float f = x - k;
     float p = c_e2[7];
 #pragma unroll
     for (int n = 6; n >= 0; --n) p = p * f + c_e2[n];
-    return p * __int_as_float(((int)k + 127) << 23);
+    return p * __int_as_float((ki + 127) << 23);
 }
 
 __device__ __forceinline__ double rpow(double r, int p) {
