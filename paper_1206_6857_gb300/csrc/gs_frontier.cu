@@ -85,6 +85,23 @@ __device__ __forceinline__ double warp_sum_sparse(double v) {
     return __any_sync(0xffffffffu, v != 0.0) ? warp_sum(v) : 0.0;
 }
 
+// The same butterfly with its value needed on lane 0 only: at each step only
+// the lanes whose partial sum lane 0 still reads add (own + higher partner,
+// the pairs and the order of warp_sum), so the FP64 pipe does 31 additions
+// instead of 160.  Lane 0's result equals warp_sum's.
+__device__ __forceinline__ double warp_sum_lane0(double v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, v, m);
+        if (lane < m) v = v + o;
+    }
+    return v;
+}
+__device__ __forceinline__ double warp_sum_sparse_lane0(double v) {
+    return __any_sync(0xffffffffu, v != 0.0) ? warp_sum_lane0(v) : 0.0;
+}
+
 // xor-butterfly sums in FP32 with every addition rounded down / up
 __device__ __forceinline__ float warp_sum_rd(float v) {
 #pragma unroll
@@ -209,28 +226,52 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             s_dl = __fadd_rd(s_dl, __fmul_rd(fp.rW32d[r], kb.kmax));
             s_W = __fadd_ru(s_W, fp.rW32u[r]);
         }
-        const double front = (double)warp_sum_rd(s_dl), Wg = (double)warp_sum_ru(s_W);
+        const float front32 = warp_sum_rd(s_dl), Wg32 = warp_sum_ru(s_W);
         const int64_t qj = q * fp.nh + j;
-        const double fin0 = fp.fin[qj], tok0 = fp.tok[qj];
-        double Gb = fin0 + front;
-        if (fp.mono) Gb = fmax(Gb, (double)fp.qwmin[q]);
-        Gb = fmax(Gb, floorW);
         const int64_t cq = node_size(fp.qn, fp.q_depth, q);
-        const double rQ = fp.qrad[q] * invh;
-        // per group: token per unit weight and the Theorem 2 scale W / (eps G)
-        const double share = tok0 / Wg;
-        const double kappa = Wtot / (eps_t * Gb);
+        // per group: token per unit weight and the Theorem 2 scale W / (eps G),
+        // and the FP32 thresholds derived from them.  Lane 0 computes them and
+        // the warp reads them by shuffle (FP64 runs at a low rate; a value
+        // every lane computes costs 32 lanes of it).
+        // FP32 screen of the FD test (n_fd <= allot  <=>  (K(dmin)-K(dmax)) kappa/2 <= 1 + share):
+        // pairs it rejects fail the exact FP64 test by a margin of 1e-4, so the
+        // FP64 test only runs where it can succeed; decisions are unchanged.
+        // Screen of the series bounds: see thrL below.
+        double front = 0.0, fin0 = 0.0, tok0 = 0.0, rQ = 0.0, share = 0.0, kappa = 0.0;
+        float hk32 = 0.f, thr32 = 0.f, thrL = 0.f, invhd = 0.f;
+        int screen_i = 0;
+        if (lane == 0) {
+            front = (double)front32;
+            const double Wg = (double)Wg32;
+            fin0 = fp.fin[qj];
+            tok0 = fp.tok[qj];
+            double Gb = fin0 + front;
+            if (fp.mono) Gb = fmax(Gb, (double)fp.qwmin[q]);
+            Gb = fmax(Gb, floorW);
+            rQ = fp.qrad[q] * invh;
+            share = tok0 / Wg;
+            kappa = Wtot / (eps_t * Gb);
+            const double st = fp.tokens ? share : 0.0;
+            screen_i = 0.5 * kappa < 1e37;   // kappa/2 representable in FP32
+            hk32 = screen_i ? (float)(0.5 * kappa) : 0.f;
+            thr32 = (float)(1.0 + st) * 1.0001f;
+            thrL = __fmul_ru(__double2float_ru(1.0 + st), 0x1.00001p+0f);
+            invhd = __double2float_rd(invh);
+        }
+        const unsigned full = 0xffffffffu;
+        rQ = __shfl_sync(full, rQ, 0);
+        share = __shfl_sync(full, share, 0);
+        kappa = __shfl_sync(full, kappa, 0);
+        hk32 = __shfl_sync(full, hk32, 0);
+        thr32 = __shfl_sync(full, thr32, 0);
+        thrL = __shfl_sync(full, thrL, 0);
+        invhd = __shfl_sync(full, invhd, 0);
+        const bool screen = __shfl_sync(full, screen_i, 0) != 0;
         // pass 2: decisions
         float s_bank = 0.f, s_fin = 0.f;   // FP32 rounded down, like the lower bound
         double s_paid = 0.0, s_est = 0.0;
         int n_fd = 0, n_dh = 0, n_dl = 0, n_h2l = 0, n_base = 0, n_split = 0;
         const double share_t = fp.tokens ? share : 0.0;
-        // FP32 screen of the FD test (n_fd <= allot  <=>  (K(dmin)-K(dmax)) kappa/2 <= 1 + share):
-        // pairs it rejects fail the exact FP64 test by a margin of 1e-4, so the
-        // FP64 test only runs where it can succeed; decisions are unchanged
-        const bool screen = 0.5 * kappa < 1e37;   // kappa/2 representable in FP32
-        const float hk32 = screen ? (float)(0.5 * kappa) : 0.f;
-        const float thr32 = (float)(1.0 + share_t) * 1.0001f;
         // Screen of the series bounds: a lower bound of E_p kappa / W_R computed
         // with every FP32 operation rounded down from inputs rounded down
         // (overflow gives FLT_MAX, underflow rounds towards zero, so it is a
@@ -242,8 +283,7 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const bool series = (MODE == 2 ? fp.selector != GS_SEL_EXHAUSTIVE
                                         : (fp.selector == GS_SEL_RULE || fp.selector == GS_SEL_MLP)) &&
                             fp.P >= 1;
-        const float thrL = __fmul_ru(__double2float_ru(1.0 + share_t), 0x1.00001p+0f);
-        const float invhd = __double2float_rd(invh);
+        // (thrL = (1 + share)(1 + 2^-20) rounded up, from lane 0)
         float *tab = s_tab[threadIdx.x >> 5];
         // per-group feature constants of the selector
         const float hkf = (float)(0.5 * kappa < 1e37 ? 0.5 * kappa : 1e37);
@@ -477,16 +517,19 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
                     trace[ti] = make_int4((int)q, (int)r, j, method | (pord << 8) | (fp.t << 16));
             }
         }
-        const double banked = (double)warp_sum_rd(s_bank), paid = warp_sum_sparse(s_paid);
-        const double fin_add = (fp.q_leaf && fp.r_leaf) ? front : (double)warp_sum_rd(s_fin);
-        const double est_add = warp_sum_sparse(s_est);
-        // Fig. 7's token update over the whole group: pruned pairs pay their
-        // need, base cases bank W_R, splits leave the token alone
-        const double tok_new = fp.tokens ? fmax(0.0, (tok0 + banked) - paid) : 0.0;
+        const float bank32 = warp_sum_rd(s_bank);
+        const float fin32 = (fp.q_leaf && fp.r_leaf) ? 0.f : warp_sum_rd(s_fin);
+        const double paid = warp_sum_sparse_lane0(s_paid);   // lane 0's values below
+        const double est_add = warp_sum_sparse_lane0(s_est);
         int n_m[6] = {n_fd, n_dh, n_dl, n_h2l, n_base, n_split};
 #pragma unroll
         for (int m = 0; m < 6; ++m) n_m[m] = __reduce_add_sync(0xffffffffu, n_m[m]);
         if (lane == 0) {
+            const double banked = (double)bank32;
+            const double fin_add = (fp.q_leaf && fp.r_leaf) ? front : (double)fin32;
+            // Fig. 7's token update over the whole group: pruned pairs pay their
+            // need, base cases bank W_R, splits leave the token alone
+            const double tok_new = fp.tokens ? fmax(0.0, (tok0 + banked) - paid) : 0.0;
             const double fin_new = fin0 + fin_add;
             fp.fin[qj] = fin_new;
             fp.tok[qj] = tok_new;
