@@ -25,9 +25,9 @@ import numpy as np
 from . import gs
 
 DEFAULT_LEAVES = (32, 64, 128)
-DEFAULT_COSTS = ((32.0, 32.0, 32.0, 1.0), (128.0, 128.0, 4.0, 1.0), (128.0, 128.0, 8.0, 1.0),
+DEFAULT_COSTS = ((32.0, 32.0, 32.0, 1.0), (128.0, 128.0, 4.0, 1.0), (256.0, 256.0, 0.5, 1.0),
                  (256.0, 256.0, 1.0, 1.0), (256.0, 256.0, 2.0, 1.0), (256.0, 256.0, 4.0, 1.0),
-                 (512.0, 512.0, 2.0, 1.0), (512.0, 512.0, 4.0, 1.0), (2048.0, 2048.0, 256.0, 1.0))
+                 (512.0, 512.0, 1.0, 1.0), (512.0, 512.0, 2.0, 1.0), (2048.0, 2048.0, 256.0, 1.0))
 
 
 def key_for(D, N, h, diameter):
