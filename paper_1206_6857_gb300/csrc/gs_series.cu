@@ -446,15 +446,20 @@ __global__ void k_series_h2l(SeriesParams sp, FrontierState *__restrict__ fs, co
 //   X2[b2,b3] = sum_a2 X1[a2,b3] H2[a2+b2]
 //   C[c1,c2,c3] += X2[c2,c3] H1[a1+c1],
 // every range cut to total degree < p: 2 p T_p + (p(p+1)/2)^2 multiply-adds
-// instead of T_p^2 (D + 1) for the double sum (order 4: 260 against 1600).
+// instead of T_p^2 (D + 1) for the double sum (order 4: 260 against 1600,
+// order 6: 1113 against 12544).
 // Only one a1 slice of X1 and X2 is live at a time.  e^{-|tau|^2} is folded
 // into the scaled moments and (-1)^{|beta|} / beta! comes from a table, so
 // each coefficient costs one multiply on the way out.  The same terms as
 // k_series_h2l, added in another order.
 // ---------------------------------------------------------------------------
-constexpr int kH2lBuckets = 4;   // 0: k_series_h2l; 1, 2, 3: k_series_h2l_d3 at orders 3, 4, 5
+constexpr int kH2lBuckets = 5;   // 0: k_series_h2l; 1..4: k_series_h2l_d3 at orders 3..6
 
-__device__ __forceinline__ int h2l_bucket(int D, int p) { return (D == 3 && p >= 3 && p <= 5) ? p - 2 : 0; }
+__device__ __forceinline__ int h2l_bucket(int D, int p) { return (D == 3 && p >= 3 && p <= 6) ? p - 2 : 0; }
+
+// Hermite values of k_series_h2l_d3 in registers up to this order
+template <int P>
+constexpr bool kHermReg = P <= 5;
 
 // dense register slot of (c1, c2, c3), c1 + c2 + c3 < P (c1 outermost)
 template <int P>
@@ -472,6 +477,7 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
     constexpr int NH = 2 * P - 1;                   // Hermite orders 0 .. 2P - 2
     __shared__ uint8_t idx3[P * P * P];             // (a1, a2, a3) -> graded-lex position
     __shared__ double sif[TP];                      // (-1)^{|beta|} / beta!
+    __shared__ double h2l_hs[kHermReg<P> ? 1 : 3 * NH * 128];
     for (int a = threadIdx.x; a < TP; a += blockDim.x) {
         const uint8_t *al = sp.tb.alpha + 3 * a;
         idx3[(al[0] * P + al[1]) * P + al[2]] = (uint8_t)a;
@@ -485,16 +491,28 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
         const double is = sp.inv_s[E.j];
         const double *mom = sp.rmom + (int64_t)E.r * sp.T;
         const double *cq = sp.qcenter + (int64_t)E.q * 3, *cr = sp.rcenter + (int64_t)E.r * 3;
-        double H[3][NH];
+        // Hermite values: registers up to order 5; at order 6 a per-thread
+        // column of shared memory, so the coefficients fit in registers
+        double Hr[kHermReg<P> ? 3 : 1][kHermReg<P> ? NH : 1];
+        auto H = [&](int d, int k) -> double & {
+            if constexpr (kHermReg<P>) return Hr[d][k];
+            else return h2l_hs[(d * NH + k) * 128 + threadIdx.x];
+        };
         double t2 = 0.0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double tau = (cq[d] - cr[d]) * is;
             t2 += tau * tau;
-            H[d][0] = 1.0;
-            H[d][1] = 2.0 * tau;
+            double hm = 1.0, hc = 2.0 * tau;
+            H(d, 0) = hm;
+            H(d, 1) = hc;
 #pragma unroll
-            for (int k = 1; k + 1 < NH; ++k) H[d][k + 1] = 2.0 * tau * H[d][k] - 2.0 * k * H[d][k - 1];
+            for (int k = 1; k + 1 < NH; ++k) {
+                const double hn = 2.0 * tau * hc - 2.0 * k * hm;
+                H(d, k + 1) = hn;
+                hm = hc;
+                hc = hn;
+            }
         }
         double ip[P];   // e^{-|tau|^2} s^-k
         ip[0] = exp(-t2);
@@ -516,7 +534,7 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
                 for (int b3 = 0; b3 < P; ++b3) {
                     double acc = 0.0;
 #pragma unroll
-                    for (int a3 = 0; a1 + a2 + a3 < P; ++a3) acc = fma(A[a3], H[2][a3 + b3], acc);
+                    for (int a3 = 0; a1 + a2 + a3 < P; ++a3) acc = fma(A[a3], H(2, a3 + b3), acc);
                     X1[a2][b3] = acc;
                 }
             }
@@ -526,10 +544,10 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
                 for (int c3 = 0; c2 + c3 < P; ++c3) {
                     double x2 = 0.0;   // X2[c2, c3] of this slice
 #pragma unroll
-                    for (int a2 = 0; a1 + a2 < P; ++a2) x2 = fma(X1[a2][c3], H[1][a2 + c2], x2);
+                    for (int a2 = 0; a1 + a2 < P; ++a2) x2 = fma(X1[a2][c3], H(1, a2 + c2), x2);
 #pragma unroll
                     for (int c1 = 0; c1 + c2 + c3 < P; ++c1) {
-                        C[slot_of<P>(c1, c2, c3)] = fma(x2, H[0][a1 + c1], C[slot_of<P>(c1, c2, c3)]);
+                        C[slot_of<P>(c1, c2, c3)] = fma(x2, H(0, a1 + c1), C[slot_of<P>(c1, c2, c3)]);
                     }
                 }
         }
@@ -807,7 +825,8 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
                     k_series_h2l_d3<3><<<gd, 128, 0, st>>>(sp, h2l_sorted, bnd + 1);
                     if (sp.P >= 4) k_series_h2l_d3<4><<<gd, 128, 0, st>>>(sp, h2l_sorted, bnd + 2);
                     if (sp.P >= 5) k_series_h2l_d3<5><<<gd, 128, 0, st>>>(sp, h2l_sorted, bnd + 3);
-                    cx.launches += 1 + (sp.P >= 4) + (sp.P >= 5);
+                    if (sp.P >= 6) k_series_h2l_d3<6><<<gd, 128, 0, st>>>(sp, h2l_sorted, bnd + 4);
+                    cx.launches += 1 + (sp.P >= 4) + (sp.P >= 5) + (sp.P >= 6);
                 }
             }
             cx.launches += 1;
