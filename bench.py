@@ -200,17 +200,19 @@ def source_sha(kernel):
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel, sha, workload):
-    """DRAM bytes per launch recorded for this kernel on this workload, if the
-    kernel's sources are unchanged since the capture."""
+def load_traffic(kernel, sha, workload, terms):
+    """DRAM bytes of one launch of this kernel with `terms` base-case terms:
+    the bytes per term recorded on a smaller launch of the same workload
+    (records come from L2; the bytes grow with the terms), if the kernel's
+    sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
     e = d.get(kernel)
-    if e and e.get("src_sha") == sha and e.get("workload") == workload:
-        return e.get("bytes_per_launch")
+    if e and e.get("src_sha") == sha and e.get("workload") == workload and e.get("bytes_per_term"):
+        return int(round(e["bytes_per_term"] * terms))
     return None
 
 
@@ -326,10 +328,9 @@ def run_gs(args):
     kname = "k_exhaustive" if eps == 0.0 else "k_basecase"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
             "frac": achieved / peak if peak else None,
-            "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d/cw%s" % (
+            "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d" % (
                 wl_config(wl, args.mode, eps)["workload"], args.mode, args.scale,
-                (tuned or {}).get("leaf_size", wl.leaf_size),
-                ",".join("%g" % v for v in (tuned or {}).get("cost_weight", gs.GS_COST_DEFAULT)))),
+                (tuned or {}).get("leaf_size", wl.leaf_size)), evals_base),
             "kernel": kname, "peak_basis": "measured %.1f ex2 lanes/SM/clk x %d SMs x %.0f MHz (median SM clock under load)"
             % (ex2_rate, props.multi_processor_count, sm_mhz),
             "ffma_lanes_per_sm_clk": ffma_rate, "kernel_ms_per_launch": base_ms}
