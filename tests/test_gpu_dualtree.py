@@ -276,3 +276,14 @@ def test_h2l_orders_3_to_5_in_three_dimensions(gs, case):
     slack = bound + 2.0 * st.fp32_rel_bound * exact + 1e-12 * W
     assert np.all(err <= slack), np.max(err / slack)
     assert np.max(bound / exact) < eps
+
+
+def test_more_bandwidths_than_one_mask(gs):
+    """40 bandwidths in one traversal: more than the merged base case's 32-bit
+    bandwidth mask holds, so the per-bandwidth base case runs; every query
+    within eps of the oracle."""
+    q, _, w = synth.small_random(79, 3000, 2)
+    h = np.geomspace(0.005, 0.5, 40)
+    out = gs.gs_sum(_dev(q), _dev(q), _dev(w), h, 1e-2, opts=_opts(gs, leaf=32)).cpu().numpy()
+    exact = oracle_ex.gauss_sum(q, q, w, h)
+    assert rel_err(out, exact, float(w.astype(np.float64).sum())).max() <= 1e-2
