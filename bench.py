@@ -216,23 +216,60 @@ def load_traffic(kernel, sha, workload, terms):
     return None
 
 
+class Replicas:
+    """Process-group plumbing of an N-GPU run.  The path does not shard, so
+    every rank runs the whole step on its own copy of the workload (replicas):
+    a barrier on both sides of the timed region, the slowest rank's time, and
+    the whole job's throughput = the units all ranks processed over that time.
+    backend "nccl" (GPU ranks) or "gloo" (the CPU tests)."""
+
+    def __init__(self, backend="nccl", device=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.device = device
+        if self.world > 1:
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=device)
+            else:
+                dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max_ms(self, ms):
+        """The largest of the ranks' step times."""
+        if self.world == 1:
+            return float(ms)
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, units_per_rank, ms):
+        """Whole-job units per second: every rank processed units_per_rank."""
+        return units_per_rank * self.world / (ms / 1e3)
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
 def run_gs(args):
     import torch
 
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    reps = Replicas("nccl", torch.device("cuda", local))
+    world, rank = reps.world, reps.rank
 
     from paper_1206_6857_gb300 import build as gbuild
     from paper_1206_6857_gb300 import gs
     if rank == 0:
         gbuild.build()
-    if world > 1:
-        dist.barrier()
+    reps.barrier()
     gs.load()
 
     wl = workload(args.scale, args.config)
@@ -290,8 +327,7 @@ def run_gs(args):
     time.sleep(0.3)
     evs = []
     stats_list = []
-    if world > 1:
-        dist.barrier()
+    reps.barrier()
     torch.cuda.synchronize()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -304,17 +340,12 @@ def run_gs(args):
         evs.append((e0, e1))
         stats_list.append(st)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    reps.barrier()
     clocks = sampler.stop()
-    ms = float(sum(a.elapsed_time(b) for a, b in evs)) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reps.max_ms(float(sum(a.elapsed_time(b) for a, b in evs)) / args.steps)
 
     units = float(wl.M) * wl.N * hs.size            # kernel evaluations one step stands for
-    value = units * world / (ms / 1e3)
+    value = reps.throughput(units, ms)
     base_ms = float(np.mean([s.ms_phase[gs.GS_PH_BASE] / max(1, s.launches_base) for s in stats_list]))
     evals_base = float(np.mean([s.point_pairs_base / max(1, s.launches_base) for s in stats_list]))
     launches = int(np.mean([s.launches for s in stats_list]))
@@ -393,8 +424,7 @@ def run_gs(args):
             line["lscv"] = {"h": [float(v) for v in wl.h], "score": [float(v) for v in sc],
                             "err_bound": [float(v) for v in er], "argmin_h": float(wl.h[int(np.argmin(sc))])}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
 
 
 def selector_opts(args, opts):
