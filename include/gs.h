@@ -290,6 +290,20 @@ void gs_tree_free(gs_tree *tree);
 int gs_sum_trees(const gs_tree *q, const gs_tree *r, const double *h, int nh, double eps, double *out,
                  const gs_opts *opts, void *stream, gs_stats *stats);
 
+/*
+ * gs_lscv_trees -- gs_lscv on a built reference tree (gs_build_tree with
+ * weights): the LSCV score of each bandwidth h[j] (nh in [1, 32]) from the
+ * dual-tree sums at h[j] and sqrt(2) h[j] (reading of the LSCV score:
+ * Section 7's bandwidth selection), reusing the tree across calls -- the
+ * building block of a search for the minimising bandwidth.
+ *   score, score_err   HOST arrays of nh doubles: scores and the bounds eps
+ *                      implies on them (score_err may be NULL)
+ * eps in (0, 1).  Returns gs_sum_trees' codes; GS_ERR_ARG also for a tree
+ * without weights or with fewer than 2 points.  Synchronises the stream.
+ */
+int gs_lscv_trees(const gs_tree *t, const double *h, int nh, double eps, double *score, double *score_err,
+                  const gs_opts *opts, void *stream, gs_stats *stats);
+
 /* ---- many problems in one call ------------------------------------------
  *
  * One independent Gaussian-sum problem (the arguments of gs_sum). */

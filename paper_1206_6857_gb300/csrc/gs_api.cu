@@ -188,6 +188,40 @@ __global__ void k_lscv_sums(const double *__restrict__ G, const float *__restric
     for (int i = threadIdx.x; i < 3 * nh; i += blockDim.x) atomicAdd(&acc[i], sh[i]);
 }
 
+// LSCV scores from the sums G (caller order, N x 2nh: h then sqrt(2) h) and
+// the weight total in *ing (device), on the host at the end:
+//   score = (4 pi h^2)^{-D/2} sum_i wbar_i G_{sqrt2 h}(x_i) / W
+//         - 2 (2 pi h^2)^{-D/2} sum_i wbar_i (G_h(x_i) - w_i) / (W - w_i)
+// and the bound eps implies on it (reading 17 of the LSCV score).
+int lscv_scores(const double *G, const float *weights, int64_t N, int D, const double *h, int nh, double eps,
+                const Ingest *ing, double *score, double *score_err, cudaStream_t st) {
+    double *acc = nullptr;
+    cudaError_t e = dev_malloc_async((void **)&acc, 3 * 32 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * 32 * sizeof(double), st);
+    if (e == cudaSuccess) {
+        int64_t blocks = (N + 255) / 256;
+        if (blocks > 1024) blocks = 1024;
+        k_lscv_sums<<<(unsigned)blocks, 256, 0, st>>>(G, weights, N, nh, ing, acc);
+        e = cudaGetLastError();
+    }
+    double hacc[3 * 32];
+    Ingest hing;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hing, ing, sizeof(hing), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (acc) cudaFreeAsync(acc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lscv scores");
+    const double W = hing.wsum;
+    const double pi = 3.141592653589793;
+    for (int j = 0; j < nh; ++j) {
+        const double c2 = pow(4.0 * pi * h[j] * h[j], -0.5 * D);
+        const double c1 = pow(2.0 * pi * h[j] * h[j], -0.5 * D);
+        score[j] = c2 * hacc[3 * j] / W - 2.0 * c1 * hacc[3 * j + 1];
+        if (score_err) score_err[j] = eps * (c2 * hacc[3 * j] / W + 2.0 * c1 * hacc[3 * j + 2]);
+    }
+    return GS_OK;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -336,44 +370,20 @@ int gs_lscv(const void *pts, int64_t N, int D, int dtype, const float *weights, 
         hh[nh + j] = h[j] * 1.4142135623730951;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    double *G = nullptr, *acc = nullptr;
+    double *G = nullptr;
     Ingest *ing = nullptr;
     GS_CUDA_TRY(dev_malloc_async((void **)&G, (size_t)N * 2 * nh * sizeof(double), st));
     int rc = sum_impl(pts, N, pts, weights, N, D, dtype, hh, 2 * nh, eps, G, opts, stream, stats, nullptr);
     if (rc == GS_OK) {
-        // total weight (the library's own ingest reduction) and the sums
+        // total weight (the library's own ingest reduction), then the scores
         cudaError_t e = dev_malloc_async((void **)&ing, sizeof(Ingest), st);
-        if (e == cudaSuccess) e = dev_malloc_async((void **)&acc, 3 * 32 * sizeof(double), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 3 * 32 * sizeof(double), st);
         CallCtx cx;
         cx.st = st;
         if (e == cudaSuccess) e = launch_ingest(ing, pts, N, pts, weights, N, D, dtype, cx);
-        if (e == cudaSuccess) {
-            int64_t blocks = (N + 255) / 256;
-            if (blocks > 1024) blocks = 1024;
-            k_lscv_sums<<<(unsigned)blocks, 256, 0, st>>>(G, weights, N, nh, ing, acc);
-            e = cudaGetLastError();
-        }
-        double hacc[3 * 32];
-        Ingest hing;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&hing, ing, sizeof(hing), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "gs_lscv");
-        } else {
-            const double W = hing.wsum;
-            const double pi = 3.141592653589793;
-            for (int j = 0; j < nh; ++j) {
-                const double c2 = pow(4.0 * pi * h[j] * h[j], -0.5 * D);
-                const double c1 = pow(2.0 * pi * h[j] * h[j], -0.5 * D);
-                score[j] = c2 * hacc[3 * j] / W - 2.0 * c1 * hacc[3 * j + 1];
-                if (score_err) score_err[j] = eps * (c2 * hacc[3 * j] / W + 2.0 * c1 * hacc[3 * j + 2]);
-            }
-        }
+        rc = e == cudaSuccess ? lscv_scores(G, weights, N, D, h, nh, eps, ing, score, score_err, st)
+                              : cuda_fail(e, "gs_lscv");
     }
     cudaFreeAsync(G, st);
-    if (acc) cudaFreeAsync(acc, st);
     if (ing) cudaFreeAsync(ing, st);
     return rc;
 }

@@ -125,6 +125,12 @@ cudaError_t scratch_pool(cudaMemPool_t *out);
 // Device status bits -> GS_ERR_* code (and message); GS_OK when clear.
 int status_to_code(unsigned st);
 
+// LSCV scores (and their eps-implied bounds) of nh bandwidths from the sums
+// G (caller order, N x 2nh: h then sqrt(2) h) and the weight total in *ing;
+// synchronises the stream.
+int lscv_scores(const double *G, const float *weights, int64_t N, int D, const double *h, int nh, double eps,
+                const Ingest *ing, double *score, double *score_err, cudaStream_t st);
+
 // Host-side error reporting (thread-local message).
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);

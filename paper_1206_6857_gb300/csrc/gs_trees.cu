@@ -168,3 +168,32 @@ extern "C" int gs_sum_trees(const gs_tree *qt, const gs_tree *rt, const double *
     if (rc == GS_OK && stats) cx.finish();
     return rc;
 }
+
+extern "C" int gs_lscv_trees(const gs_tree *t, const double *h, int nh, double eps, double *score, double *score_err,
+                             const gs_opts *opts, void *stream, gs_stats *stats) {
+    if (!t || !h || !score || nh < 1 || nh > 32) {
+        set_error("gs_lscv_trees: NULL tree, h or score, or nh outside [1, 32]");
+        return GS_ERR_ARG;
+    }
+    if (!t->w) {
+        set_error("gs_lscv_trees: the tree was built without weights");
+        return GS_ERR_ARG;
+    }
+    if (t->t.n < 2) {
+        set_error("gs_lscv_trees needs N >= 2");
+        return GS_ERR_ARG;
+    }
+    double hh[64];
+    for (int j = 0; j < nh; ++j) {
+        hh[j] = h[j];
+        hh[nh + j] = h[j] * 1.4142135623730951;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = t->t.n;
+    double *G = nullptr;
+    GS_CUDA_TRY(dev_malloc_async((void **)&G, (size_t)N * 2 * nh * sizeof(double), st));
+    int rc = gs_sum_trees(t, t, hh, 2 * nh, eps, G, opts, stream, stats);
+    if (rc == GS_OK) rc = lscv_scores(G, t->w, N, t->t.D, h, nh, eps, t->ing, score, score_err, st);
+    cudaFreeAsync(G, st);
+    return rc;
+}

@@ -117,6 +117,7 @@ SIGNATURES = {
     "gs_build_tree": (ctypes.c_int, [_VP, ctypes.c_int, _I64, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "gs_tree_free": (None, [_VP]),
     "gs_sum_trees": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP]),
+    "gs_lscv_trees": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
     "gs_selector_samples": (ctypes.c_int, [_VP, _I64, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, _VP,
                                            ctypes.c_int, ctypes.c_double, _VP, _VP, _VP, _VP, _VP, _I64, _VP,
                                            _VP, _VP]),
@@ -409,6 +410,18 @@ class Tree:
             self.close()
         except Exception:
             pass
+
+
+def gs_lscv_trees(tree: Tree, h, eps, opts: gs_opts | None = None, stream=None, stats: gs_stats | None = None):
+    """LSCV scores and their eps-implied bounds for the bandwidths h (at most
+    32) on a built reference tree; returns (score, err) host arrays."""
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    score = np.empty(hh.size)
+    err = np.empty(hh.size)
+    _check(load().gs_lscv_trees(tree._h, hh.ctypes.data, hh.size, float(eps), score.ctypes.data, err.ctypes.data,
+                                ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream),
+                                ctypes.byref(stats) if stats is not None else None))
+    return score, err
 
 
 def gs_sum_trees(qtree: Tree, rtree: Tree, h, eps, out=None, opts: gs_opts | None = None, stream=None,

@@ -48,3 +48,33 @@ def test_lscv_full_size_sweep_runs(gs):
     # the optimum lies strictly inside the sweep for clustered data
     k = int(np.argmin(score))
     assert 0 < k < wl.h.size - 1
+
+
+def test_lscv_trees_equal_gs_lscv(gs):
+    """gs_lscv_trees on a built tree gives gs_lscv's scores."""
+    x, _, w = synth.small_random(210, 4000, 3)
+    h = synth.log_bandwidths(synth.bbox_diagonal(x), 6, 1e-2, 1.0)
+    tx, tw = _dev(x), _dev(w)
+    a, ea = gs.gs_lscv(tx, tw, h, 1e-2)
+    tree = gs.Tree(tx, tw)
+    b, eb = gs.gs_lscv_trees(tree, h, 1e-2)
+    tree.close()
+    assert np.allclose(a, b, rtol=1e-9, atol=1e-12 * np.abs(a).max())
+    assert np.allclose(ea, eb, rtol=1e-9)
+
+
+def test_bandwidth_search_matches_the_oracle_search(gs):
+    """lscv_search.minimize (GPU scores on one tree) against the same search
+    run on the oracle's exact scores: the same bandwidth, or one whose exact
+    score is within the GPU score's error bound of the oracle's best."""
+    from paper_1206_6857_gb300 import lscv_search
+    x, _, w = synth.small_random(211, 3000, 2)
+    diam = synth.bbox_diagonal(x)
+    lo, hi = 1e-3 * diam, diam
+    tx, tw = _dev(x), _dev(w)
+    h, s, err, hist = lscv_search.minimize(tx, tw, 1e-3, lo, hi, rounds=4, per_round=8)
+    ho, so, _ = lscv_search.search(lambda hs: oracle_lscv.lscv(x, w, np.asarray(hs)), lo, hi, rounds=4, per_round=8)
+    exact_at_h = float(oracle_lscv.lscv(x, w, np.array([h]))[0])
+    assert abs(s - exact_at_h) <= err * (1 + 1e-6)
+    assert h == pytest.approx(ho, rel=1e-12) or exact_at_h <= so + 2 * err
+    assert sum(len(hs) for hs, _ in hist) == 32

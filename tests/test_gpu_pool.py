@@ -30,14 +30,16 @@ def test_pool_keeps_and_trims(gs):
     tw = torch.from_numpy(w).cuda()
     exact = oracle_ex.gauss_sum(q, q, w, h)
     W = float(w.astype(np.float64).sum())
+    torch.cuda.synchronize()
+    _, used0 = gs.gs_pool_bytes()        # earlier calls of this process may hold pool memory (trees)
     a = gs.gs_sum(tq, tq, tw, h, 1e-2).cpu().numpy()
     torch.cuda.synchronize()
     reserved, used = gs.gs_pool_bytes()
-    assert used == 0                     # every scratch buffer went back to the pool
-    assert reserved > 0                  # ... and the pool kept it
+    assert used == used0                 # every scratch buffer of the call went back to the pool
+    assert reserved > used               # ... and the pool kept it
     gs.gs_trim_memory(0)
     reserved2, used2 = gs.gs_pool_bytes()
-    assert used2 == 0 and reserved2 < reserved
+    assert used2 == used0 and reserved2 < reserved
     b = gs.gs_sum(tq, tq, tw, h, 1e-2).cpu().numpy()
     assert np.allclose(a, b, rtol=1e-9, atol=0)
     assert rel_err(b, exact, W).max() <= 1e-2
