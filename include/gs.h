@@ -440,8 +440,8 @@ int gs_selector_samples(const void *queries, int64_t M, const void *refs, const 
  * scratch allocations (of any call, any thread) the next one fails as if the
  * device were out of memory, once; n < 0 disarms.  The call that meets the
  * failure returns GS_ERR_OOM and later calls work normally (the tree build,
- * the traversal buffers and the outputs are freed on that path; a few small
- * scratch arrays of the base case and series phases may stay allocated).
+ * the traversal buffers, the outputs and every phase's scratch are freed on
+ * that path, so the library's pool gets all of it back).
  */
 void gs_debug_fail_alloc(long long n);
 

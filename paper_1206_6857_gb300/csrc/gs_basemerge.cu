@@ -438,9 +438,24 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     long long *off = nullptr;
     MergedEntry *ent = nullptr;
     float *rec2 = nullptr;
-    GS_CUDA_TRY(dev_malloc_async((void **)&mask, (size_t)lq * lr * sizeof(uint32_t), st));
-    GS_CUDA_TRY(cudaMemsetAsync(mask, 0, (size_t)lq * lr * sizeof(uint32_t), st));
-    GS_CUDA_TRY(dev_malloc_async((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
+    // a failed call frees what this phase holds, so the pool gets it back
+    auto release = [&]() {
+        if (mask) cudaFreeAsync(mask, st);
+        if (off) cudaFreeAsync(off, st);
+        if (ent) cudaFreeAsync(ent, st);
+        if (rec2) cudaFreeAsync(rec2, st);
+    };
+#define GS_TRY_M(call)                        \
+    do {                                      \
+        cudaError_t e__ = (call);             \
+        if (e__ != cudaSuccess) {             \
+            release();                        \
+            return cuda_fail(e__, #call);     \
+        }                                     \
+    } while (0)
+    GS_TRY_M(dev_malloc_async((void **)&mask, (size_t)lq * lr * sizeof(uint32_t), st));
+    GS_TRY_M(cudaMemsetAsync(mask, 0, (size_t)lq * lr * sizeof(uint32_t), st));
+    GS_TRY_M(dev_malloc_async((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
     const int grid = fb.grid_warps / 8;
     // mask bit of each bandwidth: its rank in ascending h
     int order[64];
@@ -457,17 +472,17 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     k_row_count<<<grid, 256, 0, st>>>(mask, lq, lr, off);
     cx.launches += 2;
     if (int rc0 = scan_i64(off, lq, off + lq, cx)) {
-        cudaFreeAsync(mask, st);
-        cudaFreeAsync(off, st);
+        release();
         return rc0;
     }
     long long total = 0;
-    GS_CUDA_TRY(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
-    GS_CUDA_TRY(cudaStreamSynchronize(st));
-    GS_CUDA_TRY(dev_malloc_async((void **)&ent, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
+    GS_TRY_M(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
+    GS_TRY_M(cudaStreamSynchronize(st));
+    GS_TRY_M(dev_malloc_async((void **)&ent, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
     k_row_compact<<<grid, 256, 0, st>>>(mask, lq, lr, rleaf0, off, ent);
     cx.launches += 1;
     cudaFreeAsync(mask, st);
+    mask = nullptr;
     int rc = cx.check("merge base pairs");
     if (!rc) {
         MergedParams bp;
@@ -496,7 +511,7 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         const int Q = qpl <= 1 ? 1 : (qpl <= 2 ? 2 : 4);
         if (merged_x2(DP, Q)) {
             const int64_t nf = in.rt->n * (int64_t)in.rt->rec_stride;
-            GS_CUDA_TRY(dev_malloc_async((void **)&rec2, (size_t)nf * 2 * sizeof(float), st));
+            GS_TRY_M(dev_malloc_async((void **)&rec2, (size_t)nf * 2 * sizeof(float), st));
             k_dup_records<<<grid, 256, 0, st>>>(in.rt->rec, nf, (float2 *)rec2);
             cx.launches += 1;
             bp.rrec2 = rec2;
@@ -519,9 +534,8 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         cx.launches_base += 1;
         if (!rc) rc = cx.check("k_basecase_merged");
     }
-    cudaFreeAsync(ent, st);
-    cudaFreeAsync(off, st);
-    if (rec2) cudaFreeAsync(rec2, st);
+    release();
+#undef GS_TRY_M
     cx.phase(GS_PH_OTHER);
     if (rc) return rc;
     cudaError_t e = cudaGetLastError();

@@ -783,14 +783,25 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         long long *pieces[2] = {nullptr, nullptr};
         SeriesEntry *h2l_sorted = nullptr;          // the H2L list bucketed by kernel (D = 3)
         unsigned long long *h2l_ctl = nullptr;
+        auto free_pieces = [&]() {
+            for (int m = 0; m < 2; ++m)
+                if (pieces[m]) cudaFreeAsync(pieces[m], st);
+        };
         for (int m = 0; m < 2; ++m) {
             const int64_t ne = fb.n_series[m];
             if (ne == 0) continue;
-            GS_CUDA_TRY(dev_malloc_async((void **)&pieces[m], (size_t)(ne + 1) * sizeof(long long), st));
+            const cudaError_t e = dev_malloc_async((void **)&pieces[m], (size_t)(ne + 1) * sizeof(long long), st);
+            if (e != cudaSuccess) {
+                free_pieces();
+                return cuda_fail(e, "series pieces");
+            }
             k_chunk_count<<<(unsigned)((ne + 255) / 256 < 4096 ? (ne + 255) / 256 : 4096), 256, 0, st>>>(
                 fb.series[m], ne, m == 0, sp.qn, sp.rn, pieces[m]);
             cx.launches += 1;
-            if ((rc = scan_i64(pieces[m], ne, pieces[m] + ne, cx))) return rc;
+            if ((rc = scan_i64(pieces[m], ne, pieces[m] + ne, cx))) {
+                free_pieces();
+                return rc;
+            }
         }
         auto launch = [&](int which, int64_t n, size_t per_warp) -> int {
             if (n <= 0) return GS_OK;
@@ -861,8 +872,7 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         if (h2l_sorted) cudaFreeAsync(h2l_sorted, st);
         if (h2l_ctl) cudaFreeAsync(h2l_ctl, st);
         cx.mark(-1);
-        for (int m = 0; m < 2; ++m)
-            if (pieces[m]) cudaFreeAsync(pieces[m], st);
+        free_pieces();
         if (rc) return rc;
         cx.phase(GS_PH_DOWN);
         for (int k = 0; k < in.qt->depth; ++k) {

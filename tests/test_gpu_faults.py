@@ -33,10 +33,14 @@ def test_injected_allocation_failures(gs):
     tq, tw = _dev(q), _dev(w)
     exact = oracle_ex.gauss_sum(q, q, w, h)
     W = float(w.astype(np.float64).sum())
+    import torch
     lib = gs.load()
     failed = 0
+    torch.cuda.synchronize()
+    _, used0 = gs.gs_pool_bytes()
+    leaks = {}
     try:
-        for n in (0, 1, 2, 5, 9, 17, 33, 65):
+        for n in (0, 1, 2, 5, 9, 17, 33, 65, 129):
             lib.gs_debug_fail_alloc(n)
             try:
                 gs.gs_sum(tq, tq, tw, h, 1e-2)
@@ -44,11 +48,14 @@ def test_injected_allocation_failures(gs):
                 assert e.code == gs.GS_ERR_OOM, e
                 failed += 1
             lib.gs_debug_fail_alloc(-1)
+            torch.cuda.synchronize()
+            leaks[n] = gs.gs_pool_bytes()[1] - used0        # scratch the failed call did not return
             out = gs.gs_sum(tq, tq, tw, h, 1e-2).cpu().numpy()      # the library is still usable
             assert rel_err(out, exact, W).max() <= 1e-2
     finally:
         lib.gs_debug_fail_alloc(-1)
     assert failed >= 4
+    assert all(v == 0 for v in leaks.values()), leaks
 
 
 def test_invalid_inputs_are_refused(gs):
