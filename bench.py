@@ -44,8 +44,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--mode", default="lscv", choices=["lscv", "sum", "batch"])
-    ap.add_argument("--selector", default="rule", choices=["rule", "mlp"],
-                    help="pair selector: Fig. 6's rule or the stored learned network")
+    ap.add_argument("--selector", default="rule", choices=["rule", "mlp", "fd_only"],
+                    help="pair selector: Fig. 6's rule, the stored learned network, or FD pruning only "
+                         "(the paper's DFD/DFDO comparison: no series approximations)")
+    ap.add_argument("--no-tokens", action="store_true",
+                    help="Theorem 2 without the token scheme (each pair within its own W_R share)")
     ap.add_argument("--count", type=int, default=256, help="problems in --mode batch")
     ap.add_argument("--workers", type=int, default=16, help="concurrent problems in --mode batch")
     ap.add_argument("--no-small-exhaustive", action="store_true",
@@ -307,8 +310,9 @@ def run_gs(args):
         opts = autotune.options(tuned)
 
     opts, _sel_params = selector_opts(args, opts)
-    if _sel_params is not None and tuned is not None:
-        tuned["selector"] = "mlp"
+    if tuned is not None:
+        tuned["selector"] = args.selector
+        tuned["tokens"] = not args.no_tokens
 
     def step(stats=None):
         if args.mode == "lscv":
@@ -428,12 +432,20 @@ def run_gs(args):
 
 
 def selector_opts(args, opts):
-    """Options with the stored learned selector when --selector mlp."""
-    if args.selector != "mlp":
+    """Options for --selector (the stored learned network for mlp, FD
+    pruning only for fd_only) and --no-tokens."""
+    from paper_1206_6857_gb300 import gs
+    if args.selector == "rule" and not args.no_tokens:
         return opts, None
-    from paper_1206_6857_gb300 import gs, selector
-    params = selector.load()
     o = opts if opts is not None else gs.gs_opts_default()
+    if args.no_tokens:
+        o.no_tokens = 1
+    if args.selector == "fd_only":
+        o.selector = gs.GS_SEL_FD_ONLY
+    if args.selector != "mlp":
+        return o, None
+    from paper_1206_6857_gb300 import selector
+    params = selector.load()
     o.selector = gs.GS_SEL_MLP
     o.selector_params = params.data_ptr()
     return o, params
