@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
-    ap.add_argument("--mode", default="lscv", choices=["lscv", "sum", "batch"])
+    ap.add_argument("--mode", default="lscv", choices=["lscv", "sum", "batch", "search"])
     ap.add_argument("--selector", default="rule", choices=["rule", "mlp", "fd_only"],
                     help="pair selector: Fig. 6's rule, the stored learned network, or FD pruning only "
                          "(the paper's DFD/DFDO comparison: no series approximations)")
@@ -71,9 +71,16 @@ def workload(scale, config=2):
     return {1: synth.config1, 2: synth.config2, 3: synth.config3, 4: synth.config4}[config](scale)
 
 
+SEARCH_ROUNDS, SEARCH_PER_ROUND = 4, 8   # --mode search: 32 LSCV scores per search
+
+
 def sum_bandwidths(wl, mode):
-    """Bandwidths one step sums over: the sweep, plus sqrt(2) h for LSCV."""
+    """Bandwidths one step sums over: the sweep, plus sqrt(2) h for LSCV;
+    for a bandwidth search, the 2 x 32 sums of its scores (their bandwidths
+    are chosen as it goes; the sweep's own set stands in for tuning)."""
     from workloads import synth
+    if mode == "search":
+        return np.resize(synth.lscv_bandwidths(wl.h), 2 * SEARCH_ROUNDS * SEARCH_PER_ROUND)
     return synth.lscv_bandwidths(wl.h) if mode == "lscv" else wl.h
 
 
@@ -315,7 +322,14 @@ def run_gs(args):
         tuned["tokens"] = not args.no_tokens
 
     def step(stats=None):
-        if args.mode == "lscv":
+        if args.mode == "search":
+            # the LSCV-optimal bandwidth over the sweep's range: tree built once,
+            # SEARCH_ROUNDS calls of SEARCH_PER_ROUND scores each
+            from paper_1206_6857_gb300 import lscv_search
+            scores["search"] = lscv_search.minimize(tq, tw, eps, float(wl.h[0]), float(wl.h[-1]),
+                                                    rounds=SEARCH_ROUNDS, per_round=SEARCH_PER_ROUND, opts=opts,
+                                                    stream=stream, stats=stats)[:3]
+        elif args.mode == "lscv":
             scores["lscv"] = gs.gs_lscv(tq, tw, wl.h, eps, opts=opts, stream=stream, stats=stats)
         else:
             gs.gs_sum(tq, tr, tw, wl.h, eps, out=out, opts=opts, stream=stream, stats=stats)
@@ -359,10 +373,10 @@ def run_gs(args):
     ex2_rate, ffma_rate = gs.gs_probe_rates()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = ex2_rate * props.multi_processor_count * sm_mhz * 1e6 / 1e12
-    achieved = evals_base / (base_ms / 1e3) / 1e12
+    achieved = evals_base / (base_ms / 1e3) / 1e12 if base_ms > 0 else None
     kname = "k_exhaustive" if eps == 0.0 else "k_basecase"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
-            "frac": achieved / peak if peak else None,
+            "frac": achieved / peak if (peak and achieved) else None,
             "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d" % (
                 wl_config(wl, args.mode, eps)["workload"], args.mode, args.scale,
                 (tuned or {}).get("leaf_size", wl.leaf_size)), evals_base),
@@ -377,7 +391,16 @@ def run_gs(args):
         hq = torch.from_numpy(wl.queries).pin_memory()
         hw = torch.from_numpy(wl.weights).pin_memory()
         n_e2e = max(1, min(args.steps, 3))
-        if args.mode == "lscv":
+        if args.mode == "search":
+            from paper_1206_6857_gb300 import lscv_search
+
+            def e2e_step():
+                dq = hq.to(dev, non_blocking=True)
+                dw = hw.to(dev, non_blocking=True)
+                return lscv_search.minimize(dq, dw, eps, float(wl.h[0]), float(wl.h[-1]), rounds=SEARCH_ROUNDS,
+                                            per_round=SEARCH_PER_ROUND, opts=opts, stream=stream)
+            d2h = 2 * 8 * SEARCH_ROUNDS * SEARCH_PER_ROUND
+        elif args.mode == "lscv":
             def e2e_step():
                 dq = hq.to(dev, non_blocking=True)
                 dw = hw.to(dev, non_blocking=True)
@@ -423,6 +446,11 @@ def run_gs(args):
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches * args.steps,
                 "stats": {k: v for k, v in s0.as_dict().items()}}
+        if "search" in scores:
+            hb, sb, eb = scores["search"]
+            line["search"] = {"h_best": hb, "score": sb, "err_bound": eb, "rounds": SEARCH_ROUNDS,
+                              "per_round": SEARCH_PER_ROUND, "range": [float(wl.h[0]), float(wl.h[-1])],
+                              "note": "roofline and stats of the search's last call"}
         if "lscv" in scores:
             sc, er = scores["lscv"]
             line["lscv"] = {"h": [float(v) for v in wl.h], "score": [float(v) for v in sc],

@@ -44,19 +44,20 @@ def search(score_fn, lo: float, hi: float, rounds: int = 5, per_round: int = 8):
 
 
 def minimize(points, weights, eps: float, lo: float, hi: float, rounds: int = 5, per_round: int = 8,
-             opts=None, stream=None):
+             opts=None, stream=None, stats=None):
     """The LSCV-optimal bandwidth of a weighted point set on the GPU.
 
     points (N x D) and weights (N, float32) are torch CUDA tensors; the tree is
     built once (opts.leaf_size) and every round evaluates per_round
     bandwidths in one call.  Returns (h_best, score_best, err_best, history)
-    where err_best bounds |score - exact score| at h_best."""
+    where err_best bounds |score - exact score| at h_best.  stats (a gs_stats)
+    receives the statistics of the last call."""
     from . import gs
     tree = gs.Tree(points, weights, opts=opts, stream=stream)
     errs = {}
     try:
         def score_fn(hs):
-            s, e = gs.gs_lscv_trees(tree, hs, eps, opts=opts, stream=stream)
+            s, e = gs.gs_lscv_trees(tree, hs, eps, opts=opts, stream=stream, stats=stats)
             for h, v in zip(hs, e):
                 errs[float(h)] = float(v)
             return s
