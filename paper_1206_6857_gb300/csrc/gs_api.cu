@@ -165,27 +165,45 @@ int status_to_code(unsigned st) {
     return GS_OK;
 }
 
-// LSCV partial sums per bandwidth j (atomics across blocks):
+// LSCV partial sums per bandwidth j (one pass over the points per j, sums
+// in registers, then the warp and the block, one atomic per block):
 //   acc[3j]   += wbar_i G_{sqrt2 h}(x_i)
 //   acc[3j+1] += wbar_i (G_h(x_i) - w_i) / (W - w_i)
 //   acc[3j+2] += wbar_i G_h(x_i) / (W - w_i)
-__global__ void k_lscv_sums(const double *__restrict__ G, const float *__restrict__ w, int64_t N, int nh,
-                            const Ingest *__restrict__ ing, double *acc) {
-    __shared__ double sh[3 * 32];
-    for (int i = threadIdx.x; i < 3 * nh; i += blockDim.x) sh[i] = 0.0;
-    __syncthreads();
+__global__ void __launch_bounds__(256) k_lscv_sums(const double *__restrict__ G, const float *__restrict__ w,
+                                                   int64_t N, int nh, const Ingest *__restrict__ ing, double *acc) {
+    __shared__ double sh[3][8];
     const double W = ing->wsum;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double wi = (double)w[i], wb = wi / W, den = W - wi;
-        for (int j = 0; j < nh; ++j) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int j = 0; j < nh; ++j) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const double wi = (double)w[i], wb = wi / W, den = W - wi;
             const double gh = G[i * 2 * nh + j], g2 = G[i * 2 * nh + nh + j];
-            atomicAdd(&sh[3 * j], wb * g2);
-            atomicAdd(&sh[3 * j + 1], wb * (gh - wi) / den);
-            atomicAdd(&sh[3 * j + 2], wb * gh / den);
+            a0 += wb * g2;
+            a1 += wb * (gh - wi) / den;
+            a2 += wb * gh / den;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            sh[0][wp] = a0;
+            sh[1][wp] = a1;
+            sh[2][wp] = a2;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double s = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[threadIdx.x][k];
+            atomicAdd(&acc[3 * j + threadIdx.x], s);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 3 * nh; i += blockDim.x) atomicAdd(&acc[i], sh[i]);
 }
 
 // LSCV scores from the sums G (caller order, N x 2nh: h then sqrt(2) h) and

@@ -565,11 +565,17 @@ __global__ void __launch_bounds__(128) k_series_h2l_d3(SeriesParams sp, const Se
     }
 }
 
-// Bucket the H2L list by kernel: warp-aggregated counts, then the start of
-// each bucket, then a scatter (the order inside a bucket is free: every
-// action adds into B with atomics)
-__global__ void k_h2l_count(const SeriesEntry *__restrict__ ent, const FrontierState *__restrict__ fs, int D,
-                            int64_t cap, unsigned long long *cnt) {
+// Bucket the H2L list by kernel: counts (per warp, then per block, then one
+// global atomic per block and bucket), the start of each bucket, then a
+// scatter that reserves each block chunk's range per bucket with one global
+// atomic.  The order inside a bucket is free: every action adds into B with
+// atomics.
+__global__ void __launch_bounds__(256) k_h2l_count(const SeriesEntry *__restrict__ ent,
+                                                   const FrontierState *__restrict__ fs, int D, int64_t cap,
+                                                   unsigned long long *cnt) {
+    __shared__ unsigned int c[kH2lBuckets];
+    if (threadIdx.x < kH2lBuckets) c[threadIdx.x] = 0;
+    __syncthreads();
     const int64_t ne = fs->series_count[2] < cap ? fs->series_count[2] : cap;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -578,8 +584,10 @@ __global__ void k_h2l_count(const SeriesEntry *__restrict__ ent, const FrontierS
         const int64_t e = w0 + lane;
         const int b = e < ne ? h2l_bucket(D, ent[e].p) : -1;
         const unsigned m = __match_any_sync(0xffffffffu, b);
-        if (b >= 0 && lane == __ffs(m) - 1) atomicAdd(&cnt[b], (unsigned long long)__popc(m));
+        if (b >= 0 && lane == __ffs(m) - 1) atomicAdd(&c[b], (unsigned)__popc(m));
     }
+    __syncthreads();
+    if (threadIdx.x < kH2lBuckets && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], (unsigned long long)c[threadIdx.x]);
 }
 
 __global__ void k_h2l_starts(const unsigned long long *cnt, unsigned long long *cur, unsigned long long *bounds) {
@@ -594,14 +602,20 @@ __global__ void k_h2l_starts(const unsigned long long *cnt, unsigned long long *
     }
 }
 
-__global__ void k_h2l_scatter(const SeriesEntry *__restrict__ ent, const FrontierState *__restrict__ fs, int D,
-                              int64_t cap, unsigned long long *cur, SeriesEntry *out) {
+__global__ void __launch_bounds__(256) k_h2l_scatter(const SeriesEntry *__restrict__ ent,
+                                                     const FrontierState *__restrict__ fs, int D, int64_t cap,
+                                                     unsigned long long *cur, SeriesEntry *out) {
+    __shared__ unsigned int sc[kH2lBuckets];          // this chunk's count per bucket
+    __shared__ unsigned long long sb[kH2lBuckets];    // its reserved start per bucket
     const int64_t ne = fs->series_count[2] < cap ? fs->series_count[2] : cap;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t w0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); w0 < ne; w0 += stride) {
-        const int64_t e = w0 + lane;
+    // the whole block steps through chunks of blockDim entries together
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < ne; base += stride) {
+        if (threadIdx.x < kH2lBuckets) sc[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t e = base + threadIdx.x;
         SeriesEntry E;
         int b = -1;
         if (e < ne) {
@@ -610,10 +624,15 @@ __global__ void k_h2l_scatter(const SeriesEntry *__restrict__ ent, const Frontie
         }
         const unsigned m = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if (b >= 0 && lane == leader) base = atomicAdd(&cur[b], (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (b >= 0) out[base + __popc(m & lt)] = E;
+        unsigned woff = 0;
+        if (b >= 0 && lane == leader) woff = atomicAdd(&sc[b], (unsigned)__popc(m));
+        woff = __shfl_sync(0xffffffffu, woff, leader);
+        __syncthreads();
+        if (threadIdx.x < kH2lBuckets)
+            sb[threadIdx.x] = sc[threadIdx.x] ? atomicAdd(&cur[threadIdx.x], (unsigned long long)sc[threadIdx.x]) : 0ull;
+        __syncthreads();
+        if (b >= 0) out[sb[b] + woff + __popc(m & lt)] = E;
+        __syncthreads();   // sc and sb are rewritten by the next chunk
     }
 }
 
