@@ -462,7 +462,7 @@ int gs_probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, void *stream
  * stays in that pool for later calls (a traversal synchronises once per
  * frontier iteration, and a pool that gave memory back at each
  * synchronisation would map its work lists afresh every time).  This call
- * waits for the current device and returns to the driver all but keep_bytes
+ * waits for the current device and returns to the CUDA driver all but keep_bytes
  * of that device's pool.  Memory held by built trees (gs_tree) is not
  * affected.
  * Returns GS_OK, or GS_ERR_CUDA (message in gs_last_error).
@@ -471,7 +471,7 @@ int gs_trim_memory(size_t keep_bytes);
 
 /*
  * gs_pool_bytes -- bytes the library's pool of the current device holds
- * from the driver (reserved) and bytes of it in use, written to the HOST
+ * from the CUDA driver (reserved) and bytes of it in use, written to the HOST
  * pointers (either may be NULL).  Returns GS_OK or GS_ERR_CUDA.
  */
 int gs_pool_bytes(uint64_t *reserved, uint64_t *used);

@@ -45,7 +45,7 @@ cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st) {
 }
 
 // The library's own stream-ordered pool, one per device.  The device's
-// default pool returns freed memory to the driver at every synchronisation,
+// default pool returns freed memory to the CUDA driver at every synchronisation,
 // so a traversal that synchronises once per frontier iteration would map
 // its lists afresh each time; this pool keeps freed memory until
 // gs_trim_memory releases it.

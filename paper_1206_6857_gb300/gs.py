@@ -295,7 +295,7 @@ def gs_probe_rates(stream=None):
 
 
 def gs_trim_memory(keep_bytes=0):
-    """Return all but keep_bytes of the library's device pool to the driver."""
+    """Return all but keep_bytes of the library's device pool to the CUDA driver."""
     _check(load().gs_trim_memory(int(keep_bytes)))
 
 
