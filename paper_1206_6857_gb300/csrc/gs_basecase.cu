@@ -9,9 +9,9 @@
 // aligned) is read once per warp with a uniform-address load (one broadcast
 // transaction from L1/L2), and each lane forms the squared distance in FP32
 // from coordinate differences and adds 2^(d^2 * c_j + l_r) from the MUFU ex2
-// unit.  Terms are summed in FP32 over one reference leaf and in FP64 across
-// leaves; the group's per-query totals go to the sorted-order accumulator
-// with FP64 atomics.  For FP64 input the records hold coordinates relative to
+// unit.  Terms are summed in FP32 over one reference leaf, in compensated
+// FP32 across leaves and in FP64 across warps; the group's per-query totals
+// go to the sorted-order accumulator with FP64 atomics.  For FP64 input the records hold coordinates relative to
 // their leaf centre and each leaf pair adds the FP64 centre difference
 // (rounded once to FP32) to every coordinate difference.
 #include <math.h>
@@ -22,8 +22,6 @@
 #include "gs_tree.cuh"
 
 namespace gs {
-
-constexpr int kLeavesPerRun = 4;
 
 struct BaseParams {
     const float *qrec, *rrec;
@@ -63,17 +61,16 @@ k_basecase(BaseParams bp, const Group *__restrict__ bgroups, const int32_t *__re
 #pragma unroll
         for (int d = 0; d < DP; ++d) xq[s][d] = bp.qrec[pos * NT + d];
     }
-    // three-level summation: FP32 over one reference leaf, FP32 over up to
-    // kLeavesPerRun leaves, FP64 across runs (keeps the FP64 pipe off the
-    // critical path while bounding each FP32 sum to a few hundred terms)
-    double acc[QPL];
-    float run[QPL];
+    // summation: FP32 over one reference leaf, then a compensated (Kahan)
+    // FP32 sum across leaves, FP64 across warps -- the scheme the FP32 error
+    // charge covers ((L_R - 1) u for the leaf, 2 u for the compensated sum)
+    // and the one of the merged base case; no FP64 work per leaf
+    float ksum[QPL], kcmp[QPL];
 #pragma unroll
     for (int s = 0; s < QPL; ++s) {
-        acc[s] = 0.0;
-        run[s] = 0.f;
+        ksum[s] = 0.f;
+        kcmp[s] = 0.f;
     }
-    int in_run = 0;
     unsigned long long grp_refs = 0;
     for (int k = w; k < G.cnt; k += kBaseWarps) {
         const int64_t rnode = base_r[G.off + k];
@@ -112,19 +109,16 @@ k_basecase(BaseParams bp, const Group *__restrict__ bgroups, const int32_t *__re
             }
         }
 #pragma unroll
-        for (int s = 0; s < QPL; ++s) run[s] += part[s];
-        if (++in_run == kLeavesPerRun) {
-#pragma unroll
-            for (int s = 0; s < QPL; ++s) {
-                acc[s] += (double)run[s];
-                run[s] = 0.f;
-            }
-            in_run = 0;
+        for (int s = 0; s < QPL; ++s) {
+            const float y = __fsub_rn(part[s], kcmp[s]);
+            const float t = __fadd_rn(ksum[s], y);
+            kcmp[s] = __fsub_rn(__fsub_rn(t, ksum[s]), y);
+            ksum[s] = t;
         }
         grp_refs += (unsigned long long)nr;
     }
 #pragma unroll
-    for (int s = 0; s < QPL; ++s) red[w][s * 32 + lane] = acc[s] + (double)run[s];
+    for (int s = 0; s < QPL; ++s) red[w][s * 32 + lane] = (double)ksum[s] - (double)kcmp[s];
     __syncthreads();
     if (w == 0) {
 #pragma unroll
