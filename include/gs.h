@@ -293,7 +293,7 @@ int gs_sum_trees(const gs_tree *q, const gs_tree *r, const double *h, int nh, do
 /*
  * gs_lscv_trees -- gs_lscv on a built reference tree (gs_build_tree with
  * weights): the LSCV score of each bandwidth h[j] (nh in [1, 32]) from the
- * dual-tree sums at h[j] and sqrt(2) h[j] (reading of the LSCV score:
+ * dual-tree sums at h[j] and sqrt(2) h[j] (the score gs_lscv computes for
  * Section 7's bandwidth selection), reusing the tree across calls -- the
  * building block of a search for the minimising bandwidth.
  *   score, score_err   HOST arrays of nh doubles: scores and the bounds eps
