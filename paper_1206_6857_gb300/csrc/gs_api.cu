@@ -210,9 +210,10 @@ __global__ void __launch_bounds__(256) k_lscv_sums(const double *__restrict__ G,
 // the weight total in *ing (device), on the host at the end:
 //   score = (4 pi h^2)^{-D/2} sum_i wbar_i G_{sqrt2 h}(x_i) / W
 //         - 2 (2 pi h^2)^{-D/2} sum_i wbar_i (G_h(x_i) - w_i) / (W - w_i)
-// and the bound eps implies on it: every G is within eps of its exact value,
-// so the first term moves by at most eps times itself and the leave-one-out
-// term by at most eps (2 pi h^2)^{-D/2} sum_i wbar_i G_h(x_i) / (W - w_i).
+// and the bound eps implies on it: every G is within a relative eps of its
+// exact value, so the first term moves by at most eps times itself and the
+// leave-one-out term by at most 2 eps (2 pi h^2)^{-D/2} sum_i wbar_i G_h(x_i)
+// / (W - w_i).
 int lscv_scores(const double *G, const float *weights, int64_t N, int D, const double *h, int nh, double eps,
                 const Ingest *ing, double *score, double *score_err, cudaStream_t st) {
     double *acc = nullptr;
