@@ -430,9 +430,9 @@ def run_gs(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import build as ob
         ob.build()
-        # a bounded sample: about 3e10 kernel evaluations (10-20 s on the
+        # a bounded sample: about 4e10 kernel evaluations (10-30 s on the
         # host cores), whatever the workload's N and number of sums
-        nq = int(min(wl.M, max(16, round(3e10 / (float(wl.N) * hs.size)))))
+        nq = int(min(wl.M, max(16, round(4e10 / (float(wl.N) * hs.size)))))
         r, dt, cores = oracle_sample_rate(wl, nq, hs)
         cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
                "sample": "%d seeded queries x all %d refs x %d bandwidths (%.1f s)" % (nq, wl.N, hs.size, dt)}
