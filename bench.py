@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--leaf", type=int, default=0, help="fixed leaf size (skips the autotuner)")
     ap.add_argument("--cost", default="", help="fixed cost weights c_DH,c_DL,c_H2L,c_Direct (skips the autotuner)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy check after the timed steps (every result against the GPU "
+                         "exhaustive sum)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
                     help="workload for --mode sum: 1 (D=2, 1e4), 2 (D=3 sweep, 1e6), 3 (D=5, 5e5, eps 1e-3), "
                          "4 (D=16 bichromatic, 2e6 refs x 2e5 queries)")
@@ -72,6 +75,7 @@ def workload(scale, config=2):
 
 
 SEARCH_ROUNDS, SEARCH_PER_ROUND = 4, 8   # --mode search: 32 LSCV scores per search
+CERTIFY_STEPS = 2                        # re-scorings of the last grid at eps/4, eps/16 to certify h*
 
 
 def sum_bandwidths(wl, mode):
@@ -153,14 +157,18 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(wl, nq, hs, seed=0):
+def oracle_sample_rate(wl, nq, hs, seed=0, idx=None):
+    """The FP64 oracle timed on nq queries (seeded, or the given indices)
+    against every reference and bandwidth; returns (evals/s, seconds,
+    threads, the oracle's sums, the query indices)."""
     from oracle import exhaustive as oracle_ex
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(wl.M, nq, replace=False))
+    if idx is None:
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(wl.M, nq, replace=False))
     t0 = time.perf_counter()
-    oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, hs)
+    exact = oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, hs)
     dt = time.perf_counter() - t0
-    return nq * wl.N * hs.size / dt, dt, oracle_ex.num_threads()
+    return idx.size * wl.N * hs.size / dt, dt, oracle_ex.num_threads(), exact, idx
 
 
 def run_reference(args):
@@ -176,7 +184,7 @@ def run_reference(args):
         oracle_sample_rate(wl, max(1, nq // 8), hs, seed=99)
     rates, secs = [], []
     for k in range(args.steps):
-        r, dt, cores = oracle_sample_rate(wl, nq, hs, seed=k)
+        r, dt, cores, _, _ = oracle_sample_rate(wl, nq, hs, seed=k)
         rates.append(r)
         secs.append(dt)
     value = float(np.mean(rates))
@@ -326,9 +334,10 @@ def run_gs(args):
             # the LSCV-optimal bandwidth over the sweep's range: tree built once,
             # SEARCH_ROUNDS calls of SEARCH_PER_ROUND scores each
             from paper_1206_6857_gb300 import lscv_search
-            scores["search"] = lscv_search.minimize(tq, tw, eps, float(wl.h[0]), float(wl.h[-1]),
-                                                    rounds=SEARCH_ROUNDS, per_round=SEARCH_PER_ROUND, opts=opts,
-                                                    stream=stream, stats=stats)[:3]
+            r = lscv_search.minimize(tq, tw, eps, float(wl.h[0]), float(wl.h[-1]), rounds=SEARCH_ROUNDS,
+                                     per_round=SEARCH_PER_ROUND, opts=opts, stream=stream, stats=stats,
+                                     certify_steps=CERTIFY_STEPS)
+            scores["search"] = r[:3] + (r[4],)
         elif args.mode == "lscv":
             scores["lscv"] = gs.gs_lscv(tq, tw, wl.h, eps, opts=opts, stream=stream, stats=stats)
         else:
@@ -398,13 +407,15 @@ def run_gs(args):
                 dq = hq.to(dev, non_blocking=True)
                 dw = hw.to(dev, non_blocking=True)
                 return lscv_search.minimize(dq, dw, eps, float(wl.h[0]), float(wl.h[-1]), rounds=SEARCH_ROUNDS,
-                                            per_round=SEARCH_PER_ROUND, opts=opts, stream=stream)
+                                            per_round=SEARCH_PER_ROUND, opts=opts, stream=stream,
+                                            certify_steps=CERTIFY_STEPS)
             d2h = 2 * 8 * SEARCH_ROUNDS * SEARCH_PER_ROUND
         elif args.mode == "lscv":
+            hqn_l, hwn_l = hq.numpy(), hw.numpy()
+
             def e2e_step():
-                dq = hq.to(dev, non_blocking=True)
-                dw = hw.to(dev, non_blocking=True)
-                return gs.gs_lscv(dq, dw, wl.h, eps, opts=opts, stream=stream)   # returns host arrays
+                # host buffers through the C ABI: the library copies them in
+                return gs.gs_lscv_host(hqn_l, hwn_l, wl.h, eps, opts=opts)
             d2h = 2 * 8 * wl.h.size
         else:
             hout = torch.empty((wl.M, wl.h.size), dtype=torch.float64).pin_memory().numpy()
@@ -426,16 +437,54 @@ def run_gs(args):
         e2e = {"value": units / dt, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
 
+    # accuracy of the step's results (after the timed region): every result
+    # against the GPU exhaustive sum, and -- in the CPU baseline leg below --
+    # a sample that includes the smallest sums against the FP64 oracle
+    acc, dt_all, ex_all = None, None, None
+    if rank == 0 and args.mode in ("lscv", "sum") and not args.no_accuracy:
+        W = float(wl.weights.astype(np.float64).sum())
+        floor = 2.0 ** -40 * W
+        ex_all = gs.gs_sum(tq, tr, tw, hs, 0.0, stream=stream).cpu().numpy()
+        acc = {"floor": "2^-40 W", "results": int(ex_all.size),
+               "under_floor": int(np.sum(ex_all < floor))}
+        if eps > 0:
+            dt_all = gs.gs_sum(tq, tr, tw, hs, eps, opts=opts, stream=stream).cpu().numpy()
+            err = np.abs(dt_all - ex_all) / np.maximum(ex_all, floor)
+            acc["max_rel_err_vs_gpu_exhaustive"] = float(err.max())
+            acc["eps"] = eps
+            acc["within_eps"] = bool(err.max() <= eps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import build as ob
         ob.build()
         # a bounded sample: about 4e10 kernel evaluations (10-30 s on the
-        # host cores), whatever the workload's N and number of sums
-        nq = int(min(wl.M, max(16, round(4e10 / (float(wl.N) * hs.size)))))
-        r, dt, cores = oracle_sample_rate(wl, nq, hs)
+        # host cores), whatever the workload's N and number of sums; it holds
+        # the 64 queries with the smallest sums (a few per bandwidth, chosen
+        # from the GPU exhaustive output), where the relative guarantee is
+        # hardest, and seeded queries for the rest
+        nq = int(min(wl.M, max(80, round(4e10 / (float(wl.N) * hs.size)))))
+        pick = np.zeros(0, np.int64)
+        if ex_all is not None:
+            per_h = max(1, -(-64 // hs.size))
+            pick = np.unique(np.concatenate([np.argsort(ex_all[:, j], kind="stable")[:per_h]
+                                             for j in range(hs.size)]))[:64]
+        rest = np.setdiff1d(np.random.default_rng(0).choice(wl.M, nq, replace=False), pick)[:max(0, nq - pick.size)]
+        idx = np.sort(np.concatenate([pick, rest]).astype(np.int64))
+        r, secs, cores, exact, idx = oracle_sample_rate(wl, idx.size, hs, idx=idx)
         cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
-               "sample": "%d seeded queries x all %d refs x %d bandwidths (%.1f s)" % (nq, wl.N, hs.size, dt)}
+               "sample": "%d queries (%d with the smallest GPU-exhaustive sums, %d seeded) x all %d refs x %d "
+                         "bandwidths (%.1f s)" % (idx.size, pick.size, idx.size - pick.size, wl.N, hs.size, secs)}
+        if acc is not None:
+            W = float(wl.weights.astype(np.float64).sum())
+            den = np.maximum(exact, 2.0 ** -40 * W)
+            acc["oracle_sample"] = "the %d queries of cpu_baseline x %d bandwidths" % (idx.size, hs.size)
+            acc["fp32_err_exhaustive_vs_oracle"] = float((np.abs(ex_all[idx] - exact) / den).max())
+            if dt_all is not None:
+                acc["max_rel_err_vs_oracle"] = float((np.abs(dt_all[idx] - exact) / den).max())
+                sel = np.isin(idx, pick)
+                acc["max_rel_err_vs_oracle_smallest_sums"] = (
+                    float((np.abs(dt_all[idx[sel]] - exact[sel]) / den[sel]).max()) if sel.any() else None)
 
     if rank == 0:
         s0 = stats_list[-1]
@@ -447,16 +496,27 @@ def run_gs(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": launches * args.steps,
+                "accuracy": acc,
+                "units": "M*N*%d kernel evaluations per step: %s" % (
+                    hs.size, "the %d sweep bandwidths and their sqrt(2) h companions, all summed in the step"
+                    % wl.h.size if args.mode == "lscv" else "every bandwidth summed in the step"),
                 "stats": {k: v for k, v in s0.as_dict().items()}}
+        if args.mode == "lscv":
+            line["value_per_sweep_bandwidth"] = float(wl.M) * wl.N * wl.h.size / (ms / 1e3) * world
         if "search" in scores:
-            hb, sb, eb = scores["search"]
+            hb, sb, eb, cert = scores["search"]
             line["search"] = {"h_best": hb, "score": sb, "err_bound": eb, "rounds": SEARCH_ROUNDS,
                               "per_round": SEARCH_PER_ROUND, "range": [float(wl.h[0]), float(wl.h[-1])],
+                              "certified": cert["certified"], "certified_bracket": cert["bracket"],
+                              "certifying_eps": cert["eps"], "certified_neighbour_distance": cert["m"],
                               "note": "roofline and stats of the search's last call"}
         if "lscv" in scores:
             sc, er = scores["lscv"]
+            k = int(np.argmin(sc))
+            sep = all(sc[k] + er[k] < sc[i] - er[i] for i in (k - 1, k + 1) if 0 <= i < sc.size)
             line["lscv"] = {"h": [float(v) for v in wl.h], "score": [float(v) for v in sc],
-                            "err_bound": [float(v) for v in er], "argmin_h": float(wl.h[int(np.argmin(sc))])}
+                            "err_bound": [float(v) for v in er], "argmin_h": float(wl.h[k]),
+                            "argmin_separated_from_grid_neighbours": bool(sep)}
         print(json.dumps(line), flush=True)
     reps.close()
 
@@ -565,7 +625,7 @@ def run_batch(args):
         ob.build()
         rates, cores, tot = [], 1, 0.0
         for wl in wls[:16]:
-            r, dt, cores = oracle_sample_rate(wl, min(wl.M, 20), wl.h)
+            r, dt, cores, _, _ = oracle_sample_rate(wl, min(wl.M, 20), wl.h)
             rates.append(r)
             tot += dt
         cpu = {"value": float(np.mean(rates)), "unit": "evals/s", "cores": cores, "kind": "oracle",

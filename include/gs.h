@@ -226,6 +226,17 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
                 const gs_opts *opts, void *stream, gs_stats *stats);
 
 /*
+ * gs_lscv_host -- gs_lscv for callers whose points and weights live in HOST
+ * memory (pts: host N x D, dtype; weights: host N floats).  The call copies
+ * them to device scratch, runs gs_lscv on `stream` and returns the scores in
+ * the HOST arrays score / score_err as gs_lscv does.  Same arguments,
+ * results and errors as gs_lscv (Section 7's LSCV sweep).
+ */
+int gs_lscv_host(const void *pts, int64_t N, int D, int dtype, const float *weights, const double *h, int nh,
+                 double eps, double *score, double *score_err, const gs_opts *opts, void *stream,
+                 gs_stats *stats);
+
+/*
  * gs_sum_exhaustive_noalloc -- the exhaustive sum (gs_sum with eps = 0) for
  * callers that cannot let the library allocate device memory: runtimes that
  * own all device memory through their own allocator and forbid direct
@@ -235,17 +246,23 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine.  Its scratch
  * (a status word and the packed reference records) lives in one fixed 16 MiB
- * array of the library's device memory, resident on every device that loads
- * the library until the process exits.  Limits: the packed references must
+ * array of the library's device memory, which stays resident on each device
+ * that used it until the process exits.  Limits: the packed references must
  * fit that array -- e.g. up to about 1.0e6 references for FP32 data with
  * D <= 3, 5.2e5 for D <= 7, 2.1e5 for D = 16; larger N returns GS_ERR_ARG with
  * a message naming the limit.
  *
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the array and each call resets what it needs,
- * but calls whose GPU work overlaps (other streams, other host threads) race
- * on it: serialise them.
+ * First call per device: the CUDA runtime loads the library's device code on
+ * a device lazily, at its first use there, and that load maps the array and
+ * may allocate inside the driver (and can fail with an out-of-memory error).
+ * A caller that must not allocate mid-run makes one warm-up call per device
+ * at start-up, before any stream capture; later calls allocate nothing.
+ * Each call looks up the array's address for the current device
+ * (cudaGetSymbolAddress, a host-side lookup once the code is loaded), so the
+ * call stays correct after cudaDeviceReset -- which frees the array: the next
+ * call on that device is a first call again.  Every call shares the array
+ * and each call resets what it needs, but calls whose GPU work overlaps
+ * (other streams, other host threads) race on it: serialise them.
  *
  * Arguments, layouts and results are those of gs_sum (device queries, refs,
  * weights and out; HOST h; dtype GS_F32 or GS_F64; 1 <= nh <= 64).  Returns

@@ -421,30 +421,64 @@ int gs_sum_host(const void *queries, int64_t M, const void *refs, const float *w
     void *dq = nullptr, *dr = nullptr;
     float *dw = nullptr;
     double *dout = nullptr;
-    GS_CUDA_TRY(dev_malloc_async(&dr, (size_t)N * D * es, st));
-    if (!mono) GS_CUDA_TRY(dev_malloc_async(&dq, (size_t)M * D * es, st));
-    GS_CUDA_TRY(dev_malloc_async((void **)&dw, (size_t)N * sizeof(float), st));
-    GS_CUDA_TRY(dev_malloc_async((void **)&dout, (size_t)M * nh * sizeof(double), st));
-    if (mono) dq = dr;
-    cudaError_t e = cudaMemcpyAsync(dr, refs, (size_t)N * D * es, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !mono)
-        e = cudaMemcpyAsync(dq, queries, (size_t)M * D * es, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dw, weights, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-        rc = cuda_fail(e, "gs_sum_host upload");
-    } else {
-        rc = gs_sum(dq, M, dr, dw, N, D, dtype, h, nh, eps, dout, opts, stream, stats);
-        if (rc == GS_OK) {
-            e = cudaMemcpyAsync(out, dout, (size_t)M * nh * sizeof(double), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) rc = cuda_fail(e, "gs_sum_host download");
+    cudaError_t e = dev_malloc_async(&dr, (size_t)N * D * es, st);
+    if (e == cudaSuccess && !mono) e = dev_malloc_async(&dq, (size_t)M * D * es, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&dw, (size_t)N * sizeof(float), st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&dout, (size_t)M * nh * sizeof(double), st);
+    if (e == cudaSuccess) {
+        if (mono) dq = dr;
+        e = cudaMemcpyAsync(dr, refs, (size_t)N * D * es, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !mono)
+            e = cudaMemcpyAsync(dq, queries, (size_t)M * D * es, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dw, weights, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "gs_sum_host upload");
+        } else {
+            rc = gs_sum(dq, M, dr, dw, N, D, dtype, h, nh, eps, dout, opts, stream, stats);
+            if (rc == GS_OK) {
+                e = cudaMemcpyAsync(out, dout, (size_t)M * nh * sizeof(double), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) rc = cuda_fail(e, "gs_sum_host download");
+            }
         }
+    } else {
+        rc = cuda_fail(e, "gs_sum_host scratch");
     }
-    cudaFreeAsync(dr, st);
-    if (!mono) cudaFreeAsync(dq, st);
-    cudaFreeAsync(dw, st);
-    cudaFreeAsync(dout, st);
+    if (dr) cudaFreeAsync(dr, st);
+    if (!mono && dq) cudaFreeAsync(dq, st);
+    if (dw) cudaFreeAsync(dw, st);
+    if (dout) cudaFreeAsync(dout, st);
+    return rc;
+}
+
+int gs_lscv_host(const void *pts, int64_t N, int D, int dtype, const float *weights, const double *h, int nh,
+                 double eps, double *score, double *score_err, const gs_opts *opts, void *stream,
+                 gs_stats *stats) {
+    g_err[0] = 0;
+    if (!pts || !weights) {
+        set_error("gs_lscv_host: NULL array argument");
+        return GS_ERR_ARG;
+    }
+    if (N < 2 || D < 1 || D > 32 || (dtype != GS_F32 && dtype != GS_F64)) {
+        set_error("gs_lscv_host: bad N, D or dtype");
+        return GS_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = dtype == GS_F64 ? sizeof(double) : sizeof(float);
+    void *dp = nullptr;
+    float *dw = nullptr;
+    int rc = GS_OK;
+    cudaError_t e = dev_malloc_async(&dp, (size_t)N * D * es, st);
+    if (e == cudaSuccess) e = dev_malloc_async((void **)&dw, (size_t)N * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pts, (size_t)N * D * es, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, weights, (size_t)N * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        rc = cuda_fail(e, "gs_lscv_host upload");
+    else
+        rc = gs_lscv(dp, N, D, dtype, dw, h, nh, eps, score, score_err, opts, stream, stats);
+    if (dp) cudaFreeAsync(dp, st);
+    if (dw) cudaFreeAsync(dw, st);
     return rc;
 }
 

@@ -347,8 +347,12 @@ int exhaustive_sum(const void *queries, int64_t M, const void *refs, const float
 // reference records -- in one fixed array in the library's device memory
 // instead of allocating it.  The caller still provides inputs and outputs.
 //
-// The array exists once per device that loads the library and stays resident
-// until the process exits.  Every call uses the same array, so calls whose GPU
+// The array exists once per device that uses it and stays resident until the
+// process exits (or the device is reset).  The CUDA runtime loads a library's
+// device code lazily, so the first call on a device is the one that maps the
+// array, and that step may allocate inside the driver; a caller that must
+// not allocate mid-run makes one warm-up call at start-up, before any stream
+// capture.  Every call uses the same array, so calls whose GPU
 // work overlaps (concurrent streams, several host threads) race on it and
 // must be serialised by the caller.  Each call resets the status word and
 // overwrites the records it reads, so nothing depends on what a previous call
@@ -359,25 +363,22 @@ constexpr size_t kNoAllocHeader = 256;               // status word (Ingest) at 
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-static void *g_noalloc_addr[64] = {nullptr};
-
-// Device address of g_noalloc_scratch for the current device.  The symbol's
-// name in host code is only a host-side stand-in, so the address is looked up
-// with cudaGetSymbolAddress once per device (with that device current) and
-// cached.
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol's name is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress, with the device current, and checked before it
+// goes to a kernel.  It is looked up on every call rather than cached: the
+// lookup is a host-side table read once the library's device code is loaded
+// on the device, and an address cached across cudaDeviceReset (which destroys
+// the array with the context) or written by several host threads at once
+// would be a hazard for nothing.
 static int noalloc_scratch(void **out) {
-    int dev = 0;
-    GS_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) {
-        set_error("device index %d out of range", dev);
+    void *p = nullptr;
+    GS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (!p) {
+        set_error("cudaGetSymbolAddress returned no address for the fixed scratch array");
         return GS_ERR_CUDA;
     }
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        GS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    *out = p;
     return GS_OK;
 }
 

@@ -108,6 +108,8 @@ SIGNATURES = {
                                                   ctypes.c_int, _VP, _VP]),
     "gs_lscv": (ctypes.c_int, [_VP, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                _VP, _VP, _VP, _VP, _VP]),
+    "gs_lscv_host": (ctypes.c_int, [_VP, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int,
+                                    ctypes.c_double, _VP, _VP, _VP, _VP, _VP]),
     "gs_mlp_forward": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP]),
     "gs_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
     "gs_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -173,6 +175,42 @@ def _dtype_code(t) -> int:
     raise TypeError("points must be float32 or float64, got %s" % t.dtype)
 
 
+def _check_sum_tensors(queries, refs, weights, nh, out=None):
+    """Refuse arguments whose sizes or element types disagree before any
+    pointer reaches the library (a mismatch there would make a kernel read
+    or write past the end of a buffer): 2-D contiguous point tensors of one
+    floating type and width D, weights (N,) float32, out (M, nh) float64 on
+    the same device.  The device check comes last, so the layout checks run
+    on CPU tensors too.  Raises ValueError."""
+    import torch
+    for name, t in (("queries", queries), ("refs", refs), ("weights", weights)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+    if queries.dim() != 2 or refs.dim() != 2:
+        raise ValueError("queries and refs must be 2-D (points x D)")
+    if queries.dtype not in (torch.float32, torch.float64):
+        raise ValueError("points must be float32 or float64, got %s" % queries.dtype)
+    if refs.dtype != queries.dtype:
+        raise ValueError("refs dtype %s differs from queries dtype %s" % (refs.dtype, queries.dtype))
+    if refs.shape[1] != queries.shape[1]:
+        raise ValueError("refs have D=%d columns, queries D=%d" % (refs.shape[1], queries.shape[1]))
+    if weights.dtype != torch.float32:
+        raise ValueError("weights must be float32, got %s" % weights.dtype)
+    if weights.dim() != 1 or weights.shape[0] != refs.shape[0]:
+        raise ValueError("weights must have shape (%d,), got %s" % (refs.shape[0], tuple(weights.shape)))
+    if not (queries.is_contiguous() and refs.is_contiguous() and weights.is_contiguous()):
+        raise ValueError("queries, refs and weights must be contiguous")
+    if out is not None:
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.float64:
+            raise ValueError("out must be a float64 tensor")
+        if tuple(out.shape) != (queries.shape[0], nh) or not out.is_contiguous():
+            raise ValueError("out must be contiguous with shape (%d, %d), got %s"
+                             % (queries.shape[0], nh, tuple(out.shape)))
+    devs = {queries.device, refs.device, weights.device} | ({out.device} if out is not None else set())
+    if len(devs) != 1 or not queries.is_cuda:
+        raise ValueError("queries, refs, weights and out must be CUDA tensors on one device")
+
+
 def _stream_ptr(stream):
     import torch
     if stream is None:
@@ -187,12 +225,10 @@ def gs_sum(queries, refs, weights, h, eps, out=None, opts: gs_opts | None = None
     tensor as queries and refs for the monochromatic problem.  Returns out
     (M x nh float64 CUDA tensor)."""
     import torch
-    assert queries.is_cuda and refs.is_cuda and weights.is_cuda
-    assert queries.is_contiguous() and refs.is_contiguous() and weights.is_contiguous()
-    assert weights.dtype == torch.float32
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    _check_sum_tensors(queries, refs, weights, hh.size, out)
     M, D = queries.shape
     N = refs.shape[0]
-    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
     if out is None:
         out = torch.empty((M, hh.size), dtype=torch.float64, device=queries.device)
     rc = load().gs_sum(_VP(queries.data_ptr()), M, _VP(refs.data_ptr()), _VP(weights.data_ptr()), N, D,
@@ -211,9 +247,10 @@ def gs_sum_trace(queries, refs, weights, h, eps, opts: gs_opts | None = None, st
     rperm) with trace an (n, 4) int32 CUDA tensor of (query node, reference
     node, bandwidth, action | order << 8 | iteration << 16)."""
     import torch
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    _check_sum_tensors(queries, refs, weights, hh.size)
     M, D = queries.shape
     N = refs.shape[0]
-    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
     dev = queries.device
     out = torch.empty((M, hh.size), dtype=torch.float64, device=dev)
     tr = torch.empty((trace_cap, 4), dtype=torch.int32, device=dev)
@@ -234,10 +271,10 @@ def gs_sum_exhaustive_noalloc(queries, refs, weights, h, out=None, stream=None, 
     """Exhaustive sums through the allocation-free entry point (its scratch is a
     fixed array inside the library); same tensors as gs_sum with eps = 0."""
     import torch
-    assert queries.is_cuda and refs.is_cuda and weights.is_cuda
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    _check_sum_tensors(queries, refs, weights, hh.size, out)
     M, D = queries.shape
     N = refs.shape[0]
-    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
     if out is None:
         out = torch.empty((M, hh.size), dtype=torch.float64, device=queries.device)
     rc = load().gs_sum_exhaustive_noalloc(_VP(queries.data_ptr()), M, _VP(refs.data_ptr()),
@@ -252,15 +289,36 @@ def gs_sum_exhaustive_noalloc(queries, refs, weights, h, out=None, stream=None, 
 def gs_lscv(points, weights, h, eps, opts: gs_opts | None = None, stream=None, stats: gs_stats | None = None):
     """LSCV scores (and their eps-implied error bounds) for every bandwidth in
     h, from a torch CUDA tensor of points (N x D) and float32 weights."""
-    assert points.is_cuda and weights.is_cuda and points.is_contiguous() and weights.is_contiguous()
-    N, D = points.shape
     hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    _check_sum_tensors(points, points, weights, hh.size)
+    N, D = points.shape
     score = np.empty(hh.size)
     err = np.empty(hh.size)
     _check(load().gs_lscv(_VP(points.data_ptr()), N, D, _dtype_code(points), _VP(weights.data_ptr()),
                           hh.ctypes.data, hh.size, float(eps), score.ctypes.data, err.ctypes.data,
                           ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream),
                           ctypes.byref(stats) if stats is not None else None))
+    return score, err
+
+
+def gs_lscv_host(points: np.ndarray, weights: np.ndarray, h, eps, opts: gs_opts | None = None, stream=None,
+                 stats: gs_stats | None = None):
+    """gs_lscv on host (numpy) arrays; the library copies the inputs in.
+    Returns (score, err) host arrays."""
+    p = np.ascontiguousarray(points)
+    if p.ndim != 2 or p.dtype not in (np.float32, np.float64):
+        raise ValueError("points must be a 2-D float32 or float64 array")
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    if w.shape != (p.shape[0],):
+        raise ValueError("weights must have shape (%d,)" % p.shape[0])
+    hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+    score = np.empty(hh.size)
+    err = np.empty(hh.size)
+    sp = None if stream is None else _stream_ptr(stream)
+    _check(load().gs_lscv_host(p.ctypes.data, p.shape[0], p.shape[1], GS_F64 if p.dtype == np.float64 else GS_F32,
+                               w.ctypes.data, hh.ctypes.data, hh.size, float(eps), score.ctypes.data,
+                               err.ctypes.data, ctypes.byref(opts) if opts is not None else None, sp,
+                               ctypes.byref(stats) if stats is not None else None))
     return score, err
 
 
@@ -375,6 +433,7 @@ def gs_sum_batched(problems, opts: gs_opts | None = None, nworkers: int = 0, str
     outs, keep = [], []
     for i, (q, r, w, h, eps) in enumerate(problems):
         hh = np.ascontiguousarray(np.atleast_1d(h), dtype=np.float64)
+        _check_sum_tensors(q, r, w, hh.size)
         keep.append(hh)
         out = torch.empty((q.shape[0], hh.size), dtype=torch.float64, device=q.device)
         outs.append(out)
@@ -392,6 +451,14 @@ class Tree:
     """A built kd-tree (gs_build_tree); freed with close() or when collected."""
 
     def __init__(self, points, weights=None, opts: gs_opts | None = None, stream=None):
+        if weights is not None:
+            _check_sum_tensors(points, points, weights, 1)
+        else:
+            import torch
+            ok = (isinstance(points, torch.Tensor) and points.dim() == 2 and points.is_contiguous()
+                  and points.dtype in (torch.float32, torch.float64) and points.is_cuda)
+            if not ok:
+                raise ValueError("points must be a contiguous 2-D float32/float64 CUDA tensor")
         self.M = points.shape[0]
         self.D = points.shape[1]
         self.device = points.device

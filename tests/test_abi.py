@@ -60,3 +60,53 @@ def test_argument_errors_need_no_gpu(lib):
     inf_h = np.array([np.inf])
     assert call(h=inf_h.ctypes.data) == gs.GS_ERR_ARG
     assert "outside" in gs.gs_last_error() or "bandwidth" in gs.gs_last_error()
+
+
+def _cpu_args(M=5, N=7, D=3, dt=None):
+    import torch
+    dt = dt or torch.float32
+    return torch.zeros(M, D, dtype=dt), torch.zeros(N, D, dtype=dt), torch.ones(N, dtype=torch.float32)
+
+
+MISMATCHES = [
+    ("refs dtype", lambda q, r, w, t: (q, r.to(t.float64), w, None), "refs dtype"),
+    ("refs width", lambda q, r, w, t: (q, t.zeros(r.shape[0], 4), w, None), "columns"),
+    ("weights dtype", lambda q, r, w, t: (q, r, w.to(t.float64), None), "weights must be float32"),
+    ("weights length", lambda q, r, w, t: (q, r, w[:-1], None), "weights must have shape"),
+    ("weights 2-D", lambda q, r, w, t: (q, r, w[:, None], None), "weights must have shape"),
+    ("points dtype", lambda q, r, w, t: (q.to(t.float16), r.to(t.float16), w, None), "float32 or float64"),
+    ("points 1-D", lambda q, r, w, t: (q.reshape(-1), r, w, None), "2-D"),
+    ("non-contiguous", lambda q, r, w, t: (t.zeros(3, 5).t(), r, w, None), "contiguous"),
+    ("out dtype", lambda q, r, w, t: (q, r, w, t.zeros(q.shape[0], 2, dtype=t.float32)), "out must be a float64"),
+    ("out rows", lambda q, r, w, t: (q, r, w, t.zeros(q.shape[0] - 1, 2, dtype=t.float64)), "shape"),
+    ("out columns", lambda q, r, w, t: (q, r, w, t.zeros(q.shape[0], 3, dtype=t.float64)), "shape"),
+]
+
+
+@pytest.mark.parametrize("case", MISMATCHES, ids=lambda c: c[0])
+def test_wrappers_refuse_mismatched_arguments(case):
+    """A dtype, width, length or output-shape mismatch is refused by the
+    binding itself, before a device pointer reaches the library (where it
+    would make a kernel read or write past a buffer's end)."""
+    import torch
+    from paper_1206_6857_gb300 import gs
+    _, make, msg = case
+    q, r, w, out = make(*_cpu_args(), torch)
+    with pytest.raises(ValueError, match=msg):
+        gs._check_sum_tensors(q, r, w, 2, out)
+    # every public wrapper runs the same check first
+    for call in (lambda: gs.gs_sum(q, r, w, [0.1, 0.2], 0.0, out=out),
+                 lambda: gs.gs_sum_exhaustive_noalloc(q, r, w, [0.1, 0.2], out=out)):
+        with pytest.raises(ValueError, match=msg):
+            call()
+
+
+def test_wrappers_refuse_host_tensors():
+    """Matching CPU tensors pass the layout checks and are then refused as
+    not being on a CUDA device."""
+    from paper_1206_6857_gb300 import gs
+    q, r, w = _cpu_args()
+    with pytest.raises(ValueError, match="CUDA"):
+        gs.gs_sum(q, r, w, [0.1], 1e-2)
+    with pytest.raises(ValueError, match="CUDA"):
+        gs.gs_sum_exhaustive_noalloc(q, r, w, [0.1])

@@ -1,0 +1,127 @@
+"""Full-size parity of the dual tree (the workloads at the sizes the
+benchmark runs).
+
+* Every result against the GPU exhaustive sum (itself checked against the
+  FP64 oracle to 1e-5 relative): with |G_ex - G| <= d G, d = 1e-5, a
+  dual-tree result within t = (eps - d) / (1 + d) of G_ex is within eps of
+  the exact G (Section 1's relative error, Theorem 2's guarantee).  At
+  eps = 1e-4 that margin is a tenth of eps, so there only the looser
+  consistency bound (eps + d) / (1 - d) is asserted against G_ex and the
+  strict bound against the oracle.
+* Against the FP64 oracle: the 1000 queries with the smallest exact sum per
+  bandwidth (chosen from the GPU exhaustive output; the relative guarantee is
+  hardest there) plus 1000 seeded queries, every bandwidth.
+* The number of results whose sum lies under the certification floor
+  2^-40 W (where the guarantee is absolute, eps 2^-40 W) is reported; for
+  monochromatic data it is zero (every query sees its own weight).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from helpers import rel_err
+from oracle import exhaustive as oracle_ex
+from workloads import synth
+
+pytestmark = pytest.mark.gpu
+DELTA = 1e-5          # the exhaustive kernel's tolerance against the oracle
+FLOOR_LOG2 = -40
+N_SMALL = 1000
+N_SEEDED = 1000
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+    from paper_1206_6857_gb300 import build, gs as _gs
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    _gs.load()
+    return _gs
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _record(name, d):
+    """Append the per-workload accuracy record to a JSON-lines file when
+    GS_ACCURACY_LOG names one (the measurement notes quote it)."""
+    path = os.environ.get("GS_ACCURACY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(dict(workload=name, **d)) + "\n")
+
+
+def _full_check(gs, wl, eps, hs, opts=None):
+    tq = _dev(wl.queries)
+    tr = tq if wl.mono else _dev(wl.refs)
+    tw = _dev(wl.weights)
+    st = gs.gs_stats()
+    dt = gs.gs_sum(tq, tr, tw, hs, eps, opts=opts, stats=st).cpu().numpy()
+    ex = gs.gs_sum(tq, tr, tw, hs, 0.0).cpu().numpy()
+    W = float(wl.weights.astype(np.float64).sum())
+    err = rel_err(dt, ex, W, FLOOR_LOG2)
+    under = int(np.sum(ex < 2.0 ** FLOOR_LOG2 * W))
+    strict = (eps - DELTA) / (1 + DELTA)
+    loose = (eps + DELTA) / (1 - DELTA)
+    worst = np.unravel_index(int(np.argmax(err)), err.shape)
+    info = dict(eps=eps, results=int(err.size), max_rel_err_vs_gpu_exhaustive=float(err.max()),
+                worst_query=int(worst[0]), worst_h=float(hs[worst[1]]), under_floor=under,
+                fp32_rel_bound=st.fp32_rel_bound, point_pairs_base=st.point_pairs_base)
+    assert err.max() <= (strict if eps >= 1e-3 else loose), info
+    return dt, ex, W, info
+
+
+def _oracle_check(wl, eps, hs, dt, ex, W, info):
+    """The FP64 oracle on the smallest-G queries of each bandwidth and on a
+    seeded sample (all bandwidths)."""
+    worst = 0.0
+    fp32 = 0.0
+    for j, h in enumerate(hs):
+        idx = np.sort(np.argsort(ex[:, j], kind="stable")[:N_SMALL])
+        exact = oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, [h])[:, 0]
+        worst = max(worst, float(rel_err(dt[idx, j], exact, W, FLOOR_LOG2).max()))
+        fp32 = max(fp32, float(rel_err(ex[idx, j], exact, W, FLOOR_LOG2).max()))
+    idx = np.sort(np.random.default_rng(11).choice(wl.M, min(N_SEEDED, wl.M), replace=False))
+    exact = oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, hs)
+    worst = max(worst, float(rel_err(dt[idx], exact, W, FLOOR_LOG2).max()))
+    fp32 = max(fp32, float(rel_err(ex[idx], exact, W, FLOOR_LOG2).max()))
+    info.update(max_rel_err_vs_oracle=worst, exhaustive_fp32_err_vs_oracle=fp32,
+                oracle_queries="%d smallest-G per h + %d seeded" % (N_SMALL, N_SEEDED))
+    _record(wl.name, info)
+    assert worst <= eps, info
+    # the exhaustive kernel's FP32 arithmetic: 1e-5 where the terms near the
+    # query dominate; isolated queries whose sum is made of far terms (large
+    # exponent arguments) are held to the FP32 charge the library derives
+    assert fp32 <= max(DELTA, info["fp32_rel_bound"]), info
+
+
+def test_config2_every_result_and_smallest_sums(gs):
+    """D=3, 1e6 points: all 16 sweep bandwidths and their sqrt(2) h LSCV
+    companions (3.2e7 results) against GPU exhaustive; the hard queries
+    against the oracle."""
+    wl = synth.config2()
+    hs = synth.lscv_bandwidths(wl.h)
+    dt, ex, W, info = _full_check(gs, wl, wl.eps, hs)
+    assert info["under_floor"] == 0
+    _oracle_check(wl, wl.eps, wl.h, dt[:, :wl.h.size], ex[:, :wl.h.size], W, info)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_config3_every_result_and_smallest_sums(gs, eps):
+    wl = synth.config3(eps=eps)
+    dt, ex, W, info = _full_check(gs, wl, eps, wl.h)
+    assert info["under_floor"] == 0
+    _oracle_check(wl, eps, wl.h, dt, ex, W, info)
+
+
+def test_config4_every_result_and_smallest_sums(gs):
+    """D=16 bichromatic, 2e6 references x 2e5 queries x 8 bandwidths."""
+    wl = synth.config4()
+    dt, ex, W, info = _full_check(gs, wl, wl.eps, wl.h)
+    _oracle_check(wl, wl.eps, wl.h, dt, ex, W, info)

@@ -78,3 +78,23 @@ def test_bandwidth_search_matches_the_oracle_search(gs):
     assert abs(s - exact_at_h) <= err * (1 + 1e-6)
     assert h == pytest.approx(ho, rel=1e-12) or exact_at_h <= so + 2 * err
     assert sum(len(hs) for hs, _ in hist) == 32
+
+
+def test_certified_search_brackets_the_exact_grid_minimiser(gs):
+    """With certification, the reported bracket of the last grid contains
+    the grid point where the oracle's exact score is smallest, and the
+    reported score is within its bound of the exact score."""
+    from paper_1206_6857_gb300 import lscv_search
+    x, _, w = synth.small_random(212, 4000, 3)
+    diam = synth.bbox_diagonal(x)
+    tx, tw = _dev(x), _dev(w)
+    h, s, err, hist, cert = lscv_search.minimize(tx, tw, 1e-2, 1e-3 * diam, diam, rounds=3, per_round=8,
+                                                 certify_steps=3)
+    hs_last = hist[-1][0]
+    exact = oracle_lscv.lscv(x, w, hs_last)
+    k_exact = int(np.argmin(exact))
+    assert abs(s - float(oracle_lscv.lscv(x, w, np.array([h]))[0])) <= err * (1 + 1e-6)
+    if cert["certified"]:
+        lo, hi = cert["bracket"]
+        assert lo <= hs_last[k_exact] <= hi
+        assert cert["eps"] <= 1e-2

@@ -48,3 +48,43 @@ def test_search_on_the_exact_lscv_score():
     step = math.log(grid[1] / grid[0])
     assert abs(math.log(h / g)) <= 2 * step
     assert s <= sg.min() + 1e-3 * abs(sg.min())
+
+
+def _noisy(h0, noise_scale, seed=0):
+    """Scores of a log-quadratic with a minimum at h0 plus deterministic
+    noise inside a bound proportional to eps (a stand-in for the library's
+    eps-implied score bounds)."""
+    rng = np.random.default_rng(seed)
+
+    def fn(hs, eps):
+        hs = np.asarray(hs)
+        exact = (np.log(hs) - math.log(h0)) ** 2
+        bound = np.full(hs.size, noise_scale * eps)
+        return exact + bound * rng.uniform(-1, 1, hs.size), bound
+    return fn
+
+
+def test_certify_brackets_the_exact_minimiser():
+    h0 = 0.0123
+    hs = np.geomspace(0.01, 0.016, 8)
+    fn = _noisy(h0, 1.0)
+    cert = lscv_search.certify(fn, hs, 1e-2, steps=4)
+    assert cert["certified"]
+    lo, hi = cert["bracket"]
+    assert lo <= h0 <= hi
+    # the scores separate only once eps is small: the bound shrank with it
+    assert cert["eps"] < 1e-2 and cert["bound"] == pytest.approx(1.0 * cert["eps"])
+
+
+def test_certify_reports_failure_when_bounds_never_separate():
+    hs = np.geomspace(0.5, 0.5001, 5)      # a flat stretch: neighbours differ by ~1e-8
+    cert = lscv_search.certify(_noisy(0.5, 1.0), hs, 1e-2, steps=1)
+    assert not cert["certified"] and cert["m"] is None
+
+
+def test_certify_edge_minimum_is_one_sided():
+    hs = np.geomspace(0.1, 1.0, 6)
+    fn = lambda h, e: (np.asarray(h) * 10.0, np.full(len(h), 1e-3))      # increasing: the lower edge
+    cert = lscv_search.certify(fn, hs, 1e-2)
+    assert cert["certified"] and cert["k"] == 0 and cert["m"] == 1
+    assert cert["bracket"] == [pytest.approx(0.1), pytest.approx(hs[1])]
