@@ -91,6 +91,9 @@ typedef struct gs_opts {
                                by the dual tree; 1e6 points x 16 (1.6e13) take 2.1 s and
                                1.1 s.  In higher D the crossover is later still.        */
 #define GS_SMALL_WORK 549755813888.0
+#define GS_FLAG_NO_TC 4     /* 9 <= D <= 16: no tensor-core base case (every leaf pair summed
+                               by the direct FP32 kernel; the FP32 charge drops its extra
+                               tensor-core term)                                         */
 
 /* Default cost weights: a series action runs in FP64 on the GPU while a
  * direct (base-case) term is an FP32 exponential, so on GB300 one unit of
@@ -130,7 +133,8 @@ typedef struct gs_stats {
     double  ms_total;        /* device time of the whole call (CUDA events)             */
     double  ms_phase[GS_NPHASE]; /* device time per GS_PH_* phase                       */
     double  ms_series[3];     /* device time of the DH, DL and H2L kernels (within GS_PH_SERIES) */
-    double  reserved[1];
+    int64_t point_pairs_tc;  /* of point_pairs_base, those summed by the tensor-core base
+                                case (9 <= D <= 16)                                     */
 } gs_stats;
 
 /* Library version string (static storage). */
@@ -472,6 +476,21 @@ void gs_debug_fail_alloc(long long n);
  * Returns GS_OK, GS_ERR_ARG (NULL pointer) or GS_ERR_CUDA.
  */
 int gs_probe_rates(double *ex2_per_sm_clk, double *ffma_per_sm_clk, void *stream);
+
+/*
+ * gs_tc_dot_check -- diagnostic of the tensor-core cross term of the base case
+ * (9 <= D <= 16): U (HOST, 128 x 16 int32) and V (HOST, N x 16 int32), every
+ * entry in [-2^29, 2^29], are split into three base-2^10 digits each
+ * (U = U2 2^20 + U1 2^10 + U0, U0 and U1 in [-512, 511]) and the tensor
+ * cores form, in FP32 accumulators,
+ *     P[0] = U2 V2^T,  P[1] = U2 V1^T + U1 V2^T,  P[2] = U2 V0^T + U1 V1^T + U0 V2^T
+ * (128 x N each), written to P (HOST, 3 x 128 x N floats, row-major).  Each
+ * entry is an integer below 2^24 in magnitude, so the result is exact; the
+ * check compares it with integer arithmetic.  N is a multiple of 16 in
+ * [16, 128].  Returns GS_OK, GS_ERR_ARG, GS_ERR_TIMEOUT (the completion wait
+ * gave up) or GS_ERR_CUDA; synchronises the stream.
+ */
+int gs_tc_dot_check(const int32_t *U, const int32_t *V, int N, float *P, void *stream);
 
 /*
  * gs_trim_memory -- device scratch of every call comes from a stream-ordered

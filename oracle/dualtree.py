@@ -208,6 +208,7 @@ class Tree:
         return (1 << (self.depth + 1)) - 1
     W32d: np.ndarray = None   # W rounded down / up to FP32
     W32u: np.ndarray = None
+    f32: bool = True          # the points are FP32 (not FP64)
 
     def __post_init__(self):
         self.W32d = f32_down(self.W)
@@ -258,8 +259,10 @@ def build_tree(x: np.ndarray, w: np.ndarray, L: int) -> Tree:
         W[node] = W[2 * node + 1] + W[2 * node + 2]
     center = (lo + hi) * 0.5
     rad = ((hi - lo) * 0.5).max(axis=1)
-    return Tree(n, D, depth, perm, lo, hi, f32_down(lo), f32_up(hi), center, rad, W, wmin, begin, end,
-                split_dim)
+    t = Tree(n, D, depth, perm, lo, hi, f32_down(lo), f32_up(hi), center, rad, W, wmin, begin, end,
+             split_dim)
+    t.f32 = x.dtype == np.float32
+    return t
 
 
 def f32_down(x):
@@ -289,7 +292,27 @@ def plimit_for(D: int) -> int:
     return DEFAULT_PLIMIT.get(D, 1)
 
 
-def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int, run: int) -> float:
+TC_GUARD_LOG2 = -11     # absolute exponent error the tensor-core base case may add (log2 units)
+
+
+def tc_enabled(D: int, f32: bool, nh: int, max_q_leaf: int, max_r_leaf: int, no_tc: bool = False) -> bool:
+    """Whether the base case of a call may take its cross term from the
+    tensor cores: 9 <= D <= 16, FP32 points, at most 32 bandwidths, leaves of
+    at most 128 points."""
+    return (not no_tc) and 9 <= D <= 16 and f32 and nh <= 32 and max_q_leaf <= 128 and max_r_leaf <= 128
+
+
+def tc_rho() -> float:
+    """Extra charge when the tensor-core base case is enabled: the expanded
+    squared distance adds two roundings of the exponent argument (over
+    exponents down to 2^-64: ln2 * 64 * 2u) and, on the leaf pairs its guard
+    admits, an absolute exponent error of at most 2^TC_GUARD_LOG2 (ln2 times
+    that)."""
+    u = 2.0 ** -24
+    return 0.6931471805599453 * (64.0 * 2.0 * u + 2.0 ** TC_GUARD_LOG2)
+
+
+def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int, run: int, tc: bool = False) -> float:
     """A-priori relative error of the FP32 base case: per-term argument
     rounding for exponents down to 2^-64 (ln2 * 64 * (D+4) u), the ex2.approx
     bound 2^-21, FP32 recursive summation of positive terms over a run of at
@@ -301,6 +324,8 @@ def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int, run: int) 
     rho = rho + 2.0 ** -21
     rho = rho + float(run + 1) * u
     rho = rho + 2.0 ** (-63 - floor_log2) * ((N * w_max) / W)
+    if tc:
+        rho = rho + tc_rho()
     return rho
 
 
@@ -387,7 +412,7 @@ def _argmax_certified(scores, certified):
 
 def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None = None,
              selector: int = SEL_RULE, tokens: bool = True, floor_log2: int = -40,
-             w_max: float = None, cost_weight=COST_WEIGHTS, mlp_params=None):
+             w_max: float = None, cost_weight=COST_WEIGHTS, mlp_params=None, no_tc: bool = False):
     """Run the level-synchronous traversal; returns a Traversal whose iters[t]
     holds the frontier (q, r, j) and the decision (method, p, E) of every
     pair in the exact order the GPU processes them.
@@ -409,7 +434,9 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
     W = float(rt.W[0])
     floorW = W * 2.0 ** floor_log2
     run = -(-rt.n // (1 << rt.depth))          # largest reference leaf
-    rho = fp32_rho(D, rt.n, w_max, W, floor_log2, run)
+    qrun = -(-qt.n // (1 << qt.depth))         # largest query leaf
+    tc = tc_enabled(D, qt.f32, nh, qrun, run, no_tc)
+    rho = fp32_rho(D, rt.n, w_max, W, floor_log2, run, tc)
     eps_t = eps - rho
     F, BT = bound_factor_table(D, P)
     Dpow = [1.0]

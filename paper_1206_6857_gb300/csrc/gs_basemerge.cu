@@ -23,11 +23,6 @@
 
 namespace gs {
 
-struct MergedEntry {
-    int32_t r;       // reference leaf (heap number)
-    uint32_t mask;   // bandwidths j with bit j set
-};
-
 struct BitMap {
     int8_t rank[64];    // bandwidth j -> mask bit (bandwidths ranked by ascending h)
 };
@@ -436,13 +431,16 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     }
     uint32_t *mask = nullptr;
     long long *off = nullptr;
-    MergedEntry *ent = nullptr;
+    MergedEntry *ent = nullptr, *ent_dir = nullptr;
+    long long *off_dir = nullptr;
     float *rec2 = nullptr;
     // a failed call frees what this phase holds, so the pool gets it back
     auto release = [&]() {
         if (mask) cudaFreeAsync(mask, st);
         if (off) cudaFreeAsync(off, st);
         if (ent) cudaFreeAsync(ent, st);
+        if (ent_dir) cudaFreeAsync(ent_dir, st);
+        if (off_dir) cudaFreeAsync(off_dir, st);
         if (rec2) cudaFreeAsync(rec2, st);
     };
 #define GS_TRY_M(call)                        \
@@ -505,6 +503,23 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         bp.Gq = Gq;
         bp.ing = in.ing;
         bp.evals = fb.evals;
+        // 9 <= D <= 16: the leaf pairs that pass the tensor-core error guard are
+        // summed there; the direct kernel below takes the rest
+        const MergedEntry *ent_run = ent;
+        const long long *off_run = off;
+        if (tc_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth, in.rt->n, in.rt->depth, in.nh)) {
+            double h_by_bit[32];
+            for (int b = 0; b < 32; ++b) h_by_bit[b] = b < in.nh ? in.h[order[b]] : 1.0;
+            rc = run_basecase_tc(in, ent, off, lq, total, bp.negc, bp.jcol, h_by_bit, Gq, &ent_dir, &off_dir,
+                                 fb.evals, cx);
+            if (rc) {
+                release();
+                cx.phase(GS_PH_OTHER);
+                return rc;
+            }
+            ent_run = ent_dir;
+            off_run = off_dir;
+        }
         int qpl, lmax;
         merged_shape(in, qpl, lmax);
         const bool anch = in.qt->dtype == GS_F64;
@@ -517,18 +532,18 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
             bp.rrec2 = rec2;
         }
         switch (DP) {
-            case 1: rc = launch_merged_dp<1>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 2: rc = launch_merged_dp<2>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 3: rc = launch_merged_dp<3>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 4: rc = launch_merged_dp<4>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 5: rc = launch_merged_dp<5>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 6: rc = launch_merged_dp<6>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 7: rc = launch_merged_dp<7>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 8: rc = launch_merged_dp<8>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 12: rc = launch_merged_dp<12>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 16: rc = launch_merged_dp<16>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            case 24: rc = launch_merged_dp<24>(qpl, anch, bp, ent, off, lq, lmax, st); break;
-            default: rc = launch_merged_dp<32>(qpl, anch, bp, ent, off, lq, lmax, st); break;
+            case 1: rc = launch_merged_dp<1>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 2: rc = launch_merged_dp<2>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 3: rc = launch_merged_dp<3>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 4: rc = launch_merged_dp<4>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 5: rc = launch_merged_dp<5>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 6: rc = launch_merged_dp<6>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 7: rc = launch_merged_dp<7>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 8: rc = launch_merged_dp<8>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 12: rc = launch_merged_dp<12>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 16: rc = launch_merged_dp<16>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 24: rc = launch_merged_dp<24>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            default: rc = launch_merged_dp<32>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
         }
         cx.launches += 1;
         cx.launches_base += 1;

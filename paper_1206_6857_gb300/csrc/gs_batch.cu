@@ -77,7 +77,7 @@ extern "C" int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts 
                 gs_stats &a = wstats[w];
                 a.pairs_fd += ps.pairs_fd; a.pairs_dh += ps.pairs_dh; a.pairs_dl += ps.pairs_dl;
                 a.pairs_h2l += ps.pairs_h2l; a.pairs_base += ps.pairs_base; a.pairs_split += ps.pairs_split;
-                a.point_pairs_base += ps.point_pairs_base; a.launches += ps.launches;
+                a.point_pairs_base += ps.point_pairs_base; a.point_pairs_tc += ps.point_pairs_tc; a.launches += ps.launches;
                 a.launches_base += ps.launches_base;
                 if (ps.levels > a.levels) a.levels = ps.levels;
                 a.retries += ps.retries;
@@ -112,7 +112,7 @@ extern "C" int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts 
             const gs_stats &a = wstats[w];
             stats->pairs_fd += a.pairs_fd; stats->pairs_dh += a.pairs_dh; stats->pairs_dl += a.pairs_dl;
             stats->pairs_h2l += a.pairs_h2l; stats->pairs_base += a.pairs_base; stats->pairs_split += a.pairs_split;
-            stats->point_pairs_base += a.point_pairs_base; stats->launches += a.launches;
+            stats->point_pairs_base += a.point_pairs_base; stats->point_pairs_tc += a.point_pairs_tc; stats->launches += a.launches;
             stats->launches_base += a.launches_base;
             if (a.levels > stats->levels) stats->levels = a.levels;
             stats->retries += a.retries;

@@ -111,8 +111,9 @@ static int alloc_bufs(FrontierBufs &fb, int64_t nodesQ, int nh, const double *h,
     }
     // pageable source: the runtime stages hc before returning, so it may go out of scope
     GS_CUDA_TRY(cudaMemcpyAsync(fb.inv_2h2, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
-    GS_ALLOC(fb.evals, sizeof(unsigned long long));
-    GS_CUDA_TRY(cudaMemsetAsync(fb.evals, 0, sizeof(unsigned long long), st));
+    // evals[0]: every base-case term; evals[1]: those of the tensor-core kernel
+    GS_ALLOC(fb.evals, 2 * sizeof(unsigned long long));
+    GS_CUDA_TRY(cudaMemsetAsync(fb.evals, 0, 2 * sizeof(unsigned long long), st));
     return GS_OK;
 }
 
@@ -196,6 +197,7 @@ int dualtree_run(const TreeDev &qt_in, const TreeDev &rt_in, bool mono, const fl
     in.eps = eps;
 
     for (int k = 0; k < 4; ++k) in.cost_w[k] = o.cost_weight[k];
+    in.flags = o.flags;
     in.mlp = o.selector_params;
     in.log = log;
     const int64_t lq = 1ll << qt.depth;
@@ -246,8 +248,9 @@ int dualtree_run(const TreeDev &qt_in, const TreeDev &rt_in, bool mono, const fl
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(&hfs, fb.fs, sizeof(hfs), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hing, ing, sizeof(hing), cudaMemcpyDeviceToHost, st);
-        unsigned long long hev = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&hev, fb.evals, sizeof(hev), cudaMemcpyDeviceToHost, st);
+        unsigned long long hev2[2] = {0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hev2, fb.evals, sizeof(hev2), cudaMemcpyDeviceToHost, st);
+        const unsigned long long hev = hev2[0];
         cx.end();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "dual-tree");
@@ -260,6 +263,7 @@ int dualtree_run(const TreeDev &qt_in, const TreeDev &rt_in, bool mono, const fl
             s->pairs_base = (int64_t)hfs.method_count[M_BASE];
             s->pairs_split = (int64_t)hfs.method_count[M_SPLIT];
             s->point_pairs_base = (int64_t)hev;
+            s->point_pairs_tc = (int64_t)hev2[1];
             s->levels = (qt.depth > rt.depth ? qt.depth : rt.depth) + 1;
             s->retries = 0;
             s->fp32_rel_bound = hfs.rho;

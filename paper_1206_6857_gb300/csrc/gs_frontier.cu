@@ -764,7 +764,7 @@ __global__ void k_front_advance(FrontierState *fs, int t) {
 // bandwidth; eps for the traversal after the FP32 base-case charge.
 __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int nh, const double *rW,
                              const double *rlo, const double *rhi, Ingest *ing, int64_t N, int D, int floor_log2,
-                             double eps, int64_t run) {
+                             double eps, int64_t run, double extra_rho) {
     const int j = threadIdx.x;
     if (j < nh) {
         Group g;
@@ -780,6 +780,7 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
         rho = rho + 4.76837158203125e-07;          // 2^-21
         rho = rho + (double)(run + 1) * u;      // FP32 sums over one reference leaf, then compensated
         rho = rho + ldexp(1.0, -63 - floor_log2) * (((double)N * wmax) / W);
+        rho = rho + extra_rho;                   // the tensor-core base case's charge, when enabled
         fs->rho = rho;
         fs->eps_t = eps - rho;
         fs->Wtot = W;
@@ -887,7 +888,11 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
 
     k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, in.rt->lo, in.rt->hi,
                                    (Ingest *)in.ing, in.rt->n, in.D, in.floor_log2, in.eps,
-                                   (in.rt->n + (1ll << in.rt->depth) - 1) >> in.rt->depth);
+                                   (in.rt->n + (1ll << in.rt->depth) - 1) >> in.rt->depth,
+                                   tc_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth, in.rt->n,
+                                                   in.rt->depth, in.nh)
+                                       ? tc_charge()
+                                       : 0.0);
     cx.launches += 1;
     if ((rc = cx.check("k_front_init"))) return rc;
     const int T = in.qt->depth > in.rt->depth ? in.qt->depth : in.rt->depth;

@@ -170,6 +170,13 @@ struct PairLog {
 };
 enum : int { LOG_FD = 0, LOG_BASE = 1, LOG_SPLIT = 2 };
 
+// One merged base-case entry: a reference leaf (heap number) and the mask of
+// the bandwidths (bits ranked by ascending h) its query leaf needs.
+struct MergedEntry {
+    int32_t r;
+    uint32_t mask;
+};
+
 struct TraversalIn {
     const TreeDev *qt = nullptr, *rt = nullptr;
     const Ingest *ing = nullptr;
@@ -178,6 +185,7 @@ struct TraversalIn {
     int D = 0, nh = 0, P = 0, selector = 0, tokens = 1, mono = 0, floor_log2 = -40;
     double eps = 0.0;
     double cost_w[4] = {GS_COST_DH, GS_COST_DL, GS_COST_H2L, GS_COST_DIRECT};
+    int flags = 0;                // gs_opts.flags
     const float *mlp = nullptr;   // selector network (GS_SEL_MLP)
     PairLog *log = nullptr;       // log every pair (FD-only decisions)
 };
@@ -219,6 +227,17 @@ bool merged_base_possible(const TraversalIn &in);
 // In-place exclusive prefix sum of n int64 values; *total (device) receives the sum.
 int scan_i64(long long *v, int64_t n, long long *total, CallCtx &cx);
 int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, CallCtx &cx);
+// Tensor-core base case (9 <= D <= 16, FP32 points, leaves of at most 128
+// points): whether a call takes it, and the extra FP32 charge it needs.
+bool tc_base_enabled(int D, int dtype, int flags, int64_t qn, int q_depth, int64_t rn, int r_depth, int nh);
+double tc_charge();
+// Splits the merged entries (ent, off over lq query-leaf rows) between the
+// tensor-core kernel (entries whose pair passes the error guard) and the
+// direct kernel: runs the former and leaves the latter in (ent_dir, off_dir),
+// allocated on the stream (the caller frees them).
+int run_basecase_tc(const TraversalIn &in, const MergedEntry *ent, const long long *off, int64_t lq,
+                    long long total, const float *negc, const int *jcol, const double *h_by_bit, double *Gq,
+                    MergedEntry **ent_dir, long long **off_dir, unsigned long long *evals, CallCtx &cx);
 int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTables *tb, double *Gq,
                          double *B, int32_t *pL, double *out, CallCtx &cx);
 

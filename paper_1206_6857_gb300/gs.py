@@ -36,6 +36,7 @@ GS_SEL_EXHAUSTIVE = 3
 GS_COST_DEFAULT = (32.0, 32.0, 32.0, 1.0)     # c_DH, c_DL, c_H2L, c_Direct weights
 GS_FLAG_NO_MERGE = 1
 GS_FLAG_SMALL_EXHAUSTIVE = 2
+GS_FLAG_NO_TC = 4
 GS_SMALL_WORK = 549755813888.0
 
 GS_MLP_NIN = 12
@@ -72,7 +73,7 @@ class gs_stats(ctypes.Structure):
                 ("retries", ctypes.c_int32), ("fp32_rel_bound", ctypes.c_double),
                 ("eps_traversal", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_phase", ctypes.c_double * GS_NPHASE), ("ms_series", ctypes.c_double * 3),
-                ("reserved", ctypes.c_double * 1)]
+                ("point_pairs_tc", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "ms_phase", "ms_series")}
@@ -102,6 +103,7 @@ SIGNATURES = {
     "gs_sum_host": (ctypes.c_int, _SUM_ARGS),
     "gs_probe_rates": (ctypes.c_int, [_VP, _VP, _VP]),
     "gs_trim_memory": (ctypes.c_int, [ctypes.c_size_t]),
+    "gs_tc_dot_check": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
     "gs_pool_bytes": (ctypes.c_int, [_VP, _VP]),
     "gs_sum_trace": (ctypes.c_int, _SUM_ARGS + [_VP, _I64, _VP, _VP, _VP]),
     "gs_sum_exhaustive_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _VP, _I64, ctypes.c_int, ctypes.c_int, _VP,
@@ -350,6 +352,19 @@ def gs_probe_rates(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().gs_probe_rates(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
     return a.value, b.value
+
+
+def gs_tc_dot_check(U: np.ndarray, V: np.ndarray, stream=None):
+    """Raw tensor-core accumulators (3 x 128 x N float32) of the base case's
+    fixed-point cross term for integer matrices U (128 x 16) and V (N x 16)."""
+    U = np.ascontiguousarray(U, dtype=np.int32)
+    V = np.ascontiguousarray(V, dtype=np.int32)
+    if U.shape != (128, 16) or V.ndim != 2 or V.shape[1] != 16:
+        raise ValueError("U must be 128 x 16 and V N x 16")
+    N = V.shape[0]
+    P = np.empty((3, 128, N), dtype=np.float32)
+    _check(load().gs_tc_dot_check(U.ctypes.data, V.ctypes.data, N, P.ctypes.data, _stream_ptr(stream)))
+    return P
 
 
 def gs_trim_memory(keep_bytes=0):

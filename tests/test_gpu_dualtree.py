@@ -74,6 +74,7 @@ CASES = [
     (9, 2000, 2, None, 1e-3, 32, 0, True, 3, [0.05, 0.2], PAPER),
     (10, 6000, 2, None, 1e-2, 32, 0, True, 0, [0.02, 0.1, 0.4], DEF),
     (11, 4000, 3, None, 1e-4, 32, 0, True, 0, [0.05, 0.3], DEF),
+    (12, 1500, 12, 1000, 1e-2, 16, 0, True, 0, [0.3, 1.0], DEF),    # tensor-core base case and its charge
 ]
 
 
