@@ -50,7 +50,7 @@
 namespace gs {
 
 constexpr int kTcRows = 128;               // M of the MMA: query rows (leaf size <= 128)
-constexpr int kTcChunk = 32;               // N of the MMA: reference columns per group
+constexpr int kTcChunk = 32;               // N of the MMA: reference columns per chunk
 constexpr int kTcWG = 4;                   // warpgroups per CTA
 constexpr int kTcDigitBytes = kTcRows * 32;    // one digit tile: 128 rows x 16 FP16
 constexpr int kTcLeafBytes = 3 * kTcDigitBytes;  // three digits of one leaf
@@ -283,11 +283,12 @@ struct TcSmem {
     static constexpr int kRecBytes = kTcRows * kTcRecFloats * 4;          // 10 KB of records per leaf
     static constexpr int A = 0;                                          // query digit tiles
     static constexpr int QREC = A + kTcLeafBytes;                        // query records
-    static constexpr int STAGE = QREC + kRecBytes;                       // per warpgroup: 2 x (tiles + records)
-    static constexpr int STAGE_ONE = kTcLeafBytes + kRecBytes;
+    static constexpr int CQ = QREC + kRecBytes;                          // query leaf centre (16 floats)
+    static constexpr int STAGE = CQ + 64;                                // per warpgroup: 2 x (tiles, records, centre)
+    static constexpr int STAGE_ONE = kTcLeafBytes + kRecBytes + 64;
     static constexpr int BL = STAGE + kTcWG * 2 * STAGE_ONE;             // per warpgroup: (beta, lw) x 128
     static constexpr int MISC = BL + kTcWG * kTcRows * 8;                 // mbarriers, TMEM address, flags
-    static constexpr int TOTAL = MISC + 128;
+    static constexpr int TOTAL = MISC + 192;
     // the cross-warpgroup reduction at the end of a query leaf reuses STAGE
     static constexpr int RED = STAGE;
 };
@@ -321,13 +322,13 @@ __device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
     return r;
 }
 
-// 16 reference columns for NJ bandwidths: gamma from the three accumulators,
-// the squared distance, then one exponential per bandwidth; two columns per
-// packed f32x2 operation.  bl holds (beta, lw) of the 16 columns.
+// One chunk of 16 reference columns for NJ bandwidths: gamma from the three
+// accumulators, the squared distance, then one exponential per bandwidth;
+// two columns per packed f32x2 operation.  bl holds (beta, lw) per column.
 template <int NJ>
 __device__ __forceinline__ void tc_cols16(const float (&a4)[16], const float (&a3)[16], const float (&a2)[16],
-                                          const float *bl, f2_t alpha2, f2_t m2s2, const f2_t (&c2)[kTcBlk],
-                                          f2_t (&part)[kTcBlk]) {
+                                          const float *bl, f2_t alpha2, f2_t m2s2, const f2_t (&c2)[NJ],
+                                          f2_t (&part)[NJ]) {
     const f2_t k1024 = pk2(1024.f, 1024.f);
 #pragma unroll
     for (int i = 0; i < 16; i += 2) {
@@ -346,17 +347,91 @@ __device__ __forceinline__ void tc_cols16(const float (&a4)[16], const float (&a
     }
 }
 
+// Everything a warpgroup needs to run the chunks of one entry.
+struct TcEntryCtx {
+    uint32_t tmem_lane;     // this thread's lane, the warpgroup's first column
+    uint32_t tmem_mma;      // lane 0, the warpgroup's first column
+    uint32_t a0, b0;        // shared addresses of the query and reference digit tiles
+    uint32_t idesc;
+    uint64_t *full;         // the MMAs of the current chunk completed (1 arrival)
+    volatile int *abort;    // the warpgroup's give-up flag
+    int bar_id;
+    bool leader;            // the thread that issues the MMAs
+    uint32_t fparity;       // parity of the next completion phase
+};
+
+// The warpgroup's accumulators: columns g * 32, g = 0, 1, 2 for P4, P3, P2 of
+// one 32-column chunk.  Issued once every lane has read the previous chunk.
+__device__ __forceinline__ void tc_issue_chunk(const TcEntryCtx &x, int c) {
+    tc::fence_after_sync();
+    const uint32_t bb = x.b0 + (uint32_t)(c * kTcChunk * 32);
+    const uint32_t d = x.tmem_mma;
+    auto A = [&](int g) { return tc::smem_desc(x.a0 + g * kTcDigitBytes, 128, 256); };
+    auto B = [&](int g) { return tc::smem_desc(bb + g * kTcDigitBytes, 128, 256); };
+    // digit g of a tile at + g * kTcDigitBytes: 0 = U2, 1 = U1, 2 = U0
+    tc::mma_f16(d + 0 * kTcChunk, A(0), B(0), x.idesc, 0);   // P4 = U2 V2
+    tc::mma_f16(d + 1 * kTcChunk, A(0), B(1), x.idesc, 0);   // P3 = U2 V1
+    tc::mma_f16(d + 1 * kTcChunk, A(1), B(0), x.idesc, 1);   //    + U1 V2
+    tc::mma_f16(d + 2 * kTcChunk, A(0), B(2), x.idesc, 0);   // P2 = U2 V0
+    tc::mma_f16(d + 2 * kTcChunk, A(1), B(1), x.idesc, 1);   //    + U1 V1
+    tc::mma_f16(d + 2 * kTcChunk, A(2), B(0), x.idesc, 1);   //    + U0 V2
+    tc::mma_commit(x.full);
+}
+
+// The chunks of one entry.  Chunk 0 was issued by the caller (its MMAs ran
+// while beta and alpha were formed); chunk c + 1 is issued as soon as every
+// lane has read chunk c.  The NJ bandwidths are the lowest set bits of m;
+// their per-entry sums go into the compensated per-slot sums.
 template <int NJ>
-__device__ __forceinline__ void tc_chunk_epilogue(uint32_t taddr, const float *bl, f2_t alpha2, f2_t m2s2,
-                                                  const f2_t (&c2)[kTcBlk], f2_t (&part)[kTcBlk]) {
+__device__ __forceinline__ void tc_entry(TcEntryCtx &x, int nchunks, const float *bl, f2_t alpha2, f2_t m2s2,
+                                         uint32_t m, const float *negc, float (&ksum)[kTcBlk],
+                                         float (&kcmp)[kTcBlk]) {
+    f2_t c2[NJ], part[NJ];
+    {
+        uint32_t mm = m;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        float a4[16], a3[16], a2[16];
-        tc::tmem_ld16(taddr + 0 * kTcChunk + 16 * half, a4);
-        tc::tmem_ld16(taddr + 1 * kTcChunk + 16 * half, a3);
-        tc::tmem_ld16(taddr + 2 * kTcChunk + 16 * half, a2);
-        tc::tmem_wait_ld();
-        tc_cols16<NJ>(a4, a3, a2, bl + 32 * half, alpha2, m2s2, c2, part);
+        for (int k = 0; k < NJ; ++k) {
+            const float c = negc[__ffs(mm) - 1];
+            c2[k] = pk2(c, c);
+            part[k] = 0ull;
+            mm &= mm - 1;
+        }
+    }
+    for (int c = 0; c < nchunks; ++c) {
+        if (c > 0 && x.leader && !*x.abort) tc_issue_chunk(x, c);
+        if (!*x.abort && !tc::mbar_wait_bounded(x.full, x.fparity, kTcWaitPolls)) *x.abort = 1;
+        x.fparity ^= 1u;
+        tc::fence_after_sync();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float a4[16], a3[16], a2[16];
+            const uint32_t ta = x.tmem_lane + (uint32_t)(16 * half);
+            tc::tmem_ld16(ta + 0 * kTcChunk, a4);
+            tc::tmem_ld16(ta + 1 * kTcChunk, a3);
+            tc::tmem_ld16(ta + 2 * kTcChunk, a2);
+            tc::tmem_wait_ld();
+            tc_cols16<NJ>(a4, a3, a2, bl + 2 * (kTcChunk * c + 16 * half), alpha2, m2s2, c2, part);
+        }
+        tc::fence_before_sync();
+        tc::bar_sync(x.bar_id, 128);   // every lane has read the accumulators
+    }
+    // FP32 sum over the reference leaf, then compensated across leaves
+    uint32_t mm = m;
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) {
+        const int slot = __ffs(mm) - 1;
+        mm &= mm - 1;
+        float lo, hi;
+        upk2(part[k], lo, hi);
+        const float v = lo + hi;
+#pragma unroll
+        for (int kk = 0; kk < kTcBlk; ++kk)
+            if (kk == slot) {
+                const float y = v - kcmp[kk];
+                const float s2 = ksum[kk] + y;
+                kcmp[kk] = (s2 - ksum[kk]) - y;
+                ksum[kk] = s2;
+            }
     }
 }
 
@@ -366,16 +441,16 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
     const int tid = threadIdx.x;
     const int wg = tid >> 7;          // warpgroup
     const int t = tid & 127;          // query row (tensor-memory lane) of this thread
-    const int bar_id = 1 + wg;        // named barrier of the warpgroup
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + TcSmem::MISC);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + TcSmem::MISC + 64);
-    int *s_leaf = reinterpret_cast<int *>(sm + TcSmem::MISC + 72);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + TcSmem::MISC);     // one per warpgroup
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + TcSmem::MISC + 128);
+    int *s_leaf = reinterpret_cast<int *>(sm + TcSmem::MISC + 136);
     // a warpgroup whose completion wait gave up sets its own flag (read by its
     // threads after its own barrier); the CTA reads all four after __syncthreads
-    volatile int *s_abort = reinterpret_cast<volatile int *>(sm + TcSmem::MISC + 80);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(sm + TcSmem::MISC + 144);
     auto any_abort = [&]() { return (s_abort[0] | s_abort[1] | s_abort[2] | s_abort[3]) != 0; };
     unsigned char *sA = sm + TcSmem::A;
     const float *sQrec = reinterpret_cast<const float *>(sm + TcSmem::QREC);
+    float *sCq = reinterpret_cast<float *>(sm + TcSmem::CQ);
     float *bl = reinterpret_cast<float *>(sm + TcSmem::BL) + wg * kTcRows * 2;
 
     if (tid < 32) {
@@ -383,21 +458,25 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int w = 0; w < kTcWG; ++w) {
-            tc::mbar_init(&mbar[w], 1);
-            s_abort[w] = 0;
-        }
+        for (int w = 0; w < kTcWG; ++w) tc::mbar_init(&mbar[w], 1);
+        for (int w = 0; w < kTcWG; ++w) s_abort[w] = 0;
         tc::mbar_fence_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tmem_slot + (uint32_t)(wg * 128) + ((uint32_t)((t >> 5) * 32) << 16);
-    const uint32_t tmem_mma = *tmem_slot + (uint32_t)(wg * 128);
-    const uint32_t idesc = tc::idesc_f16_f32(kTcRows, kTcChunk);
-    const int64_t qleaf0 = ((int64_t)1 << p.q_depth) - 1, rleaf0 = ((int64_t)1 << p.r_depth) - 1;
+    TcEntryCtx x;
+    x.tmem_mma = *tmem_slot + (uint32_t)(wg * 128);
+    x.tmem_lane = x.tmem_mma + ((uint32_t)((t >> 5) * 32) << 16);
+    x.a0 = tc::smem_u32(sA);
+    x.idesc = tc::idesc_f16_f32(kTcRows, kTcChunk);
+    x.full = mbar + wg;
+    x.fparity = 0;
+    x.abort = s_abort + wg;
+    x.bar_id = 1 + wg;
+    x.leader = t == 0;
+    const int64_t rleaf0 = ((int64_t)1 << p.r_depth) - 1;
     const double wmax = (double)__uint_as_float(p.ing->wmax_bits);
-    uint32_t phase = 0;
     unsigned long long evals = 0;
     const int nblk = (p.nh + kTcBlk - 1) / kTcBlk;
 
@@ -409,22 +488,21 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
         if (i >= lq || any_abort()) break;
         const long long e0 = off[i], e1 = off[i + 1];
         if (e0 == e1) continue;
-        (void)qleaf0;
         const int64_t qb = level_begin(p.qn, p.q_depth, i), qe = level_begin(p.qn, p.q_depth, i + 1);
         const int nq = (int)(qe - qb);
-        // the query leaf: digit tiles and records
+        // the query leaf: digit tiles, records and centre
         {
             const unsigned char *src = p.qtiles + i * (int64_t)kTcLeafBytes;
             for (int v = tid; v < kTcLeafBytes / 16; v += blockDim.x) cp16(sA + 16 * v, src + 16 * v);
             const float *rs = p.qrec + qb * p.stride;
             for (int v = tid; v < nq * (p.stride / 4); v += blockDim.x)
                 cp16((unsigned char *)sQrec + 16 * v, rs + 4 * v);
+            if (tid < 4) cp16(sCq + 4 * tid, p.qc32 + i * 16 + 4 * tid);
             cp_commit();
             cp_wait<0>();
             tc::fence_proxy_async_smem();
         }
         __syncthreads();
-        const float *cq = p.qc32 + i * 16;
         const int sQ = p.qscale[i];
         for (int jb = 0; jb < nblk; ++jb) {
             const uint32_t bmask = 0xFFu << (kTcBlk * jb);
@@ -435,6 +513,7 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
                 while (e < e1 && !(ent[e].mask & bmask)) e += kTcWG;
                 return e;
             };
+            // stage entry e's reference leaf into buffer b: tiles, records, centre
             auto stage = [&](long long e, int b) {
                 const int64_t ri = ent[e].r - rleaf0;
                 const int64_t rb = level_begin(p.rn, p.r_depth, ri), re = level_begin(p.rn, p.r_depth, ri + 1);
@@ -444,6 +523,7 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
                 const float *rs = p.rrec + rb * p.stride;
                 const int nv = (int)(re - rb) * (p.stride / 4);
                 for (int v = t; v < nv; v += 128) cp16(dst + kTcLeafBytes + 16 * v, rs + 4 * v);
+                if (t < 4) cp16(dst + kTcLeafBytes + TcSmem::kRecBytes + 16 * t, p.rc32 + ri * 16 + 4 * t);
                 cp_commit();
             };
             long long e = next_used(e0 + wg);
@@ -458,23 +538,23 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
                     cp_wait<0>();
                 }
                 tc::fence_proxy_async_smem();
-                tc::bar_sync(bar_id, 128);
+                tc::fence_before_sync();
+                tc::bar_sync(x.bar_id, 128);
                 const MergedEntry E = ent[e];
                 const int64_t ri = E.r - rleaf0;
                 const int nr = (int)(level_begin(p.rn, p.r_depth, ri + 1) - level_begin(p.rn, p.r_depth, ri));
                 const unsigned char *st_tiles = sm + TcSmem::STAGE + (wg * 2 + buf) * TcSmem::STAGE_ONE;
                 const float *st_rec = reinterpret_cast<const float *>(st_tiles + kTcLeafBytes);
-                const float *cr = p.rc32 + ri * 16;
-                const int sR = p.rscale[ri];
-                // beta of reference t, alpha of query t
+                const float *cR = st_rec + TcSmem::kRecBytes / 4;
+                const int nchunks = (nr + kTcChunk - 1) / kTcChunk;
+                x.b0 = tc::smem_u32(st_tiles);
+                // chunk 0's MMAs run while beta and alpha are formed
+                if (x.leader && !*x.abort) tc_issue_chunk(x, 0);
                 float beta = 0.f, lw = -INFINITY, alpha = 0.f;
                 {
-                    float cR[16], dl[16];
+                    float dl[16];
 #pragma unroll
-                    for (int d = 0; d < 16; ++d) {
-                        cR[d] = __ldg(cr + d);
-                        dl[d] = __ldg(cq + d) - cR[d];
-                    }
+                    for (int d = 0; d < 16; ++d) dl[d] = sCq[d] - cR[d];
                     if (t < nr) {
                         const float *rv = st_rec + t * p.stride;
                         float s = 0.f;
@@ -499,84 +579,24 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
                 }
                 bl[2 * t] = beta;
                 bl[2 * t + 1] = lw;
-                // bandwidths of this entry in the block
-                // slot k takes the k-th set bit (compile-time indices keep these in registers)
                 const uint32_t m = (E.mask & bmask) >> (kTcBlk * jb);
                 const int nj = __popc(m);
-                int ks[kTcBlk];
-                f2_t c2[kTcBlk];
-                {
-                    uint32_t mm = m;
-#pragma unroll
-                    for (int k = 0; k < kTcBlk; ++k) {
-                        const int b = mm ? __ffs(mm) - 1 : 0;
-                        const float c = mm ? p.negc[kTcBlk * jb + b] : 0.f;
-                        ks[k] = b;
-                        c2[k] = pk2(c, c);
-                        mm &= mm - 1;
-                    }
-                }
                 evals += (unsigned long long)nj * (unsigned long long)nr;
-                const float m2s = ldexpf(-2.f, 20 - sQ - sR);
+                const float m2s = ldexpf(-2.f, 20 - sQ - __ldg(p.rscale + ri));
                 const f2_t m2s2 = pk2(m2s, m2s), alpha2 = pk2(alpha, alpha);
-                f2_t part[kTcBlk];
-#pragma unroll
-                for (int k = 0; k < kTcBlk; ++k) part[k] = 0ull;
-                tc::fence_before_sync();
-                tc::bar_sync(bar_id, 128);   // (beta, lw) visible; the accumulators are free
-                const int nchunks = (nr + kTcChunk - 1) / kTcChunk;
-                for (int c = 0; c < nchunks; ++c) {
-                    if (t == 0) {
-                        tc::fence_after_sync();
-                        const uint32_t a0 = tc::smem_u32(sA);
-                        const uint32_t b0 = tc::smem_u32(st_tiles) + (uint32_t)(c * kTcChunk * 32);
-                        // digit g of A / B at + g * kTcDigitBytes: 0 = U2, 1 = U1, 2 = U0
-                        auto A = [&](int g) { return tc::smem_desc(a0 + g * kTcDigitBytes, 128, 256); };
-                        auto B = [&](int g) { return tc::smem_desc(b0 + g * kTcDigitBytes, 128, 256); };
-                        tc::mma_f16(tmem_mma + 0 * kTcChunk, A(0), B(0), idesc, 0);   // P4 = U2 V2
-                        tc::mma_f16(tmem_mma + 1 * kTcChunk, A(0), B(1), idesc, 0);   // P3 = U2 V1
-                        tc::mma_f16(tmem_mma + 1 * kTcChunk, A(1), B(0), idesc, 1);   //    + U1 V2
-                        tc::mma_f16(tmem_mma + 2 * kTcChunk, A(0), B(2), idesc, 0);   // P2 = U2 V0
-                        tc::mma_f16(tmem_mma + 2 * kTcChunk, A(1), B(1), idesc, 1);   //    + U1 V1
-                        tc::mma_f16(tmem_mma + 2 * kTcChunk, A(2), B(0), idesc, 1);   //    + U0 V2
-                        tc::mma_commit(&mbar[wg]);
-                    }
-                    if (!tc::mbar_wait_bounded(&mbar[wg], phase, kTcWaitPolls)) s_abort[wg] = 1;
-                    phase ^= 1u;
-                    tc::bar_sync(bar_id, 128);
-                    if (s_abort[wg]) break;
-                    tc::fence_after_sync();
-                    const float *blc = bl + 2 * kTcChunk * c;
-                    switch (nj) {
-                        case 1: tc_chunk_epilogue<1>(tmem, blc, alpha2, m2s2, c2, part); break;
-                        case 2: tc_chunk_epilogue<2>(tmem, blc, alpha2, m2s2, c2, part); break;
-                        case 3: tc_chunk_epilogue<3>(tmem, blc, alpha2, m2s2, c2, part); break;
-                        case 4: tc_chunk_epilogue<4>(tmem, blc, alpha2, m2s2, c2, part); break;
-                        case 5: tc_chunk_epilogue<5>(tmem, blc, alpha2, m2s2, c2, part); break;
-                        case 6: tc_chunk_epilogue<6>(tmem, blc, alpha2, m2s2, c2, part); break;
-                        case 7: tc_chunk_epilogue<7>(tmem, blc, alpha2, m2s2, c2, part); break;
-                        default: tc_chunk_epilogue<8>(tmem, blc, alpha2, m2s2, c2, part); break;
-                    }
-                    tc::fence_before_sync();
-                    tc::bar_sync(bar_id, 128);   // every lane has read the accumulators
+                tc::bar_sync(x.bar_id, 128);   // (beta, lw) visible
+                const float *negc = p.negc + kTcBlk * jb;
+                switch (nj) {
+                    case 1: tc_entry<1>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
+                    case 2: tc_entry<2>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
+                    case 3: tc_entry<3>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
+                    case 4: tc_entry<4>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
+                    case 5: tc_entry<5>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
+                    case 6: tc_entry<6>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
+                    case 7: tc_entry<7>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
+                    default: tc_entry<8>(x, nchunks, bl, alpha2, m2s2, m, negc, ksum, kcmp); break;
                 }
-                if (s_abort[wg]) break;
-                // FP32 sum over the reference leaf, then compensated across leaves
-#pragma unroll
-                for (int k = 0; k < kTcBlk; ++k) {
-                    if (k >= nj) break;
-                    float lo, hi;
-                    upk2(part[k], lo, hi);
-                    const float v = lo + hi;
-#pragma unroll
-                    for (int kk = 0; kk < kTcBlk; ++kk)
-                        if (kk == ks[k]) {
-                            const float y = v - kcmp[kk];
-                            const float s2 = ksum[kk] + y;
-                            kcmp[kk] = (s2 - ksum[kk]) - y;
-                            ksum[kk] = s2;
-                        }
-                }
+                if (*x.abort) break;
                 buf ^= 1;
                 e = en;
             }
@@ -588,15 +608,14 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
 #pragma unroll
             for (int k = 0; k < kTcBlk; ++k) red[(wg * kTcBlk + k) * kTcRows + t] = (double)ksum[k] - (double)kcmp[k];
             __syncthreads();
-            for (int x = tid; x < kTcBlk * kTcRows; x += blockDim.x) {
-                const int k = x / kTcRows, row = x % kTcRows;
+            for (int xx = tid; xx < kTcBlk * kTcRows; xx += blockDim.x) {
+                const int k = xx / kTcRows, row = xx % kTcRows;
                 const int bit = kTcBlk * jb + k;
                 if (row >= nq || bit >= p.nh) continue;
                 double v = 0.0;
                 for (int w = 0; w < kTcWG; ++w) v += red[(w * kTcBlk + k) * kTcRows + row];
                 if (v != 0.0) atomicAdd(&p.Gq[(qb + row) * p.nh + p.jcol[bit]], v * wmax);
             }
-            __syncthreads();
         }
         if (p.evals && t == 0 && evals) {
             atomicAdd(p.evals, evals * (unsigned long long)nq);
