@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--leaf", type=int, default=0, help="fixed leaf size (skips the autotuner)")
     ap.add_argument("--cost", default="", help="fixed cost weights c_DH,c_DL,c_H2L,c_Direct (skips the autotuner)")
+    ap.add_argument("--plimit", type=int, default=0, help="fixed highest series order PLIMIT (with --leaf/--cost; "
+                                                           "0: the Section 6 table)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy check after the timed steps (every result against the GPU "
@@ -311,17 +313,17 @@ def run_gs(args):
     if args.leaf or args.cost:
         from paper_1206_6857_gb300 import autotune
         cw = [float(v) for v in args.cost.split(",")] if args.cost else list(gs.GS_COST_DEFAULT)
-        tuned = {"leaf_size": args.leaf or 32, "plimit": 0, "cost_weight": cw, "fixed": True}
+        tuned = {"leaf_size": args.leaf or 32, "plimit": args.plimit, "cost_weight": cw, "fixed": True}
         opts = autotune.options(tuned)
     elif eps > 0 and not args.no_tune:
         from paper_1206_6857_gb300 import autotune
         t0 = time.perf_counter()
         # every bandwidth of the step: the merged base case handles them in
         # blocks of 8, so a subset would favour the wrong leaf size
-        tuned, _table = autotune.tune(tr, tw, hs, eps, h_subset=0, queries=None if wl.mono else tq)
+        tuned, _table = autotune.tune_staged(tr, tw, hs, eps, wl.D, h_subset=0, queries=None if wl.mono else tq)
         tuned["tuning_seconds"] = time.perf_counter() - t0
-        tuned["candidates"] = [[r["leaf_size"]] + list(r["cost_weight"]) + [round(r["seconds"] * 1e3, 1)]
-                               for r in _table]     # leaf, c_DH, c_DL, c_H2L, c_Direct, ms
+        tuned["candidates"] = [[r["leaf_size"], r["plimit"]] + list(r["cost_weight"]) + [round(r["seconds"] * 1e3, 1)]
+                               for r in _table]     # leaf, PLIMIT, c_DH, c_DL, c_H2L, c_Direct, ms
         opts = autotune.options(tuned)
 
     opts, _sel_params = selector_opts(args, opts)

@@ -46,6 +46,12 @@ def _opts(leaf, plimit, cw):
     return o
 
 
+def default_plimits(D):
+    """PLIMIT candidates: the Section 6 table (0) and, where series orders
+    are affordable (D <= 8), every even order from 2 to 8."""
+    return (0, 2, 4, 6, 8) if D <= 8 else (0,)
+
+
 def tune(points, weights, h, eps, fraction=1.0, h_subset=8, leaves=DEFAULT_LEAVES, costs=DEFAULT_COSTS,
          plimits=(0,), seed=0, reps=1, queries=None):
     """Time every candidate on a seeded subsample; returns (best dict, table).
@@ -87,6 +93,23 @@ def tune(points, weights, h, eps, fraction=1.0, h_subset=8, leaves=DEFAULT_LEAVE
             ts.append(time.perf_counter() - t0)
         table.append({"leaf_size": leaf, "plimit": P, "cost_weight": list(cw), "seconds": float(min(ts))})
     best = min(table, key=lambda r: r["seconds"])
+    return best, table
+
+
+def tune_staged(points, weights, h, eps, D, queries=None, **kw):
+    """tune() over leaf sizes and cost weights at the Section 6 PLIMIT, then
+    over PLIMIT (default_plimits(D)) at the best leaf size and weights: the
+    series order only matters where series actions are chosen, so the second
+    stage is a short one.  Returns (best, table of both stages)."""
+    best, table = tune(points, weights, h, eps, queries=queries, **kw)
+    extra = [P for P in default_plimits(D) if P != 0]
+    if extra:
+        kw2 = dict(kw)
+        kw2.update(leaves=(best["leaf_size"],), costs=(tuple(best["cost_weight"]),), plimits=tuple(extra))
+        b2, t2 = tune(points, weights, h, eps, queries=queries, **kw2)
+        table = table + t2
+        if b2["seconds"] < best["seconds"]:
+            best = b2
     return best, table
 
 

@@ -58,3 +58,10 @@ def test_bench_workload_record():
     cfg = b.wl_config(wl, "lscv", 1e-2)
     assert cfg["gaussian_sums"] == 2 * cfg["nh"] and cfg["mode"] == "lscv" and cfg["eps"] == 1e-2
     assert cfg["parallelism"] == "replicas"
+
+
+def test_autotuner_plimit_candidates():
+    """PLIMIT is searched (2..8, even) where series orders are affordable."""
+    from paper_1206_6857_gb300 import autotune
+    assert autotune.default_plimits(5) == (0, 2, 4, 6, 8)
+    assert autotune.default_plimits(16) == (0,)
