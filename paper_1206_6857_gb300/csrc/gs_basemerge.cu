@@ -4,16 +4,23 @@
 // of reference leaves).  A bandwidth sweep leaves the same leaf pair
 // unpruned for several neighbouring bandwidths, and every one of them needs
 // the same squared distances.  This pass folds the per-bandwidth lists into
-// one list of (Q, R, bandwidth mask) entries per query leaf:
-//   mark    -- atomicOr of bit j into a dense lq x lr mask array;
-//   count   -- nonzero masks per query-leaf row;
+// one list of (Q, R, bandwidth mask) entries per query leaf.  In complete
+// kd-trees every leaf-leaf pair meets in the same frontier iteration, so each
+// (Q, h_j) has at most one list:
+//   index   -- the list of each (Q, mask bit) in a lq x 32 table;
+//   count   -- per query leaf, the bandwidth masks built in shared memory one
+//              slice of reference leaves at a time, nonzero masks counted;
 //   scan    -- row offsets;
-//   compact -- (R, mask) entries per row in ascending R.
+//   write   -- the masks rebuilt and the (R, mask) entries written in ascending R.
+// Global scratch grows with the number of base pairs (the lists and the
+// entries), not with lq x lr; the lq x lr mask words exist only in shared
+// memory, one slice per CTA at a time.
 // The base-case kernel then forms each squared distance once per (query,
 // reference) and evaluates one exponential per bandwidth in the mask
 // (Section 1's sum term, DITOBase of Fig. 7).  Sums: FP32 over the terms of
 // one reference leaf, then compensated (Kahan) FP32 per (bandwidth, query)
 // across leaves, then FP64 across warps.
+#include <limits.h>
 #include <math.h>
 
 #include "gs_device.cuh"
@@ -27,50 +34,85 @@ struct BitMap {
     int8_t rank[64];    // bandwidth j -> mask bit (bandwidths ranked by ascending h)
 };
 
-__global__ void k_mark_masks(const Group *__restrict__ bgroups, int64_t nbg, const int32_t *__restrict__ base_r,
-                             int64_t qleaf0, int64_t rleaf0, int64_t lr, uint32_t *mask, BitMap bm) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < nbg; g += warps) {
+// A second base group for the same (query leaf, bandwidth) would mean leaf
+// pairs met in two frontier iterations, which complete trees rule out; it is
+// reported (ST_INTERNAL) rather than merged.
+__global__ void k_row_groups(const Group *__restrict__ bgroups, int64_t nbg, int64_t qleaf0, BitMap bm,
+                             int32_t *gidx, Ingest *ing) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nbg; g += (int64_t)gridDim.x * blockDim.x) {
         const Group G = bgroups[g];
-        uint32_t *row = mask + (G.q - qleaf0) * lr;
-        const uint32_t bit = 1u << bm.rank[G.j];
-        for (int k = lane; k < G.cnt; k += 32) atomicOr(&row[base_r[G.off + k] - rleaf0], bit);
+        if (atomicCAS(&gidx[(G.q - qleaf0) * 32 + bm.rank[G.j]], -1, (int32_t)g) != -1)
+            atomicOr(&ing->status, ST_INTERNAL);
     }
 }
 
-__global__ void k_row_count(const uint32_t *__restrict__ mask, int64_t lq, int64_t lr, long long *cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < lq; i += warps) {
-        const uint32_t *row = mask + i * lr;
-        int c = 0;
-        for (int64_t k = lane; k < lr; k += 32) c += row[k] != 0u;
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0) cnt[i] = c;
-    }
-}
+// One CTA per query-leaf row (grid-stride): the row's bandwidth masks are
+// built in shared memory, one slice of kSlice reference leaves at a time
+// (atomicOr of bit b for every reference leaf on the list of mask bit b), then
+// the nonzero masks of the slice are counted (WRITE = false: cnt_off[row] =
+// count) or written in ascending R at cnt_off[row] (WRITE = true: each thread
+// takes a contiguous run of words; a block-wide exclusive scan of the run
+// counts orders the writes).
+constexpr int kSlice = 16384;
+constexpr int kMergeThreads = 256;
 
-__global__ void k_row_compact(const uint32_t *__restrict__ mask, int64_t lq, int64_t lr, int64_t rleaf0,
-                              const long long *__restrict__ off, MergedEntry *ent) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < lq; i += warps) {
-        const uint32_t *row = mask + i * lr;
-        int64_t o = off[i];
-        for (int64_t k0 = 0; k0 < lr; k0 += 32) {
-            const int64_t k = k0 + lane;
-            const uint32_t m = k < lr ? row[k] : 0u;
-            const unsigned b = __ballot_sync(0xffffffffu, m != 0u);
-            if (m) {
-                MergedEntry e;
-                e.r = (int32_t)(rleaf0 + k);
-                e.mask = m;
-                ent[o + __popc(b & lt)] = e;
+template <bool WRITE>
+__global__ void __launch_bounds__(kMergeThreads)
+k_row_masks(const Group *__restrict__ bgroups, const int32_t *__restrict__ base_r, const int32_t *__restrict__ gidx,
+            int64_t lq, int64_t lr, int64_t rleaf0, long long *__restrict__ cnt_off, MergedEntry *__restrict__ ent) {
+    extern __shared__ uint32_t smask[];          // kSlice words
+    __shared__ int s_warp[kMergeThreads / 32];
+    constexpr int kRun = kSlice / kMergeThreads;  // words per thread
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int64_t i = blockIdx.x; i < lq; i += gridDim.x) {
+        long long o = WRITE ? cnt_off[i] : 0;
+        long long total = 0;
+        for (int64_t s0 = 0; s0 < lr; s0 += kSlice) {
+            for (int k = t; k < kSlice; k += kMergeThreads) smask[k] = 0u;
+            __syncthreads();
+            for (int b = 0; b < 32; ++b) {
+                const int32_t g = gidx[i * 32 + b];
+                if (g < 0) continue;
+                const Group G = bgroups[g];
+                for (int k = t; k < G.cnt; k += kMergeThreads) {
+                    const int64_t rl = (int64_t)base_r[G.off + k] - rleaf0 - s0;
+                    if (rl >= 0 && rl < kSlice) atomicOr(&smask[rl], 1u << b);
+                }
             }
-            o += __popc(b);
+            __syncthreads();
+            int c = 0;
+#pragma unroll 8
+            for (int k = 0; k < kRun; ++k) c += smask[t * kRun + k] != 0u;
+            // block-wide exclusive scan of the per-thread counts
+            int incl = c;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            if (lane == 31) s_warp[w] = incl;
+            __syncthreads();
+            int before = 0, slice_total = 0;
+            for (int k = 0; k < kMergeThreads / 32; ++k) {
+                if (k < w) before += s_warp[k];
+                slice_total += s_warp[k];
+            }
+            if (WRITE) {
+                long long pos = o + total + before + (incl - c);
+                for (int k = 0; k < kRun; ++k) {
+                    const uint32_t m = smask[t * kRun + k];
+                    if (m) {
+                        MergedEntry e;
+                        e.r = (int32_t)(rleaf0 + s0 + t * kRun + k);
+                        e.mask = m;
+                        ent[pos++] = e;
+                    }
+                }
+            }
+            total += slice_total;
+            __syncthreads();   // the slice and s_warp are reused
         }
+        if (!WRITE && t == 0) cnt_off[i] = total;
     }
 }
 
@@ -408,8 +450,9 @@ bool merged_base_possible(const TraversalIn &in) {
     merged_shape(in, qpl, lmax);
     const int DP = dp_for(in.D);
     const int NT = (int)(((DP + 1) * sizeof(float) + 15) / 16) * 4;
-    return in.nh <= 32 && lq * lr <= (3ll << 30)   // mask array at most 12 GB
-           && qpl <= 4 && merged_smem(DP, NT, qpl, lmax) <= 220 * 1024;
+    (void)lq;
+    (void)lr;
+    return in.nh <= 32 && qpl <= 4 && merged_smem(DP, NT, qpl, lmax) <= 220 * 1024;
 }
 
 // records with every float duplicated, for the packed path
@@ -429,14 +472,14 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         cx.phase(GS_PH_OTHER);
         return GS_OK;
     }
-    uint32_t *mask = nullptr;
+    int32_t *gidx = nullptr;   // lq x 32: base group of (query leaf, mask bit), -1 if none
     long long *off = nullptr;
     MergedEntry *ent = nullptr, *ent_dir = nullptr;
     long long *off_dir = nullptr;
     float *rec2 = nullptr;
     // a failed call frees what this phase holds, so the pool gets it back
     auto release = [&]() {
-        if (mask) cudaFreeAsync(mask, st);
+        if (gidx) cudaFreeAsync(gidx, st);
         if (off) cudaFreeAsync(off, st);
         if (ent) cudaFreeAsync(ent, st);
         if (ent_dir) cudaFreeAsync(ent_dir, st);
@@ -451,8 +494,8 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
             return cuda_fail(e__, #call);     \
         }                                     \
     } while (0)
-    GS_TRY_M(dev_malloc_async((void **)&mask, (size_t)lq * lr * sizeof(uint32_t), st));
-    GS_TRY_M(cudaMemsetAsync(mask, 0, (size_t)lq * lr * sizeof(uint32_t), st));
+    GS_TRY_M(dev_malloc_async((void **)&gidx, (size_t)lq * 32 * sizeof(int32_t), st));
+    GS_TRY_M(cudaMemsetAsync(gidx, 0xFF, (size_t)lq * 32 * sizeof(int32_t), st));
     GS_TRY_M(dev_malloc_async((void **)&off, (size_t)(lq + 2) * sizeof(long long), st));
     const int grid = fb.grid_warps / 8;
     // mask bit of each bandwidth: its rank in ascending h
@@ -466,8 +509,12 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         }
     BitMap bmap;
     for (int b = 0; b < in.nh; ++b) bmap.rank[order[b]] = (int8_t)b;
-    k_mark_masks<<<grid, 256, 0, st>>>(fb.base_groups, fb.n_base_groups, fb.base_r, qleaf0, rleaf0, lr, mask, bmap);
-    k_row_count<<<grid, 256, 0, st>>>(mask, lq, lr, off);
+    k_row_groups<<<grid, 256, 0, st>>>(fb.base_groups, fb.n_base_groups, qleaf0, bmap, gidx, (Ingest *)in.ing);
+    const unsigned mgrid = (unsigned)(lq < 4096 ? lq : 4096);
+    GS_TRY_M(allow_max_smem((const void *)k_row_masks<false>));
+    GS_TRY_M(allow_max_smem((const void *)k_row_masks<true>));
+    k_row_masks<false><<<mgrid, kMergeThreads, kSlice * sizeof(uint32_t), st>>>(fb.base_groups, fb.base_r, gidx, lq, lr,
+                                                                             rleaf0, off, nullptr);
     cx.launches += 2;
     if (int rc0 = scan_i64(off, lq, off + lq, cx)) {
         release();
@@ -477,10 +524,11 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     GS_TRY_M(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
     GS_TRY_M(cudaStreamSynchronize(st));
     GS_TRY_M(dev_malloc_async((void **)&ent, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
-    k_row_compact<<<grid, 256, 0, st>>>(mask, lq, lr, rleaf0, off, ent);
+    k_row_masks<true><<<mgrid, kMergeThreads, kSlice * sizeof(uint32_t), st>>>(fb.base_groups, fb.base_r, gidx, lq, lr,
+                                                                            rleaf0, off, ent);
     cx.launches += 1;
-    cudaFreeAsync(mask, st);
-    mask = nullptr;
+    cudaFreeAsync(gidx, st);
+    gidx = nullptr;
     int rc = cx.check("merge base pairs");
     if (!rc) {
         MergedParams bp;

@@ -125,3 +125,36 @@ def test_config4_every_result_and_smallest_sums(gs):
     wl = synth.config4()
     dt, ex, W, info = _full_check(gs, wl, wl.eps, wl.h)
     _oracle_check(wl, wl.eps, wl.h, dt, ex, W, info)
+
+
+def test_config2_four_million_points_merged_base_case(gs):
+    """C2's law at N = 4e6 with leaf 64 and every other sweep bandwidth:
+    2^16 x 2^16 leaves, where a dense (query leaf x reference leaf)
+    bandwidth-mask array would take 17 GB (more than the 12 GB the earlier
+    dense version allowed itself before falling back to the per-bandwidth
+    kernel).  The merged base case's scratch grows with the base pairs
+    instead; the sample (300 seeded queries and the 64 with the smallest sums)
+    is within eps of the oracle.  The pool's high-water mark (the frontier's
+    pair lists dominate it) is recorded."""
+    import torch
+    wl = synth.config2(4.0)
+    h = wl.h[::2]
+    tq, tw = _dev(wl.queries), _dev(wl.weights)
+    o = gs.gs_opts_default()
+    o.leaf_size = 64
+    gs.gs_trim_memory(0)
+    st = gs.gs_stats()
+    got = gs.gs_sum(tq, tq, tw, h, wl.eps, opts=o, stats=st).cpu().numpy()
+    torch.cuda.synchronize()
+    reserved, _ = gs.gs_pool_bytes()
+    W = float(wl.weights.astype(np.float64).sum())
+    small = np.unique(np.argsort(got, axis=0, kind="stable")[:8].ravel())[:64]
+    seeded = np.random.default_rng(4).choice(wl.M, 300, replace=False)
+    idx = np.sort(np.union1d(small, seeded))
+    exact = oracle_ex.gauss_sum(wl.queries[idx], wl.refs, wl.weights, h)
+    err = rel_err(got[idx], exact, W, FLOOR_LOG2)
+    info = dict(eps=wl.eps, N=wl.N, leaf=64, nh=int(h.size), pool_reserved_bytes=int(reserved),
+                sample=int(idx.size), max_rel_err_vs_oracle=float(err.max()),
+                point_pairs_base=st.point_pairs_base, ms_total=st.ms_total)
+    _record(wl.name + "_leaf64_8h", info)
+    assert err.max() <= wl.eps, info
