@@ -102,7 +102,7 @@ int CallCtx::check(const char *what) {
     return GS_OK;
 }
 
-static int check_common(const void *queries, int64_t M, const void *refs, const float *weights,
+int check_common(const void *queries, int64_t M, const void *refs, const float *weights,
                         int64_t N, int D, int dtype, const double *h, int nh, double eps,
                         double *out) {
     if (!queries || !refs || !weights || !out || !h) {

@@ -1,9 +1,13 @@
 // Many independent Gaussian-sum problems in one call (a batch of KDE
-// problems of uneven N and D).  Each problem is a full gs_sum: its own trees,
-// frontier and base case.  A problem's traversal is a chain of small launches
-// with one host read per frontier iteration, so the batch keeps the GPU busy
-// by running several problems at once: worker host threads, each with its own
-// stream, take problems largest-first from a shared counter.  The caller's
+// problems of uneven N and D).  Problems summed exhaustively (eps = 0, or
+// small ones under GS_FLAG_SMALL_EXHAUSTIVE) with FP32 points and D <= 8 go
+// through the grouped exhaustive path: a handful of launches for all of them
+// together.  Every other problem is a full gs_sum: its own trees, frontier
+// and base case.  A problem's traversal is a chain of small launches with one
+// host read per frontier iteration, so the batch keeps the GPU busy by
+// running several problems at once: worker host threads, each with its own
+// stream, take problems largest-first from a shared counter, while the
+// calling thread runs the grouped path on a stream of its own.  The caller's
 // stream is joined at both ends with events.
 #include <algorithm>
 #include <atomic>
@@ -33,9 +37,20 @@ extern "C" int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts 
     if (nworkers == 0) nworkers = 8;
     if (nworkers > nprob) nworkers = nprob;
     cudaStream_t caller = (cudaStream_t)stream;
-    // largest problems first (M N nh)
-    std::vector<int> order(nprob);
-    for (int i = 0; i < nprob; ++i) order[i] = i;
+    // exhaustive problems the grouped path takes; the rest, largest first (M N nh)
+    const bool small_ex = opts && (opts->flags & GS_FLAG_SMALL_EXHAUSTIVE);
+    std::vector<int> grouped, order;
+    for (int i = 0; i < nprob; ++i) {
+        const gs_problem &p = probs[i];
+        const bool exh = p.eps == 0.0 || (small_ex && (double)p.M * (double)p.N * (double)p.nh <= GS_SMALL_WORK);
+        if (exh && exhaustive_groupable(p) &&
+            check_common(p.queries, p.M, p.refs, p.weights, p.N, p.D, p.dtype, p.h, p.nh, p.eps, p.out) == GS_OK)
+            grouped.push_back(i);
+        else
+            order.push_back(i);
+    }
+    const int nrest = (int)order.size();
+    if (nworkers > nrest) nworkers = nrest > 0 ? nrest : 1;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const double wa = (double)probs[a].M * (double)probs[a].N * probs[a].nh;
         const double wb = (double)probs[b].M * (double)probs[b].N * probs[b].nh;
@@ -58,7 +73,7 @@ extern "C" int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts 
         if (rc == GS_OK) rc = cu_ok(cudaStreamWaitEvent(st, start, 0), "worker start");
         if (rc == GS_OK) rc = cu_ok(cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming), "worker event");
         memset(&wstats[w], 0, sizeof(gs_stats));
-        for (int k; rc == GS_OK && (k = next.fetch_add(1)) < nprob;) {
+        for (int k; rc == GS_OK && (k = next.fetch_add(1)) < nrest;) {
             const int i = order[k];
             const gs_problem &p = probs[i];
             gs_stats ps;
@@ -97,9 +112,35 @@ extern "C" int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts 
         }
     };
     std::vector<std::thread> th;
-    for (int w = 1; w < nworkers; ++w) th.emplace_back(worker, w);
-    worker(0);
+    for (int w = 0; w < nworkers && nrest > 0; ++w) th.emplace_back(worker, w);
+    // the grouped exhaustive problems, on a stream of their own
+    gs_stats gstats;
+    memset(&gstats, 0, sizeof(gstats));
+    cudaStream_t gst = nullptr;
+    cudaEvent_t gdone = nullptr;
+    if (!grouped.empty()) {
+        int grc = cu_ok(cudaStreamCreateWithFlags(&gst, cudaStreamNonBlocking), "grouped stream");
+        if (grc == GS_OK) grc = cu_ok(cudaStreamWaitEvent(gst, start, 0), "grouped start");
+        if (grc == GS_OK) grc = cu_ok(cudaEventCreateWithFlags(&gdone, cudaEventDisableTiming), "grouped event");
+        if (grc == GS_OK)
+            grc = exhaustive_batch(probs, grouped.data(), (int)grouped.size(), gst, status, stats ? &gstats : nullptr);
+        if (grc != GS_OK) {
+            if (status && !gdone)
+                for (int i : grouped) status[i] = grc;
+            std::lock_guard<std::mutex> lk(mu);
+            if (first_rc == GS_OK) {
+                first_rc = grc;
+                first_msg = std::string("grouped exhaustive problems: ") + gs_last_error();
+            }
+        }
+        if (gdone) cudaEventRecord(gdone, gst);
+    }
     for (auto &t : th) t.join();
+    if (gdone) {
+        cudaStreamWaitEvent(caller, gdone, 0);
+        cudaEventDestroy(gdone);
+    }
+    if (gst) cudaStreamDestroy(gst);
     for (int w = 0; w < nworkers; ++w)
         if (done[w]) {
             cudaStreamWaitEvent(caller, done[w], 0);
@@ -108,6 +149,9 @@ extern "C" int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts 
     cudaEventRecord(stop, caller);
     cudaError_t e = cudaEventSynchronize(stop);
     if (stats && e == cudaSuccess) {
+        stats->point_pairs_base += gstats.point_pairs_base;
+        stats->launches += gstats.launches;
+        stats->launches_base += gstats.launches_base;
         for (int w = 0; w < nworkers; ++w) {
             const gs_stats &a = wstats[w];
             stats->pairs_fd += a.pairs_fd; stats->pairs_dh += a.pairs_dh; stats->pairs_dl += a.pairs_dl;

@@ -20,8 +20,13 @@
 // bandwidths in registers.  A 3-D grid spans query blocks x reference splits
 // x bandwidth chunks; splits are chosen so the grid covers every SM several
 // times even when M is small, and then accumulate with FP64 atomics.
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include <math.h>
 #include <stdarg.h>
+#include <string.h>
 #include <stdio.h>
 
 #include "gs_device.cuh"
@@ -162,25 +167,23 @@ __device__ __forceinline__ void load_rec(const T *p, T (&v)[NT]) {
     }
 }
 
+// One tile of the exhaustive sum: query block bx (kThreads * QPT queries),
+// reference range [by * chunk, (by + 1) * chunk) of the packed records, the NJ
+// bandwidths starting at bz * NJ (nc: their -log2(e) / 2h^2, 0 beyond nh).
 template <typename T, int DP, int NJ, int QPT>
-__global__ void __launch_bounds__(kThreads)
-k_exhaustive(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ rec,
-             int64_t chunk, int64_t Npad, NegC negc, int nh, const Ingest *__restrict__ ing,
-             double *__restrict__ out, int atomic) {
+__device__ __forceinline__ void exhaustive_tile(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ rec,
+                                                int64_t chunk, int64_t Npad, const float (&nc)[NJ], int nh,
+                                                const Ingest *__restrict__ ing, double *__restrict__ out, int atomic,
+                                                int64_t bx, int64_t by, int bz, T *tile) {
     using Cfg = TileCfg<T, DP>;
     constexpr int NT = Cfg::NT, TILE = Cfg::TILE;
-    __shared__ __align__(16) T tile[TILE * NT];
-
-    const int j0 = blockIdx.z * NJ;
-    float nc[NJ];
-#pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) nc[jj] = (j0 + jj < nh) ? negc.v[j0 + jj] : 0.f;
+    const int j0 = bz * NJ;
 
     T xq[QPT][DP];
     int64_t qi[QPT];
 #pragma unroll
     for (int k = 0; k < QPT; ++k) {
-        qi[k] = (int64_t)blockIdx.x * (kThreads * QPT) + k * kThreads + threadIdx.x;
+        qi[k] = bx * (kThreads * QPT) + k * kThreads + threadIdx.x;
         const int64_t qs = qi[k] < M ? qi[k] : M - 1;
 #pragma unroll
         for (int d = 0; d < DP; ++d) xq[k][d] = d < D ? qx[qs * D + d] : (T)0;
@@ -192,7 +195,7 @@ k_exhaustive(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ r
 #pragma unroll
         for (int jj = 0; jj < NJ; ++jj) acc[k][jj] = 0.0;
 
-    const int64_t r0 = blockIdx.y * chunk;
+    const int64_t r0 = by * chunk;
     const int64_t r1 = min(r0 + chunk, Npad);
     for (int64_t t0 = r0; t0 < r1; t0 += TILE) {
         __syncthreads();
@@ -250,6 +253,21 @@ k_exhaustive(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ r
                 out[qi[k] * nh + j] = v;
         }
     }
+}
+
+template <typename T, int DP, int NJ, int QPT>
+__global__ void __launch_bounds__(kThreads)
+k_exhaustive(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ rec,
+             int64_t chunk, int64_t Npad, NegC negc, int nh, const Ingest *__restrict__ ing,
+             double *__restrict__ out, int atomic) {
+    using Cfg = TileCfg<T, DP>;
+    __shared__ __align__(16) T tile[Cfg::TILE * Cfg::NT];
+    const int j0 = blockIdx.z * NJ;
+    float nc[NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) nc[jj] = (j0 + jj < nh) ? negc.v[j0 + jj] : 0.f;
+    exhaustive_tile<T, DP, NJ, QPT>(qx, M, D, rec, chunk, Npad, nc, nh, ing, out, atomic, blockIdx.x, blockIdx.y,
+                                    blockIdx.z, tile);
 }
 
 static int num_sms() {
@@ -333,6 +351,261 @@ int exhaustive_sum(const void *queries, int64_t M, const void *refs, const float
     if (dtype == GS_F64)
         return dispatch_d<double>(queries, M, refs, weights, N, D, h, nh, ing, out, st);
     return dispatch_d<float>(queries, M, refs, weights, N, D, h, nh, ing, out, st);
+}
+
+// --------------------------------------------------------------------------
+// Many small problems in one launch.  The problems of a batch that are summed
+// exhaustively are grouped by dimension bucket and bandwidth-chunk size; a
+// group runs as four launches whatever its size: reset and ingest of every
+// problem's inputs, packing of every problem's references, then one
+// exhaustive launch over the flattened (problem, query block, bandwidth
+// chunk) tiles, largest problems first.  Each problem's references are
+// covered by a single tile row (no reference splits), so outputs are written
+// once, without atomics.
+// --------------------------------------------------------------------------
+struct GroupProb {
+    const void *q, *r;
+    const float *w;
+    double *out;
+    void *rec;          // packed references, Npad records
+    Ingest *ing;
+    int64_t M, N, Npad, bx;
+    int D, nh, nz, pad;
+    long long tile0;    // first flattened tile of this problem
+    float negc[64];
+};
+
+__global__ void k_group_reset(GroupProb *gp, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        Ingest *g = gp[i].ing;
+        g->status = 0;
+        g->wmax_bits = 0;
+        g->wmin_bits = 0x7f800000u;
+        g->pad = 0;
+        g->wsum = 0.0;
+    }
+}
+
+// the checks of launch_ingest for problem blockIdx.y
+__global__ void k_group_ingest(const GroupProb *__restrict__ gp) {
+    const GroupProb &P = gp[blockIdx.y];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned bad = 0;
+    const int64_t nr = P.N * P.D, nq = P.q != P.r ? P.M * P.D : 0;
+    for (int64_t i = i0; i < nr; i += stride)
+        if (!isfinite(((const float *)P.r)[i])) bad |= ST_NONFINITE;
+    for (int64_t i = i0; i < nq; i += stride)
+        if (!isfinite(((const float *)P.q)[i])) bad |= ST_NONFINITE;
+    float wmax = 0.f, wmin = INFINITY;
+    double wsum = 0.0;
+    for (int64_t i = i0; i < P.N; i += stride) {
+        const float wi = P.w[i];
+        if (!isfinite(wi)) {
+            bad |= ST_NONFINITE;
+        } else if (!(wi > 0.f)) {
+            bad |= ST_WEIGHT;
+        } else {
+            wmax = fmaxf(wmax, wi);
+            wmin = fminf(wmin, wi);
+            wsum += wi;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    for (int o = 16; o > 0; o >>= 1) {
+        wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&P.ing->status, bad);
+        atomicMax(&P.ing->wmax_bits, __float_as_uint(wmax));
+        atomicMin(&P.ing->wmin_bits, __float_as_uint(wmin));
+        atomicAdd(&P.ing->wsum, wsum);
+    }
+}
+
+template <int DP>
+__global__ void k_group_pack(const GroupProb *__restrict__ gp) {
+    const GroupProb &P = gp[blockIdx.y];
+    constexpr int NT = RefRec<float, DP>::NT;
+    const double wmax = (double)__uint_as_float(P.ing->wmax_bits);
+    const float *x = (const float *)P.r;
+    float *rec = (float *)P.rec;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.Npad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float *o = rec + i * NT;
+        if (i < P.N) {
+            for (int d = 0; d < DP; ++d) o[d] = d < P.D ? x[i * P.D + d] : 0.f;
+            o[DP] = (float)log2((double)P.w[i] / wmax);
+        } else {
+            for (int d = 0; d < DP; ++d) o[d] = 0.f;
+            o[DP] = -INFINITY;
+        }
+        for (int k = DP + 1; k < NT; ++k) o[k] = 0.f;
+    }
+}
+
+template <int DP, int NJ>
+__global__ void __launch_bounds__(kThreads) k_group_exhaustive(const GroupProb *__restrict__ gp, int nprob) {
+    using Cfg = TileCfg<float, DP>;
+    constexpr int QPT = (DP <= 8) ? 2 : 1;
+    __shared__ __align__(16) float tile[Cfg::TILE * Cfg::NT];
+    const long long t = blockIdx.x;
+    int lo = 0, hi = nprob - 1;   // the problem owning tile t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gp[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const GroupProb &P = gp[lo];
+    const long long local = t - P.tile0;
+    const int bz = (int)(local % P.nz);
+    const int64_t bx = local / P.nz;
+    float nc[NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) nc[jj] = (bz * NJ + jj < P.nh) ? P.negc[bz * NJ + jj] : 0.f;
+    exhaustive_tile<float, DP, NJ, QPT>((const float *)P.q, P.M, P.D, (const float *)P.rec, P.Npad, P.Npad, nc,
+                                        P.nh, P.ing, P.out, 0, bx, 0, bz, tile);
+}
+
+template <int DP, int NJ>
+static int launch_group(const gs_problem *probs, const std::vector<int> &ids, cudaStream_t st, void **block,
+                        GroupProb **dgp_out, std::vector<GroupProb> &hgp, int64_t &launches) {
+    using Cfg = TileCfg<float, DP>;
+    constexpr int NT = Cfg::NT, TILE = Cfg::TILE, QPT = (DP <= 8) ? 2 : 1;
+    const int n = (int)ids.size();
+    hgp.assign(n, GroupProb());
+    size_t rec_bytes = 0;
+    long long tiles = 0;
+    for (int k = 0; k < n; ++k) {
+        const gs_problem &p = probs[ids[k]];
+        GroupProb &g = hgp[k];
+        memset(&g, 0, sizeof(g));
+        g.q = p.queries;
+        g.r = p.refs;
+        g.w = p.weights;
+        g.out = p.out;
+        g.M = p.M;
+        g.N = p.N;
+        g.D = p.D;
+        g.nh = p.nh;
+        g.Npad = (p.N + TILE - 1) / TILE * TILE;
+        g.bx = (p.M + kThreads * QPT - 1) / (kThreads * QPT);
+        g.nz = (p.nh + NJ - 1) / NJ;
+        g.tile0 = tiles;
+        tiles += g.bx * g.nz;
+        for (int j = 0; j < p.nh; ++j) g.negc[j] = (float)(-1.4426950408889634 / (2.0 * p.h[j] * p.h[j]));
+        rec_bytes += (size_t)g.Npad * NT * sizeof(float);
+    }
+    if (tiles > 2147483647LL || n > 65535) {
+        set_error("gs_sum_batched: exhaustive group too large for one launch");
+        return GS_ERR_ARG;
+    }
+    const size_t head = ((n * sizeof(GroupProb) + 255) / 256) * 256;
+    const size_t ings = ((n * sizeof(Ingest) + 255) / 256) * 256;
+    GS_CUDA_TRY(dev_malloc_async(block, head + ings + rec_bytes, st));
+    unsigned char *base = (unsigned char *)*block;
+    size_t off = head + ings;
+    for (int k = 0; k < n; ++k) {
+        hgp[k].ing = (Ingest *)(base + head) + k;
+        hgp[k].rec = base + off;
+        off += (size_t)hgp[k].Npad * NT * sizeof(float);
+    }
+    GroupProb *dgp = (GroupProb *)base;
+    GS_CUDA_TRY(cudaMemcpyAsync(dgp, hgp.data(), n * sizeof(GroupProb), cudaMemcpyHostToDevice, st));
+    k_group_reset<<<(n + 127) / 128, 128, 0, st>>>(dgp, n);
+    k_group_ingest<<<dim3(32, n), 256, 0, st>>>(dgp);
+    k_group_pack<DP><<<dim3(32, n), 256, 0, st>>>(dgp);
+    k_group_exhaustive<DP, NJ><<<(unsigned)tiles, kThreads, 0, st>>>(dgp, n);
+    launches += 4;
+    *dgp_out = dgp;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : cuda_fail(e, "grouped exhaustive launch");
+}
+
+template <int DP>
+static int launch_group_nj(int nj, const gs_problem *probs, const std::vector<int> &ids, cudaStream_t st,
+                           void **block, GroupProb **dgp, std::vector<GroupProb> &hgp, int64_t &launches) {
+    if (nj == 1) return launch_group<DP, 1>(probs, ids, st, block, dgp, hgp, launches);
+    if (nj == 2) return launch_group<DP, 2>(probs, ids, st, block, dgp, hgp, launches);
+    if (nj == 4) return launch_group<DP, 4>(probs, ids, st, block, dgp, hgp, launches);
+    return launch_group<DP, 8>(probs, ids, st, block, dgp, hgp, launches);
+}
+
+bool exhaustive_groupable(const gs_problem &p) { return p.dtype == GS_F32 && p.D >= 1 && p.D <= 8; }
+
+int exhaustive_batch(const gs_problem *probs, const int *idx, int n, cudaStream_t st, int32_t *status,
+                     gs_stats *stats) {
+    // groups: (dimension bucket, bandwidths per chunk), problems largest first
+    std::vector<std::vector<int>> groups(9 * 4);
+    for (int k = 0; k < n; ++k) {
+        const gs_problem &p = probs[idx[k]];
+        const int nj = p.nh <= 1 ? 0 : (p.nh <= 2 ? 1 : (p.nh <= 4 ? 2 : 3));
+        groups[dp_for(p.D) * 4 + nj].push_back(idx[k]);
+    }
+    std::vector<void *> blocks;
+    std::vector<std::pair<std::vector<int>, std::vector<GroupProb>>> launched;
+    int64_t launches = 0;
+    int rc = GS_OK;
+    for (int key = 0; key < (int)groups.size() && rc == GS_OK; ++key) {
+        std::vector<int> &ids = groups[key];
+        if (ids.empty()) continue;
+        std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) {
+            return (double)probs[a].M * probs[a].N * probs[a].nh > (double)probs[b].M * probs[b].N * probs[b].nh;
+        });
+        const int DP = key / 4, nj = 1 << (key % 4);
+        void *block = nullptr;
+        GroupProb *dgp = nullptr;
+        std::vector<GroupProb> hgp;
+        switch (DP) {
+            case 1: rc = launch_group_nj<1>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+            case 2: rc = launch_group_nj<2>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+            case 3: rc = launch_group_nj<3>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+            case 4: rc = launch_group_nj<4>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+            case 5: rc = launch_group_nj<5>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+            case 6: rc = launch_group_nj<6>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+            case 7: rc = launch_group_nj<7>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+            default: rc = launch_group_nj<8>(nj, probs, ids, st, &block, &dgp, hgp, launches); break;
+        }
+        if (block) blocks.push_back(block);
+        if (rc == GS_OK) launched.emplace_back(ids, hgp);
+    }
+    // one status read for every grouped problem
+    std::vector<std::vector<Ingest>> hing(launched.size());
+    for (size_t g = 0; g < launched.size() && rc == GS_OK; ++g) {
+        hing[g].resize(launched[g].first.size());
+        cudaError_t e = cudaMemcpyAsync(hing[g].data(), launched[g].second[0].ing,
+                                        hing[g].size() * sizeof(Ingest), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "grouped exhaustive status");
+    }
+    if (rc == GS_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "grouped exhaustive");
+    }
+    int first = GS_OK;
+    if (rc == GS_OK)
+        for (size_t g = 0; g < launched.size(); ++g)
+            for (size_t k = 0; k < launched[g].first.size(); ++k) {
+                const int i = launched[g].first[k];
+                const int r = status_to_code(hing[g][k].status);
+                if (status) status[i] = r;
+                if (r != GS_OK && first == GS_OK) {
+                    first = r;
+                    char msg[256];
+                    snprintf(msg, sizeof(msg), "%s", gs_last_error());
+                    set_error("problem %d: %s", i, msg);
+                }
+                if (stats) stats->point_pairs_base += launched[g].second[k].M * launched[g].second[k].N *
+                                                      (int64_t)launched[g].second[k].nh;
+            }
+    if (rc != GS_OK && status)   // the batch itself failed: every problem of it reports that
+        for (int k = 0; k < n; ++k) status[idx[k]] = rc;
+    if (stats) {
+        stats->launches += launches;
+        stats->launches_base += (int64_t)launched.size();
+    }
+    for (void *b : blocks) cudaFreeAsync(b, st);
+    return rc != GS_OK ? rc : first;
 }
 
 // --------------------------------------------------------------------------

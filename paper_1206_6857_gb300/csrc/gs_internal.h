@@ -153,6 +153,18 @@ int exhaustive_sum(const void *queries, int64_t M, const void *refs, const float
                    int64_t N, int D, int dtype, const double *h, int nh, const Ingest *ing,
                    double *out, CallCtx &cx);
 
+// Argument checks shared by gs_sum and the batched entry point.
+int check_common(const void *queries, int64_t M, const void *refs, const float *weights, int64_t N, int D,
+                 int dtype, const double *h, int nh, double eps, double *out);
+
+// Exhaustive sums of many problems with few launches (FP32 points, D <= 8:
+// exhaustive_groupable): every listed problem (probs[idx[k]]) is summed as
+// gs_sum with eps = 0 would, its code written to status[idx[k]]; synchronises
+// the stream once.  Returns GS_OK or the first failing code.
+bool exhaustive_groupable(const gs_problem &p);
+int exhaustive_batch(const gs_problem *probs, const int *idx, int n, cudaStream_t st, int32_t *status,
+                     gs_stats *stats);
+
 // ---- dual-tree path -------------------------------------------------------
 // Per-pair record of a logged traversal (training data of the pair
 // selector), indexed by global pair id (iterations in order, pairs of an

@@ -104,3 +104,32 @@ def test_small_problems_summed_exactly_with_the_flag(gs):
         assert float(q.shape[0]) * r.shape[0] * len(h) <= gs.GS_SMALL_WORK
         exact = oracle_ex.gauss_sum(q, r, w, h)
         assert rel_err(out.cpu().numpy(), exact, float(w.astype(np.float64).sum())).max() <= 1e-5
+
+
+def test_grouped_exhaustive_problems(gs):
+    """Under GS_FLAG_SMALL_EXHAUSTIVE every small FP32 problem with D <= 8
+    goes through the grouped exhaustive path (a few launches for all of
+    them): each result within 1e-5 of the oracle, far fewer launches than
+    problems, and a bad weight in one problem reported for that problem only."""
+    wls = [synth.config5_problem(i, scale=0.03) for i in range(40)]
+    dev = [(_dev(wl.queries), None, _dev(wl.weights), wl.h, wl.eps) for wl in wls]
+    dev = [(q, q, w, h, eps) for q, _, w, h, eps in dev]
+    o = gs.gs_opts_default()
+    o.flags = gs.GS_FLAG_SMALL_EXHAUSTIVE
+    st = gs.gs_stats()
+    outs, status = gs.gs_sum_batched(dev, opts=o, nworkers=4, stats=st)
+    assert status == [0] * len(wls)
+    assert st.launches <= 4 * 7 * 4, st.launches          # four launches per (dimension, chunk) group
+    assert st.point_pairs_base == sum(wl.M * wl.N * wl.h.size for wl in wls)
+    for wl, out in zip(wls, outs):
+        exact = oracle_ex.gauss_sum(wl.queries, wl.refs, wl.weights, wl.h)
+        assert np.max(np.abs(out.cpu().numpy() - exact) / exact) <= 1e-5, wl.name
+    w = wls[7].weights.copy()
+    w[5] = 0.0
+    bad = list(dev)
+    bad[7] = (dev[7][0], dev[7][1], _dev(w), wls[7].h, wls[7].eps)
+    outs, status = gs.gs_sum_batched(bad, opts=o, nworkers=4, raise_on_error=False)
+    assert status[7] == gs.GS_ERR_WEIGHT and all(s == 0 for k, s in enumerate(status) if k != 7)
+    with pytest.raises(gs.GSError) as ei:
+        gs.gs_sum_batched(bad, opts=o, nworkers=4)
+    assert ei.value.code == gs.GS_ERR_WEIGHT and "problem 7" in str(ei.value)
