@@ -322,27 +322,30 @@ __device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
     return r;
 }
 
-// One chunk of 16 reference columns for NJ bandwidths: gamma from the three
-// accumulators, the squared distance, then one exponential per bandwidth;
-// two columns per packed f32x2 operation.  bl holds (beta, lw) per column.
+// 16 reference columns for NJ bandwidths: gamma from the three accumulators,
+// the squared distance and each exponent argument two columns per packed
+// f32x2 operation; the exponentials are summed per column parity in scalar
+// FP32 (part[k][0] even columns, part[k][1] odd).  bl holds, per column pair,
+// (beta_i, beta_i+1, lw_i, lw_i+1), so one 16-byte load gives both pairs.
 template <int NJ>
 __device__ __forceinline__ void tc_cols16(const float (&a4)[16], const float (&a3)[16], const float (&a2)[16],
                                           const float *bl, f2_t alpha2, f2_t m2s2, const f2_t (&c2)[NJ],
-                                          f2_t (&part)[NJ]) {
+                                          float (&part)[NJ][2]) {
     const f2_t k1024 = pk2(1024.f, 1024.f);
 #pragma unroll
     for (int i = 0; i < 16; i += 2) {
-        const float4 b = *reinterpret_cast<const float4 *>(bl + 2 * i);   // beta_i, lw_i, beta_i+1, lw_i+1
+        const float4 b = *reinterpret_cast<const float4 *>(bl + 2 * i);
         f2_t g = fma2(pk2(a4[i], a4[i + 1]), k1024, pk2(a3[i], a3[i + 1]));
         g = fma2(g, k1024, pk2(a2[i], a2[i + 1]));
-        const f2_t ab = add2(alpha2, pk2(b.x, b.z));
+        const f2_t ab = add2(alpha2, pk2(b.x, b.y));
         const f2_t d2 = fma2(g, m2s2, ab);
-        const f2_t lw = pk2(b.y, b.w);
+        const f2_t lw = pk2(b.z, b.w);
 #pragma unroll
         for (int k = 0; k < NJ; ++k) {
             float x0, x1;
             upk2(fma2(d2, c2[k], lw), x0, x1);
-            part[k] = add2(part[k], pk2(ex2_approx(x0), ex2_approx(x1)));
+            part[k][0] += ex2_approx(x0);
+            part[k][1] += ex2_approx(x1);
         }
     }
 }
@@ -386,14 +389,15 @@ template <int NJ>
 __device__ __forceinline__ void tc_entry(TcEntryCtx &x, int nchunks, const float *bl, f2_t alpha2, f2_t m2s2,
                                          uint32_t m, const float *negc, float (&ksum)[kTcBlk],
                                          float (&kcmp)[kTcBlk]) {
-    f2_t c2[NJ], part[NJ];
+    f2_t c2[NJ];
+    float part[NJ][2];
     {
         uint32_t mm = m;
 #pragma unroll
         for (int k = 0; k < NJ; ++k) {
             const float c = negc[__ffs(mm) - 1];
             c2[k] = pk2(c, c);
-            part[k] = 0ull;
+            part[k][0] = part[k][1] = 0.f;
             mm &= mm - 1;
         }
     }
@@ -421,9 +425,7 @@ __device__ __forceinline__ void tc_entry(TcEntryCtx &x, int nchunks, const float
     for (int k = 0; k < NJ; ++k) {
         const int slot = __ffs(mm) - 1;
         mm &= mm - 1;
-        float lo, hi;
-        upk2(part[k], lo, hi);
-        const float v = lo + hi;
+        const float v = part[k][0] + part[k][1];
 #pragma unroll
         for (int kk = 0; kk < kTcBlk; ++kk)
             if (kk == slot) {
@@ -459,7 +461,7 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
     }
     if (tid == 0) {
         for (int w = 0; w < kTcWG; ++w) tc::mbar_init(&mbar[w], 1);
-        for (int w = 0; w < kTcWG; ++w) s_abort[w] = 0;
+        for (int w = 0; w < 4; ++w) s_abort[w] = 0;
         tc::mbar_fence_init();
     }
     tc::fence_before_sync();
@@ -552,15 +554,30 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
                 if (x.leader && !*x.abort) tc_issue_chunk(x, 0);
                 float beta = 0.f, lw = -INFINITY, alpha = 0.f;
                 {
-                    float dl[16];
+                    // 16-byte shared loads (centres and records are 16-byte aligned);
+                    // record slots at or past D are masked to zero (slot D holds the
+                    // log-weight when D <= 12)
+                    float cRv[16], dl[16];
 #pragma unroll
-                    for (int d = 0; d < 16; ++d) dl[d] = sCq[d] - cR[d];
+                    for (int v = 0; v < 4; ++v) {
+                        const float4 a = reinterpret_cast<const float4 *>(cR)[v];
+                        const float4 b = reinterpret_cast<const float4 *>(sCq)[v];
+                        cRv[4 * v] = a.x; cRv[4 * v + 1] = a.y; cRv[4 * v + 2] = a.z; cRv[4 * v + 3] = a.w;
+                        dl[4 * v] = b.x - a.x; dl[4 * v + 1] = b.y - a.y;
+                        dl[4 * v + 2] = b.z - a.z; dl[4 * v + 3] = b.w - a.w;
+                    }
                     if (t < nr) {
                         const float *rv = st_rec + t * p.stride;
+                        float x[16];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const float4 a = reinterpret_cast<const float4 *>(rv)[v];
+                            x[4 * v] = a.x; x[4 * v + 1] = a.y; x[4 * v + 2] = a.z; x[4 * v + 3] = a.w;
+                        }
                         float s = 0.f;
 #pragma unroll
                         for (int d = 0; d < 16; ++d) {
-                            const float v = (d < p.D ? rv[d] : 0.f) - cR[d];
+                            const float v = (d < p.D ? x[d] : 0.f) - cRv[d];
                             s = fmaf(v, v - 2.f * dl[d], s);
                         }
                         beta = s;
@@ -568,17 +585,23 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
                     }
                     if (t < nq) {
                         const float *qv = sQrec + t * p.stride;
+                        float x[16];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const float4 a = reinterpret_cast<const float4 *>(qv)[v];
+                            x[4 * v] = a.x; x[4 * v + 1] = a.y; x[4 * v + 2] = a.z; x[4 * v + 3] = a.w;
+                        }
                         float s = 0.f;
 #pragma unroll
                         for (int d = 0; d < 16; ++d) {
-                            const float a = (d < p.D ? qv[d] : 0.f) - cR[d];
+                            const float a = (d < p.D ? x[d] : 0.f) - cRv[d];
                             s = fmaf(a, a, s);
                         }
                         alpha = s;
                     }
                 }
-                bl[2 * t] = beta;
-                bl[2 * t + 1] = lw;
+                bl[4 * (t >> 1) + (t & 1)] = beta;         // (beta_i, beta_i+1, lw_i, lw_i+1) per pair
+                bl[4 * (t >> 1) + 2 + (t & 1)] = lw;
                 const uint32_t m = (E.mask & bmask) >> (kTcBlk * jb);
                 const int nj = __popc(m);
                 evals += (unsigned long long)nj * (unsigned long long)nr;
