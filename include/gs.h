@@ -440,8 +440,9 @@ int gs_mlp_train(float *params, const float *x, const int32_t *y, const float *s
  *   per series action; DH = u_act + N_Q (T_p (D+1) + 3Dp + 30) u_dh,
  *   DL = u_act + N_R (T' (D+1) + 3Dp + 30) u_dl with T' = T_p if T_p <= 32
  *   else 32 ceil(T_p / 32), H2L = u_act + U_p u_h2l with
- *   U_p = 4D + 30 (p = 1), 16D + 30 (p = 2), T_p^2 (D+1) + T_p D + 3D(2p-1) + 30
- *   (T_p <= 20, D(2p-1) <= 32), else 32 (ceil(T_p/32) T_p (D+1) + 40).
+ *   U_p = 4D + 30 (p = 1), 16D + 30 (p = 2), 2 p T_p + (p(p+1)/2)^2 + 80
+ *   (D = 3, p = 3..6), T_p^2 (D+1) + T_p D + 3D(2p-1) + 30 (T_p <= 20,
+ *   D(2p-1) <= 32), else 32 (ceil(T_p/32) T_p (D+1) + 40).
  * Every pair the selector would be consulted on (FD test failed, a certified
  * series method, N_Q N_R >= GS_MLP_MIN_WORK) becomes a sample: x (DEVICE, 12
  * floats each), y (DEVICE, the cheapest action 1..4), s (DEVICE, nullable:

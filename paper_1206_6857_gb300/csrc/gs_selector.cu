@@ -20,6 +20,8 @@
 //       reference, T_p <= 32) or 32 ceil(T_p / 32) (lanes over coefficients)
 //   H2L u_act + U_p u_h2l,   T_p = C(D+p-1, D), with U_p the H2L kernel's path:
 //       p = 1: 4D + 30; p = 2: 16D + 30 (one lane, Lemma 1 written out);
+//       D = 3, p = 3..6: 2 p T_p + (p(p+1)/2)^2 + 80 (one lane, summed one
+//       dimension at a time);
 //       T_p <= 20 and D(2p-1) <= 32: T_p^2 (D+1) + T_p D + 3D(2p-1) + 30 (one lane);
 //       otherwise 32 (ceil(T_p/32) T_p (D+1) + 40) (one warp).
 #include <math.h>
@@ -53,6 +55,8 @@ __device__ __forceinline__ double series_cost(const DpArgs &a, int m, int p, dou
         U = 4.0 * D + 30.0;
     else if (p == 2)
         U = 16.0 * D + 30.0;
+    else if (a.D == 3 && p <= 6)   // the separable three-dimensional kernel
+        U = 2.0 * p * T + (0.5 * p * (p + 1)) * (0.5 * p * (p + 1)) + 80.0;
     else if (T <= 20.0 && a.D * (2 * p - 1) <= 32)
         U = T * T * (D + 1.0) + T * D + 3.0 * D * (2 * p - 1) + 30.0;
     else

@@ -54,6 +54,8 @@ def h2l_units(D, p):
         return 4.0 * D + 30.0
     if p == 2:
         return 16.0 * D + 30.0
+    if D == 3 and p <= 6:                      # the separable three-dimensional kernel
+        return 2.0 * p * T + (0.5 * p * (p + 1)) ** 2 + 80.0
     if T <= 20 and D * (2 * p - 1) <= 32:
         return T * T * (D + 1.0) + T * D + 3.0 * D * (2 * p - 1) + 30.0
     return 32.0 * (np.ceil(T / 32.0) * T * (D + 1.0) + 40.0)

@@ -165,7 +165,8 @@ def test_selector_samples(gs):
 def test_trained_selector_against_the_rule(gs, capsys):
     """The stored network (trained on the GPU by selector.main) on problems it
     was not trained on: both orderings stay within eps of the oracle; the
-    test reports the wall time of each (the gain or loss of the network)."""
+    test reports the wall time of each (the gain or loss of the network) and
+    fails if the network falls below x0.75 of the rule."""
     import time
     import torch
     from paper_1206_6857_gb300 import selector
@@ -196,7 +197,13 @@ def test_trained_selector_against_the_rule(gs, capsys):
             assert err.max() <= wl.eps, (wl.name, name, err.max())
             res[name] = (best, st.pairs_dh + st.pairs_dl + st.pairs_h2l, st.pairs_base)
         assert res["mlp"][1:] != res["rule"][1:]       # the network changed decisions
+        ratio = res["rule"][0] / res["mlp"][0]
         rows.append("%s: rule %.2f ms, learned %.2f ms (x%.2f)" % (wl.name, 1e3 * res["rule"][0],
-                                                                 1e3 * res["mlp"][0], res["rule"][0] / res["mlp"][0]))
+                                                                 1e3 * res["mlp"][0], ratio))
+        # the stored network is measured at x0.88-0.90 of the rule on these two
+        # problems (its H2L actions at large nodes cost more than its labels
+        # model); a drop below x0.75 is a regression of the selector or the
+        # series kernels
+        assert ratio >= 0.75, rows[-1]
     with capsys.disabled():
         print("\n" + "\n".join(rows))
