@@ -251,8 +251,9 @@ constexpr int kBlk = 8;   // bandwidths accumulated per pass
 // Shared memory per warp: Kahan sums and compensations for one block of
 // kBlk bandwidths (2 x kBlk x QPL x 32 floats), then two staging buffers of
 // lmax reference records each.  Mask bits are bandwidths in ascending h, so
-// the bandwidths a leaf pair needs sit in one or two blocks; the CTA makes one
-// pass over its entries per block of bandwidths.
+// the bandwidths a leaf pair needs are consecutive; the CTA makes one pass
+// over its entries per block of kBlk bandwidths, blocks starting at the
+// lowest bandwidth any of its entries needs.
 template <int DP, int QPL, bool ANCH>
 __global__ void __launch_bounds__(32 * kMW)
 k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const long long *__restrict__ off,
@@ -295,9 +296,23 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
     };
     const double wmax = (double)__uint_as_float(bp.ing->wmax_bits);
     unsigned long long evals = 0;
-    const int nblk = (nh + kBlk - 1) / kBlk;
+    // the blocks start at the lowest bandwidth this query leaf's entries use,
+    // so a leaf pair's (consecutive) bandwidths are split across passes only
+    // when the leaf's whole range is wider than a block
+    __shared__ uint32_t s_union[kMW];
+    uint32_t un = 0u;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) un |= ent[e].mask;
+    un = __reduce_or_sync(0xffffffffu, un);
+    if (lane == 0) s_union[w] = un;
+    __syncthreads();
+    un = 0u;
+#pragma unroll
+    for (int ww = 0; ww < kMW; ++ww) un |= s_union[ww];
+    const int b0 = __ffs(un) - 1, b1 = 31 - __clz(un);
+    const int nblk = (b1 - b0) / kBlk + 1;
     for (int jb = 0; jb < nblk; ++jb) {
-        const uint32_t bmask = 0xFFu << (kBlk * jb);
+        const int sh = b0 + kBlk * jb;     // first mask bit of this block (<= b1 <= 31)
+        const uint32_t bmask = 0xFFu << sh;
         for (int t = lane; t < 2 * KS; t += 32) ksum[t] = 0.f;
         auto next_used = [&](int64_t e) {
             while (e < e1 && !(ent[e].mask & bmask)) e += kMW;
@@ -325,7 +340,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                             ? (float)(bp.qcenter[qnode * bp.D + d] - bp.rcenter[(int64_t)E.r * bp.D + d])
                             : 0.f;
             const float *rp = stage + (size_t)buf * lmax * NS;
-            uint32_t m = (E.mask & bmask) >> (kBlk * jb);
+            uint32_t m = (E.mask & bmask) >> sh;
             evals += (unsigned long long)__popc(m) * (unsigned long long)nr;
             while (m) {
                 int ks[8];
@@ -335,7 +350,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                     const int k = __ffs(m) - 1;
                     m &= m - 1;
                     ks[nj] = k;
-                    c[nj] = bp.negc[kBlk * jb + k];
+                    c[nj] = bp.negc[sh + k];
                     ++nj;
                 }
                 float part[QPL][8];
@@ -393,7 +408,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
         for (int t = threadIdx.x; t < KS; t += blockDim.x) {
             const int k = t / (QPL * 32), s = (t / 32) % QPL, ln = t % 32;
             const int qq = ln + 32 * s;
-            const int bit = kBlk * jb + k;
+            const int bit = sh + k;
             if (qq >= nq || bit >= nh) continue;
             double v = 0.0;
             for (int ww = 0; ww < kMW; ++ww) {
