@@ -207,6 +207,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # sources of each kernel whose DRAM traffic profiles/traffic.json records
 KERNEL_SOURCES = {"k_basecase": ("gs_basemerge.cu", "gs_device.cuh"),
+                  "k_basecase_tc": ("gs_basetc.cu", "gs_tc.cuh", "gs_device.cuh"),
                   "k_exhaustive": ("gs_exhaustive.cu", "gs_device.cuh")}
 
 
@@ -320,9 +321,12 @@ def run_gs(args):
         t0 = time.perf_counter()
         # every bandwidth of the step: the merged base case handles them in
         # blocks of 8, so a subset would favour the wrong leaf size
-        tuned, _table = autotune.tune_staged(tr, tw, hs, eps, wl.D, h_subset=0, queries=None if wl.mono else tq)
+        # (a search repeats the sweep's bandwidths: tune on the distinct ones)
+        tuned, _table = autotune.tune_staged(tr, tw, np.unique(hs), eps, wl.D, h_subset=0,
+                                             queries=None if wl.mono else tq)
         tuned["tuning_seconds"] = time.perf_counter() - t0
-        tuned["candidates"] = [[r["leaf_size"], r["plimit"]] + list(r["cost_weight"]) + [round(r["seconds"] * 1e3, 1)]
+        tuned["candidates"] = [[r["leaf_size"], r["plimit"]] + list(r["cost_weight"]) +
+                               [round(r["seconds"] * 1e3, 1) if r["seconds"] != float("inf") else "out of memory"]
                                for r in _table]     # leaf, PLIMIT, c_DH, c_DL, c_H2L, c_Direct, ms
         opts = autotune.options(tuned)
 
@@ -375,8 +379,16 @@ def run_gs(args):
 
     units = float(wl.M) * wl.N * hs.size            # kernel evaluations one step stands for
     value = reps.throughput(units, ms)
-    base_ms = float(np.mean([s.ms_phase[gs.GS_PH_BASE] / max(1, s.launches_base) for s in stats_list]))
-    evals_base = float(np.mean([s.point_pairs_base / max(1, s.launches_base) for s in stats_list]))
+    # the dominant kernel: the base case (the tensor-core one when it carries
+    # the terms, timed in its own phase), or the exhaustive kernel
+    tc_terms = float(np.mean([s.point_pairs_tc for s in stats_list]))
+    use_tc = tc_terms > 0.5 * float(np.mean([s.point_pairs_base for s in stats_list]))
+    if use_tc:
+        base_ms = float(np.mean([s.ms_phase[gs.GS_PH_BASE_TC] for s in stats_list]))
+        evals_base = tc_terms
+    else:
+        base_ms = float(np.mean([s.ms_phase[gs.GS_PH_BASE] / max(1, s.launches_base) for s in stats_list]))
+        evals_base = float(np.mean([s.point_pairs_base / max(1, s.launches_base) for s in stats_list]))
     launches = int(np.mean([s.launches for s in stats_list]))
 
     # roofline: the base-case / exhaustive kernel is bound by the MUFU ex2 rate
@@ -385,7 +397,7 @@ def run_gs(args):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = ex2_rate * props.multi_processor_count * sm_mhz * 1e6 / 1e12
     achieved = evals_base / (base_ms / 1e3) / 1e12 if base_ms > 0 else None
-    kname = "k_exhaustive" if eps == 0.0 else "k_basecase"
+    kname = "k_exhaustive" if eps == 0.0 else ("k_basecase_tc" if use_tc else "k_basecase")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
             "frac": achieved / peak if (peak and achieved) else None,
             "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d" % (
@@ -511,6 +523,7 @@ def run_gs(args):
                               "per_round": SEARCH_PER_ROUND, "range": [float(wl.h[0]), float(wl.h[-1])],
                               "certified": cert["certified"], "certified_bracket": cert["bracket"],
                               "certifying_eps": cert["eps"], "certified_neighbour_distance": cert["m"],
+                              "certified_grid_round": cert.get("grid_round"),
                               "note": "roofline and stats of the search's last call"}
         if "lscv" in scores:
             sc, er = scores["lscv"]

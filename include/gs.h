@@ -111,6 +111,8 @@ typedef struct gs_opts {
 #define GS_PH_BASE      4   /* exhaustive or leaf-leaf base-case kernel (a8, a14)    */
 #define GS_PH_DOWN      5   /* downward pass and output (a9)                         */
 #define GS_PH_OTHER     6   /* everything else (e.g. LSCV reduction)                 */
+#define GS_PH_BASE_TC   7   /* the tensor-core base-case kernel (9 <= D <= 16), timed
+                               apart from the rest of GS_PH_BASE                        */
 #define GS_NPHASE       8
 
 /* Per-call counters (host struct filled by the call when non-NULL; timing

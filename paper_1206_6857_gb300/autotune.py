@@ -83,15 +83,27 @@ def tune(points, weights, h, eps, fraction=1.0, h_subset=8, leaves=DEFAULT_LEAVE
     table = []
     for leaf, cw, P in itertools.product(leaves, costs, plimits):
         o = _opts(leaf, P, cw)
-        gs.gs_sum(sub_q, sub_p, sub_w, h, eps, out=out, opts=o)          # warm
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            t0 = time.perf_counter()
-            gs.gs_sum(sub_q, sub_p, sub_w, h, eps, out=out, opts=o)
+        try:
+            gs.gs_sum(sub_q, sub_p, sub_w, h, eps, out=out, opts=o)          # warm
             torch.cuda.synchronize()
-            ts.append(time.perf_counter() - t0)
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                gs.gs_sum(sub_q, sub_p, sub_w, h, eps, out=out, opts=o)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+        except gs.GSError as err:
+            # a candidate whose work lists do not fit the device is not a
+            # configuration this problem can use: record it and go on
+            if err.code != gs.GS_ERR_OOM:
+                raise
+            gs.gs_trim_memory(0)
+            table.append({"leaf_size": leaf, "plimit": P, "cost_weight": list(cw), "seconds": float("inf"),
+                          "out_of_memory": True})
+            continue
         table.append({"leaf_size": leaf, "plimit": P, "cost_weight": list(cw), "seconds": float(min(ts))})
+    if all(r["seconds"] == float("inf") for r in table):
+        raise gs.GSError(gs.GS_ERR_OOM, "every autotuner candidate ran out of device memory")
     best = min(table, key=lambda r: r["seconds"])
     return best, table
 

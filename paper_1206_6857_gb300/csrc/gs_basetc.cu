@@ -761,8 +761,10 @@ int run_basecase_tc(const TraversalIn &in, const MergedEntry *ent, const long lo
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             const int64_t grid = lq < sms ? lq : sms;
+            cx.phase(GS_PH_BASE_TC);
             k_basecase_tc<<<(unsigned)(grid > 0 ? grid : 1), kTcWG * 128, TcSmem::TOTAL, st>>>(tp, ent_tc, cnt_tc,
                                                                                                 lq);
+            cx.phase(GS_PH_BASE);
             cx.launches += 1;
             cx.launches_base += 1;
             e = cudaGetLastError();

@@ -52,9 +52,9 @@ class gs_opts(ctypes.Structure):
                 ("selector_params", ctypes.c_void_p), ("reserved", ctypes.c_int64 * 3)]
 
 
-GS_PH_INGEST, GS_PH_TREE, GS_PH_FRONTIER, GS_PH_SERIES, GS_PH_BASE, GS_PH_DOWN, GS_PH_OTHER = range(7)
+GS_PH_INGEST, GS_PH_TREE, GS_PH_FRONTIER, GS_PH_SERIES, GS_PH_BASE, GS_PH_DOWN, GS_PH_OTHER, GS_PH_BASE_TC = range(8)
 GS_NPHASE = 8
-PHASE_NAMES = ["ingest", "tree", "frontier", "series", "base", "down", "other", "spare"]
+PHASE_NAMES = ["ingest", "tree", "frontier", "series", "base", "down", "other", "base_tc"]
 
 
 class gs_problem(ctypes.Structure):

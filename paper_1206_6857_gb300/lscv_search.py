@@ -106,8 +106,10 @@ def minimize(points, weights, eps: float, lo: float, hi: float, rounds: int = 5,
     certify_steps > 0 appends a fifth element, certify()'s record for the
     last round's grid: when the score bounds of the best grid point and its
     neighbours overlap, that grid is re-scored at eps / 4, eps / 16, ... (up
-    to certify_steps times) on the same tree until they separate; h_best,
-    score_best and err_best then come from the certifying evaluation."""
+    to certify_steps times) on the same tree until they separate, and if they
+    never do, the previous round's (coarser) grid is tried the same way;
+    h_best, score_best and err_best then come from the certifying evaluation
+    (record key grid_round: the round whose grid was certified)."""
     from . import gs
     tree = gs.Tree(points, weights, opts=opts, stream=stream)
     errs = {}
@@ -120,13 +122,20 @@ def minimize(points, weights, eps: float, lo: float, hi: float, rounds: int = 5,
             return s
         h, s, hist = search(score_fn, lo, hi, rounds, per_round)
         if certify_steps > 0:
-            hs_last, sc_last = hist[-1]
-            er_last = np.array([errs[float(v)] for v in hs_last])
-            cert = certify(lambda hs, e: gs.gs_lscv_trees(tree, hs, e, opts=opts, stream=stream, stats=stats),
-                           hs_last, eps, steps=certify_steps, scores=(sc_last, er_last))
-            if cert["certified"]:
-                h, s = cert["h"], cert["score"]
-                errs[h] = cert["bound"]
+            # the last grid first; if its neighbours are too close for the
+            # bounds, the grid of the round before (a wider bracket)
+            for back in (1, 2):
+                if back > len(hist):
+                    break
+                hs_g, sc_g = hist[-back]
+                er_g = np.array([errs[float(v)] for v in hs_g])
+                cert = certify(lambda hs, e: gs.gs_lscv_trees(tree, hs, e, opts=opts, stream=stream, stats=stats),
+                               hs_g, eps, steps=certify_steps, scores=(sc_g, er_g))
+                cert["grid_round"] = len(hist) - back
+                if cert["certified"]:
+                    h, s = cert["h"], cert["score"]
+                    errs[h] = cert["bound"]
+                    break
     finally:
         tree.close()
     if certify_steps > 0:
