@@ -640,65 +640,98 @@ __global__ void __launch_bounds__(256) k_h2l_scatter(const SeriesEntry *__restri
 // downward pass, one query level at a time: L2L of every (node, j) with a
 // local expansion into both children (Lemma 3)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSerTB) k_l2l_level(SeriesParams sp, int k) {
-    __shared__ double pw[2][kMaxDP];
+// Moving the centre of sum_b B_b u^b by delta (u -> u + delta) factors over
+// the dimensions, (u + delta)^b = prod_d (u_d + delta_d)^{b_d}, and the
+// truncation |b| < p is closed under lowering an exponent, so Lemma 3's
+// shift equals D one-dimensional shifts applied in turn.  Along dimension d
+// the coefficients of a line alpha0 + k e_d (k < n) are the coefficients of
+// a polynomial in u_d, shifted in place by repeated synthetic division:
+//   for i = 0 .. n-2, for k = n-2 down to i:  c_k += delta_d c_{k+1},
+// n (n - 1) / 2 multiply-adds per line.  One warp per (node, j); each lane
+// takes a (child, line) and copies the line into its own scratch row.
+constexpr int kL2lWarps = 4;
+constexpr int kL2lLine = 17;     // longest line (P <= 16) plus one
+__host__ __device__ inline size_t l2l_smem_per_warp(int T) { return (size_t)(2 * T + 32 * kL2lLine) * sizeof(double); }
+
+__global__ void __launch_bounds__(kL2lWarps * 32) k_l2l_level(SeriesParams sp, int k) {
+    extern __shared__ double l2l_s[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int T = sp.T, D = sp.D;
+    double *buf = l2l_s + (size_t)w * (2 * T + 32 * kL2lLine);
+    double *line = buf + 2 * T + lane;          // this lane's scratch, stride 32
     const int64_t nn = 1ll << k;
     const int64_t items = nn * sp.nh;
-    const int D = sp.D;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t warps = (int64_t)gridDim.x * kL2lWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kL2lWarps + w; it < items; it += warps) {
         const int64_t node = nn - 1 + it / sp.nh;
         const int j = (int)(it % sp.nh);
         const int pl = sp.pL[node * sp.nh + j];
         if (pl == 0) continue;
         const int Tp = sp.tb.Tp[pl];
         const double is = sp.inv_s[j];
-        const double *Bp = sp.B + (node * sp.nh + j) * sp.T;
-        __syncthreads();
-        for (int t = threadIdx.x; t < 2 * D; t += blockDim.x) {
-            const int c = t / D, d = t % D;
-            const int64_t ch = 2 * node + 1 + c;
-            const double dl = (sp.qcenter[ch * D + d] - sp.qcenter[node * D + d]) * is;
-            double v = 1.0;
-            for (int q = 0; q < pl; ++q) {
-                pw[c][d * pl + q] = v;
-                v *= dl;
-            }
+        const double *Bp = sp.B + (node * sp.nh + j) * T;
+        for (int a = lane; a < Tp; a += 32) {
+            const double b = Bp[a];
+            buf[a] = b;
+            buf[T + a] = b;
         }
-        __syncthreads();
+        __syncwarp();
+        for (int d = 0; d < D; ++d) {
+            const double cp = sp.qcenter[node * D + d];
+            const double dl0 = (sp.qcenter[(2 * node + 1) * D + d] - cp) * is;
+            const double dl1 = (sp.qcenter[(2 * node + 2) * D + d] - cp) * is;
+            const int nl = sp.tb.l2s_nlines[d * 17 + pl];
+            const int32_t *starts = sp.tb.l2s_line + (size_t)d * T;
+            const int32_t *nxt = sp.tb.l2s_next + (size_t)d * T;
+            for (int v = lane; v < 2 * nl; v += 32) {
+                const int c = v >= nl;
+                const int a0 = starts[v - c * nl];
+                const int n = pl - sp.tb.deg[a0];
+                if (n < 2) continue;
+                double *bc = buf + c * T;
+                const double dl = c ? dl1 : dl0;
+                int a = a0;
+                for (int i = 0; i < n; ++i) {
+                    line[32 * i] = bc[a];
+                    a = nxt[a];
+                }
+                for (int i = 0; i + 1 < n; ++i)
+                    for (int q = n - 2; q >= i; --q) line[32 * q] = fma(dl, line[32 * (q + 1)], line[32 * q]);
+                a = a0;
+                for (int i = 0; i < n; ++i) {
+                    bc[a] = line[32 * i];
+                    a = nxt[a];
+                }
+            }
+            __syncwarp();
+        }
         for (int c = 0; c < 2; ++c) {
             const int64_t ch = 2 * node + 1 + c;
-            double *Bc = sp.B + (ch * sp.nh + j) * sp.T;
-            for (int a = threadIdx.x; a < Tp; a += blockDim.x) {
-                double s = 0.0;
-                for (int e2 = sp.tb.l2l_off[a]; e2 < sp.tb.l2l_off[a + 1]; ++e2) {
-                    const int bt = sp.tb.l2l_pairs[2 * e2], dt = sp.tb.l2l_pairs[2 * e2 + 1];
-                    if (bt >= Tp) continue;
-                    const uint8_t *de = sp.tb.alpha + dt * D;
-                    double m = sp.tb.l2l_coef[e2] * Bp[bt];
-                    for (int d = 0; d < D; ++d) m *= pw[c][d * pl + de[d]];
-                    s += m;
-                }
-                Bc[a] += s;
-            }
-            if (threadIdx.x == 0) {
+            double *Bc = sp.B + (ch * sp.nh + j) * T;
+            for (int a = lane; a < Tp; a += 32) Bc[a] += buf[c * T + a];
+            if (lane == 0) {
                 int32_t *pc = &sp.pL[ch * sp.nh + j];
                 if (*pc < pl) *pc = pl;
             }
         }
+        __syncwarp();
     }
 }
 
 // leaves: out = base + DH + sum of ancestors' FD estimates + EVALL(B)
 // Final values, one warp per (query leaf, bandwidth).  Local expansions of
-// at most kFinLane terms (D <= 16) are evaluated one query per lane: the
-// monomials u^a, u = (x_q - x_Q)/s, are built in graded-lex order from the
-// monomial with the last exponent one lower (one multiply each) in a
-// lane-interleaved shared buffer.  Longer expansions: lanes over the terms,
-// one query at a time.
+// at most kFinLane terms are evaluated one query per lane, u = (x_q - x_Q)/s,
+// by Horner's rule on the tree that links each multi-index a to dpred(a) (a
+// with its last non-zero exponent lowered by one, always earlier in the
+// graded order): S(a) = B_a + sum over the children c of u_{dim(c)} S(c), so
+// that S(0) = sum_a B_a u^a.  Walking the terms from the last to the first,
+// each one is final when reached and adds u_{dim(a)} S(a) into its parent:
+// one multiply-add per term, in a lane-interleaved shared buffer.  Longer
+// expansions: lanes over the terms, one query at a time.
 constexpr int kFinLane = 64;
 constexpr size_t kFinSmemPerWarp = (size_t)(kFinLane * 32 + 32 * 32) * sizeof(double);
 __global__ void __launch_bounds__(kSerTB) k_final(SeriesParams sp) {
-    extern __shared__ double fin_s[];   // per warp: monomials [kFinLane][32 lanes], u [32 dims][32 lanes]
+    extern __shared__ double fin_s[];   // per warp: partial sums S [kFinLane][32 lanes], u [32 dims][32 lanes]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int depth = sp.q_depth, D = sp.D;
     const int64_t nl = 1ll << depth;
@@ -718,22 +751,20 @@ __global__ void __launch_bounds__(kSerTB) k_final(SeriesParams sp) {
         const double is = sp.inv_s[j];
         const double *Bl = sp.B ? sp.B + (leaf * sp.nh + j) * sp.T : nullptr;
         const int64_t b = level_begin(sp.qn, depth, i), e = level_begin(sp.qn, depth, i + 1);
-        double *mono = fin_s + (size_t)w * (kFinLane * 32 + 32 * 32) + lane;
-        double *uw = mono - lane + kFinLane * 32;     // this warp's u region
+        double *acc = fin_s + (size_t)w * (kFinLane * 32 + 32 * 32) + lane;
+        double *uw = acc - lane + kFinLane * 32;      // this warp's u region
         if (Tp <= kFinLane) {
             const double *cQ = sp.qcenter + leaf * D;
             for (int64_t pos = b + lane; pos < e; pos += 32) {
                 double v = sp.Gq[pos * sp.nh + j] + es;
                 if (Tp > 0) {
                     for (int d = 0; d < D; ++d) uw[d * 32 + lane] = (coord(sp.qxs, sp.dtype, pos, D, d) - cQ[d]) * is;
-                    double s = Bl[0];
-                    mono[0] = 1.0;
-                    for (int a = 1; a < Tp; ++a) {
-                        const double m = mono[sp.tb.dpred[a] * 32] * uw[sp.tb.pred_dim[a] * 32 + lane];
-                        mono[a * 32] = m;
-                        s += Bl[a] * m;
+                    for (int a = 0; a < Tp; ++a) acc[a * 32] = Bl[a];
+                    for (int a = Tp - 1; a >= 1; --a) {
+                        double *pa = acc + sp.tb.dpred[a] * 32;
+                        *pa = fma(uw[sp.tb.pred_dim[a] * 32 + lane], acc[a * 32], *pa);
                     }
-                    v += s;
+                    v += acc[0];
                 }
                 sp.out[(int64_t)sp.qperm[pos] * sp.nh + j] = v;
             }
@@ -894,9 +925,17 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
         free_pieces();
         if (rc) return rc;
         cx.phase(GS_PH_DOWN);
+        const size_t l2l_sm = kL2lWarps * l2l_smem_per_warp(sp.T);
+        if (in.qt->depth > 0 && l2l_sm > 220 * 1024) {
+            set_error("series order too high for the L2L kernel (D=%d, P=%d)", sp.D, sp.P);
+            return GS_ERR_ARG;
+        }
+        allow_max_smem((const void *)k_l2l_level);
         for (int k = 0; k < in.qt->depth; ++k) {
-            const int64_t items = (1ll << k) * in.nh;
-            k_l2l_level<<<(unsigned)(items < 65535 ? items : 65535), kSerTB, 0, st>>>(sp, k);
+            const int64_t warps = (1ll << k) * in.nh;
+            const int64_t blocks = (warps + kL2lWarps - 1) / kL2lWarps;
+            const int64_t mx = fb.grid_warps / kL2lWarps;
+            k_l2l_level<<<(unsigned)(blocks < mx ? blocks : mx), kL2lWarps * 32, l2l_sm, st>>>(sp, k);
             cx.launches += 1;
             if ((rc = cx.check("k_l2l_level"))) return rc;
         }

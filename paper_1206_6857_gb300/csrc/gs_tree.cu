@@ -538,10 +538,9 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
     std::vector<uint8_t> alpha(T * D), deg(T), pdim(T);
     std::vector<int32_t> pred(T), dpred(T);
     std::vector<double> invf(T);
-    std::vector<int32_t> hoff(T + 1), hp, loff(T + 1), lp;
-    std::vector<double> lc;
+    std::vector<int32_t> hoff(T + 1), hp;
+    std::vector<int32_t> snext((size_t)D * T, -1), sline((size_t)D * T, 0), snl((size_t)D * 17, 0);
     auto fact = [](int m) { double f = 1.0; for (int q = 2; q <= m; ++q) f *= q; return f; };
-    auto binom = [&](int a, int b) { return fact(a) / (fact(b) * fact(a - b)); };
     for (int i = 0; i < T; ++i) {
         int dg = 0, last = -1;
         double f = 1.0;
@@ -582,30 +581,28 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
         }
     }
     hoff[T] = (int32_t)(hp.size() / 2);
-    for (int a = 0; a < T; ++a) {
-        loff[a] = (int32_t)(lp.size() / 2);
-        for (int b = 0; b < T; ++b) {
-            bool ge = true;
-            std::vector<int> df(D);
-            double c = 1.0;
-            for (int d = 0; d < D; ++d) {
-                if (al[b][d] < al[a][d]) ge = false;
-                df[d] = al[b][d] - al[a][d];
+    // separable L2L: successor along each dimension and the line starts
+    for (int d = 0; d < D; ++d) {
+        int n = 0;
+        for (int a = 0; a < T; ++a) {
+            if ((int)deg[a] + 1 < P) {
+                std::vector<int> b = al[a];
+                b[d] += 1;
+                snext[(size_t)d * T + a] = index[b];
             }
-            if (!ge) continue;
-            for (int d = 0; d < D; ++d) c *= binom(al[b][d], al[a][d]);
-            lp.push_back(b);
-            lp.push_back(index[df]);
-            lc.push_back(c);
+            if (al[a][d] == 0) {
+                sline[(size_t)d * T + n++] = a;
+                for (int p = deg[a] + 1; p <= 16; ++p) snl[d * 17 + p]++;
+            }
         }
     }
-    loff[T] = (int32_t)(lp.size() / 2);
     // one device allocation, 8-byte aligned sections
     auto al8 = [](size_t b) { return (b + 7) & ~(size_t)7; };
     size_t o_alpha = 0, o_deg = al8(o_alpha + alpha.size()), o_pdim = al8(o_deg + T), o_pred = al8(o_pdim + T);
     size_t o_invf = al8(o_pred + 4 * T), o_hoff = al8(o_invf + 8 * T), o_hp = al8(o_hoff + 4 * (T + 1));
-    size_t o_loff = al8(o_hp + 4 * hp.size()), o_lp = al8(o_loff + 4 * (T + 1)), o_lc = al8(o_lp + 4 * lp.size());
-    size_t o_dpred = al8(o_lc + 8 * lc.size());
+    size_t o_snext = al8(o_hp + 4 * hp.size()), o_sline = al8(o_snext + 4 * snext.size());
+    size_t o_snl = al8(o_sline + 4 * sline.size());
+    size_t o_dpred = al8(o_snl + 4 * snl.size());
     size_t total = al8(o_dpred + 4 * T);
     std::vector<uint8_t> host(total, 0);
     memcpy(&host[o_alpha], alpha.data(), alpha.size());
@@ -615,9 +612,9 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
     memcpy(&host[o_invf], invf.data(), 8 * T);
     memcpy(&host[o_hoff], hoff.data(), 4 * (T + 1));
     if (!hp.empty()) memcpy(&host[o_hp], hp.data(), 4 * hp.size());
-    memcpy(&host[o_loff], loff.data(), 4 * (T + 1));
-    if (!lp.empty()) memcpy(&host[o_lp], lp.data(), 4 * lp.size());
-    if (!lc.empty()) memcpy(&host[o_lc], lc.data(), 8 * lc.size());
+    memcpy(&host[o_snext], snext.data(), 4 * snext.size());
+    memcpy(&host[o_sline], sline.data(), 4 * sline.size());
+    memcpy(&host[o_snl], snl.data(), 4 * snl.size());
     memcpy(&host[o_dpred], dpred.data(), 4 * T);
     uint8_t *dm = nullptr;
     GS_CUDA_TRY(cudaMalloc((void **)&dm, total));   // cached for the life of the process
@@ -634,9 +631,9 @@ static int make_series_tables(int D, int P, SeriesTables *tb) {
     h.inv_fact = (double *)(dm + o_invf);
     h.h2h_off = (int32_t *)(dm + o_hoff);
     h.h2h_pairs = (int32_t *)(dm + o_hp);
-    h.l2l_off = (int32_t *)(dm + o_loff);
-    h.l2l_pairs = (int32_t *)(dm + o_lp);
-    h.l2l_coef = (double *)(dm + o_lc);
+    h.l2s_next = (int32_t *)(dm + o_snext);
+    h.l2s_line = (int32_t *)(dm + o_sline);
+    h.l2s_nlines = (int32_t *)(dm + o_snl);
     h.dpred = (int32_t *)(dm + o_dpred);
     *tb = h;
     return GS_OK;

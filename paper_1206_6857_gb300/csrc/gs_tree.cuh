@@ -47,11 +47,11 @@ struct SeriesTables {
     // H2H: for each gamma, the (alpha, beta) index pairs with alpha + beta = gamma
     int32_t *h2h_off = nullptr;        // T + 1
     int32_t *h2h_pairs = nullptr;      // 2 per entry
-    // L2L: for each alpha, the (beta, beta - alpha) pairs with beta >= alpha and
-    // the binomial product prod_d C(beta_d, alpha_d)
-    int32_t *l2l_off = nullptr;        // T + 1
-    int32_t *l2l_pairs = nullptr;      // 2 per entry
-    double *l2l_coef = nullptr;
+    // L2L one dimension at a time: the multi-indices along dimension d form
+    // lines alpha0, alpha0 + e_d, alpha0 + 2 e_d, ... (alpha0_d = 0)
+    int32_t *l2s_next = nullptr;       // D x T: index of alpha + e_d (-1 past order P)
+    int32_t *l2s_line = nullptr;       // D x T: the line starts alpha0 of dimension d, in table order
+    int32_t *l2s_nlines = nullptr;     // D x 17: lines of dimension d whose start has degree < p
     void *mem = nullptr;               // single device allocation holding all of the above
 };
 
