@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--selector", default="rule", choices=["rule", "mlp", "fd_only"],
                     help="pair selector: Fig. 6's rule, the stored learned network, or FD pruning only "
                          "(the paper's DFD/DFDO comparison: no series approximations)")
+    ap.add_argument("--best-first", action="store_true",
+                    help="ablation: best-first look-ahead of each group's largest bound gaps (GS_FLAG_BEST_FIRST)")
     ap.add_argument("--no-tokens", action="store_true",
                     help="Theorem 2 without the token scheme (each pair within its own W_R share)")
     ap.add_argument("--count", type=int, default=256, help="problems in --mode batch")
@@ -334,6 +336,7 @@ def run_gs(args):
     if tuned is not None:
         tuned["selector"] = args.selector
         tuned["tokens"] = not args.no_tokens
+        tuned["best_first"] = bool(args.best_first)
 
     def step(stats=None):
         if args.mode == "search":
@@ -540,9 +543,11 @@ def selector_opts(args, opts):
     """Options for --selector (the stored learned network for mlp, FD
     pruning only for fd_only) and --no-tokens."""
     from paper_1206_6857_gb300 import gs
-    if args.selector == "rule" and not args.no_tokens:
+    if args.selector == "rule" and not args.no_tokens and not args.best_first:
         return opts, None
     o = opts if opts is not None else gs.gs_opts_default()
+    if args.best_first:
+        o.flags |= gs.GS_FLAG_BEST_FIRST
     if args.no_tokens:
         o.no_tokens = 1
     if args.selector == "fd_only":

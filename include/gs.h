@@ -94,6 +94,14 @@ typedef struct gs_opts {
 #define GS_FLAG_NO_TC 4     /* 9 <= D <= 16: no tensor-core base case (every leaf pair summed
                                by the direct FP32 kernel; the FP32 charge drops its extra
                                tensor-core term)                                         */
+#define GS_FLAG_BEST_FIRST 8 /* best-first ordering inside each frontier level (the
+                               priority-queue traversal of Section 1, ordered by bound
+                               gap): in every (query node, bandwidth) group the pairs whose
+                               gap W_R (K(delta_min) - K(delta_max)) is at least 1/8 of the
+                               group's total are expanded one level on the reference side
+                               before the group's decisions, and their children's lower
+                               bound replaces theirs in G^min when larger.  Same eps
+                               guarantee; an ablation, off by default                    */
 
 /* Default cost weights: a series action runs in FP64 on the GPU while a
  * direct (base-case) term is an FP32 exponential, so on GB300 one unit of

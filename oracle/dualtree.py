@@ -364,6 +364,7 @@ class Traversal:
     rho: float = 0.0
     W: float = 0.0
     consulted: int = 0          # pairs scored by the selector network
+    lookahead: int = 0          # pairs expanded ahead by the best-first ordering
 
 
 COST_WEIGHTS = (32.0, 32.0, 32.0, 1.0)
@@ -412,7 +413,8 @@ def _argmax_certified(scores, certified):
 
 def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None = None,
              selector: int = SEL_RULE, tokens: bool = True, floor_log2: int = -40,
-             w_max: float = None, cost_weight=COST_WEIGHTS, mlp_params=None, no_tc: bool = False):
+             w_max: float = None, cost_weight=COST_WEIGHTS, mlp_params=None, no_tc: bool = False,
+             best_first: bool = False):
     """Run the level-synchronous traversal; returns a Traversal whose iters[t]
     holds the frontier (q, r, j) and the decision (method, p, E) of every
     pair in the exact order the GPU processes them.
@@ -425,7 +427,15 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
     series method and whose N_Q N_R is at least MLP_MIN_WORK take the
     highest-scoring certified action of the selector network (mlp_params,
     oracle.mlp layout; ties: lowest action), split / base case counting as
-    always certified; smaller such pairs keep the rule's choice."""
+    always certified; smaller such pairs keep the rule's choice.
+
+    best_first: the best-first ordering of Section 1's priority-queue
+    traversal, restricted to one level: in each (j, Q) group, the pairs whose
+    bound gap W_R (K(delta_min) - K(delta_max)) is at least 1/8 of the group's
+    total gap (the ones a queue ordered by gap pops first) are expanded on the
+    reference side before the group is decided; the children's lower bound
+    W_R1 K(delta_max(Q, R1)) + W_R2 K(delta_max(Q, R2)) replaces the pair's
+    own in G^min (and in the finished lower bound) when it is larger."""
     kw = [float(v) for v in cost_weight]
     h = np.asarray(h, np.float64)
     nh = h.size
@@ -482,6 +492,19 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
         WR = rt.W[pr]
         # the lower bound sum and the weight sum in FP32, rounded down and up
         dl32 = f32_mul_dir(rt.W32d[pr], kmax32, up=False)
+        if best_first and not r_leaf:
+            # gaps rounded to nearest in FP32, their group sum rounded up
+            gap32 = rt.W32u[pr] * (kmin32 - kmax32)
+            gtot = group_reduce_f32(gap32, gid, pos, ng, up=True).astype(np.float32)
+            sel = np.flatnonzero((gap32 > 0) & (gap32 * np.float32(8.0) >= gtot[gid]))
+            if sel.size:
+                r1, r2 = 2 * pr[sel] + 1, 2 * pr[sel] + 2
+                k1 = kernel_bounds(qt, rt, pq[sel], r1, c32[pj[sel]])[0]
+                k2 = kernel_bounds(qt, rt, pq[sel], r2, c32[pj[sel]])[0]
+                lc = f32_add_dir(f32_mul_dir(rt.W32d[r1], k1, up=False), f32_mul_dir(rt.W32d[r2], k2, up=False),
+                                 up=False)
+                dl32[sel] = np.maximum(dl32[sel], lc)
+            out.lookahead += sel.size
         front = group_reduce_f32(dl32, gid, pos, ng, up=False)
         Wg = group_reduce_f32(rt.W32u[pr], gid, pos, ng, up=True)
         G = fin[gq, gj] + front

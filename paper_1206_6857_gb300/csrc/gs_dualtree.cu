@@ -78,8 +78,8 @@ static int alloc_bufs(FrontierBufs &fb, int64_t nodesQ, int nh, const double *h,
     }
     fb.cap_pairs = initial;
     GS_ALLOC(fb.dec, initial);
-    fb.cap_geo = 3 * initial;
-    GS_ALLOC(fb.geo, 3 * initial * sizeof(float));
+    fb.cap_geo = 4 * initial;
+    GS_ALLOC(fb.geo, 4 * initial * sizeof(float));
     GS_ALLOC(fb.cnt, fb.cap_groups * kCols * sizeof(int32_t));
     GS_ALLOC(fb.off, fb.cap_groups * kCols * sizeof(long long));
     GS_ALLOC(fb.partial, kCols * 256 * sizeof(long long));

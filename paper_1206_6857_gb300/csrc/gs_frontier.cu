@@ -116,6 +116,7 @@ __device__ __forceinline__ float warp_sum_ru(float v) {
 
 struct FrontierParams {
     int D, nh, P, selector, tokens, mono;
+    int best_first;       // look-ahead of each group's largest bound gaps (GS_FLAG_BEST_FIRST)
     int t, q_depth, r_depth, q_leaf, r_leaf;
     int floor_log2;
     int64_t qn, rn;
@@ -127,7 +128,8 @@ struct FrontierParams {
     const float *rW32d, *rW32u;   // reference weight sums rounded down / up to FP32
     const double *inv_h;
     double *fin, *tok, *est;
-    float *geo;           // per pair cache: K(delta_max) lower, K(delta_min) upper, e^{-dmin^2/4h^2} upper
+    float *geo;           // per pair cache: K(delta_max) lower, K(delta_min) upper, e^{-dmin^2/4h^2} upper,
+                          // the pair's lower bound of its kernel sum (W_R K(delta_max) or the look-ahead's)
     double F[17], BT[17], Dpow[34];
     double cw[4];         // cost weights of c_DH, c_DL, c_H2L, c_Direct
     // weighted bestMethod costs of this iteration, for node sizes floor(n / 2^depth) + {0, 1}
@@ -150,6 +152,11 @@ __device__ __forceinline__ int64_t node_size(int64_t n, int depth, int64_t node)
 
 // floats per warp of the per-group screen tables (4 x 17)
 constexpr int kTab = 68;
+// Best-first look-ahead: a pair whose bound gap W_R (K(delta_min) - K(delta_max))
+// is at least 1 / kBestFirst of its group's total gap (so at most kBestFirst
+// pairs per group, the largest gaps) contributes the lower bound of its
+// reference node's two children to G^min when that is larger.
+constexpr float kBestFirst = 8.f;
 static_assert(sizeof(FrontierParams) <= 4096, "kernel parameters above 4 KB");
 
 struct KBounds {
@@ -216,15 +223,52 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         // the token is shared by, from W_R rounded up): a smaller lower bound
         // and a larger weight sum keep every budget valid.
         float s_dl = 0.f, s_W = 0.f;
-        for (int k = lane; k < G.cnt; k += 32) {
-            const int64_t r = pr[G.off + k];
-            const KBounds kb = kernel_bounds(fp, q, r, c32);
-            float *gc = fp.geo + 3 * (G.off + k);
-            gc[0] = kb.kmax;
-            gc[1] = kb.kmin;
-            gc[2] = kb.e4;
-            s_dl = __fadd_rd(s_dl, __fmul_rd(fp.rW32d[r], kb.kmax));
-            s_W = __fadd_ru(s_W, fp.rW32u[r]);
+        if (fp.best_first && !fp.r_leaf) {
+            // Best-first ordering within the group: the pairs with the largest
+            // bound gaps (those a priority queue on the gap would expand first)
+            // are expanded one level on the reference side before any decision,
+            // and the lower bound of the two children,
+            //   W_R1 K(delta_max(Q, R1)) + W_R2 K(delta_max(Q, R2)) >= W_R K(delta_max(Q, R)),
+            // replaces the pair's own in G^min.  Gaps in FP32 rounded to nearest,
+            // their group sum rounded up; the selection only has to be
+            // reproducible, every lower bound stays rigorous.
+            float s_gap = 0.f;
+            for (int k = lane; k < G.cnt; k += 32) {
+                const int64_t r = pr[G.off + k];
+                const KBounds kb = kernel_bounds(fp, q, r, c32);
+                float *gc = fp.geo + 4 * (G.off + k);
+                gc[0] = kb.kmax;
+                gc[1] = kb.kmin;
+                gc[2] = kb.e4;
+                s_gap = __fadd_ru(s_gap, __fmul_rn(fp.rW32u[r], __fsub_rn(kb.kmin, kb.kmax)));
+                s_W = __fadd_ru(s_W, fp.rW32u[r]);
+            }
+            const float gap_tot = warp_sum_ru(s_gap);
+            for (int k = lane; k < G.cnt; k += 32) {
+                const int64_t r = pr[G.off + k];
+                float *gc = fp.geo + 4 * (G.off + k);
+                const float kmax = gc[0];
+                float dl = __fmul_rd(fp.rW32d[r], kmax);
+                const float gap = __fmul_rn(fp.rW32u[r], __fsub_rn(gc[1], kmax));
+                if (gap > 0.f && __fmul_rn(gap, kBestFirst) >= gap_tot) {
+                    const int64_t r1 = 2 * r + 1, r2 = 2 * r + 2;
+                    const float k1 = kernel_bounds(fp, q, r1, c32).kmax;
+                    const float k2 = kernel_bounds(fp, q, r2, c32).kmax;
+                    dl = fmaxf(dl, __fadd_rd(__fmul_rd(fp.rW32d[r1], k1), __fmul_rd(fp.rW32d[r2], k2)));
+                }
+                gc[3] = dl;
+                s_dl = __fadd_rd(s_dl, dl);
+            }
+        } else {
+            for (int k = lane; k < G.cnt; k += 32) {
+                const int64_t r = pr[G.off + k];
+                const KBounds kb = kernel_bounds(fp, q, r, c32);
+                float *gc = fp.geo + 4 * (G.off + k);
+                const float dl = __fmul_rd(fp.rW32d[r], kb.kmax);
+                *reinterpret_cast<float4 *>(gc) = make_float4(kb.kmax, kb.kmin, kb.e4, dl);
+                s_dl = __fadd_rd(s_dl, dl);
+                s_W = __fadd_ru(s_W, fp.rW32u[r]);
+            }
         }
         const float front32 = warp_sum_rd(s_dl), Wg32 = warp_sum_ru(s_W);
         const int64_t qj = q * fp.nh + j;
@@ -311,9 +355,9 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
         const int iq = (int)(cq - (fp.qn >> fp.q_depth));
         for (int k = lane; k < G.cnt; k += 32) {
             const int64_t r = pr[G.off + k];
-            const float *gc = fp.geo + 3 * (G.off + k);
-            const float kmax32 = gc[0], kmin32 = gc[1];
-            const float e4f = gc[2];
+            const float4 gc = *reinterpret_cast<const float4 *>(fp.geo + 4 * (G.off + k));
+            const float kmax32 = gc.x, kmin32 = gc.y;
+            const float e4f = gc.z;
             const double WR = fp.rW[r];
             int method = (fp.q_leaf && fp.r_leaf) ? M_BASE : M_SPLIT;
             int pord = 0;
@@ -502,8 +546,7 @@ k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ g
             if (method == M_FD || (method >= M_DH && method <= M_H2L)) s_paid = s_paid + spent;
             if (method == M_BASE) s_bank = __fadd_rd(s_bank, fp.rW32d[r]);
             // at a leaf-leaf iteration no pair splits, so this sum equals pass 1's s_dl
-            if (method != M_SPLIT && !(fp.q_leaf && fp.r_leaf))
-                s_fin = __fadd_rd(s_fin, __fmul_rd(fp.rW32d[r], kmax32));
+            if (method != M_SPLIT && !(fp.q_leaf && fp.r_leaf)) s_fin = __fadd_rd(s_fin, gc.w);
             n_fd += method == M_FD;
             n_dh += method == M_DH;
             n_dl += method == M_DL;
@@ -860,6 +903,7 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.selector = in.selector;
     fp.tokens = in.tokens;
     fp.mono = in.mono;
+    fp.best_first = (in.flags & GS_FLAG_BEST_FIRST) != 0;
     fp.floor_log2 = in.floor_log2;
     fp.qn = in.qt->n;
     fp.rn = in.rt->n;
@@ -923,7 +967,7 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         for (int p = 1; p <= 16 && p <= in.P; ++p) fp.cH2L[p] = fp.Dpow[2 * p + 1] * fp.cw[2];
         // this iteration's per-pair arrays
         if ((rc = grow(&fb.dec, &fb.cap_pairs, npairs, 0, st))) return rc;
-        if ((rc = grow(&fb.geo, &fb.cap_geo, 3 * npairs, 0, st))) return rc;
+        if ((rc = grow(&fb.geo, &fb.cap_geo, 4 * npairs, 0, st))) return rc;
         fp.geo = fb.geo;
         PairLog *lg = in.log;
         if (lg) {

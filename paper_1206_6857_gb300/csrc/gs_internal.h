@@ -212,7 +212,7 @@ struct FrontierBufs {
     Group *base_groups = nullptr;
     int32_t *base_r = nullptr;
     SeriesEntry *series[3] = {nullptr, nullptr, nullptr};   // DH, DL, H2L action lists
-    float *geo = nullptr;           // per pair: kernel bounds K(delta_max), K(delta_min), e^{-dmin^2/4h^2}
+    float *geo = nullptr;           // per pair (4 floats): K(delta_max), K(delta_min), e^{-dmin^2/4h^2}, lower bound
     double *fin = nullptr, *tok = nullptr, *est = nullptr;
     double *inv_2h2 = nullptr, *inv_4h2 = nullptr, *inv_h = nullptr, *inv_s = nullptr;
     unsigned long long *evals = nullptr;

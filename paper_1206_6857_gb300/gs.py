@@ -37,6 +37,7 @@ GS_COST_DEFAULT = (32.0, 32.0, 32.0, 1.0)     # c_DH, c_DL, c_H2L, c_Direct weig
 GS_FLAG_NO_MERGE = 1
 GS_FLAG_SMALL_EXHAUSTIVE = 2
 GS_FLAG_NO_TC = 4
+GS_FLAG_BEST_FIRST = 8
 GS_SMALL_WORK = 549755813888.0
 
 GS_MLP_NIN = 12

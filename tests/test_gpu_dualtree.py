@@ -48,11 +48,11 @@ def _opts(gs, leaf=32, selector=0, tokens=True, plimit=0, cw=None):
     return o
 
 
-def _cpu_trace(q, r, w, mono, h, eps, leaf, selector, tokens, plimit, cw):
+def _cpu_trace(q, r, w, mono, h, eps, leaf, selector, tokens, plimit, cw, best_first=False):
     rt = T.build_tree(r, w, leaf)
     qt = rt if mono else T.build_tree(q, np.ones(q.shape[0], np.float32), leaf)
     trav = T.traverse(qt, rt, mono, h, eps, plimit=plimit or None, selector=selector, tokens=tokens,
-                      w_max=float(w.max()), cost_weight=cw)
+                      w_max=float(w.max()), cost_weight=cw, best_first=best_first)
     rec = []
     for t, it in enumerate(trav.iters):
         code = it["method"] | (it["p"] << 8) | (t << 16)
@@ -78,16 +78,20 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_n%d_d%d" % (c[0], c[1], c[2]))
-def test_traversal_bit_exact_and_within_eps(gs, case):
+def _bit_exact_case(gs, case, best_first=False):
     seed, n, D, m, eps, leaf, sel, tok, plim, h, cw = case
     q, r, w = synth.small_random(seed, n, D, m=m)
     mono = m is None
     h = np.asarray(h, np.float64)
     tq = _dev(q)
     tr = tq if mono else _dev(r)
-    out, trace, qperm, rperm = gs.gs_sum_trace(tq, tr, _dev(w), h, eps, opts=_opts(gs, leaf, sel, tok, plim, cw))
-    qt, rt, want, trav = _cpu_trace(q, r, w, mono, h, eps, leaf, sel, tok, plim, cw)
+    o = _opts(gs, leaf, sel, tok, plim, cw)
+    if best_first:
+        o.flags = gs.GS_FLAG_BEST_FIRST
+    out, trace, qperm, rperm = gs.gs_sum_trace(tq, tr, _dev(w), h, eps, opts=o)
+    qt, rt, want, trav = _cpu_trace(q, r, w, mono, h, eps, leaf, sel, tok, plim, cw, best_first)
+    if best_first:
+        assert trav.lookahead > 0
     assert np.array_equal(rperm.cpu().numpy(), rt.perm)
     assert np.array_equal(qperm.cpu().numpy(), qt.perm)
     got = trace.cpu().numpy().astype(np.int64)
@@ -97,6 +101,19 @@ def test_traversal_bit_exact_and_within_eps(gs, case):
     exact = oracle_ex.gauss_sum(q, r, w, h)
     err = rel_err(out.cpu().numpy(), exact, float(w.astype(np.float64).sum()))
     assert err.max() <= eps, err.max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_n%d_d%d" % (c[0], c[1], c[2]))
+def test_traversal_bit_exact_and_within_eps(gs, case):
+    _bit_exact_case(gs, case)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] in (1, 2, 3, 6, 11)],
+                         ids=lambda c: "s%d_n%d_d%d" % (c[0], c[1], c[2]))
+def test_best_first_traversal_bit_exact_and_within_eps(gs, case):
+    """GS_FLAG_BEST_FIRST: the look-ahead of the largest-gap pairs of every
+    group, bit-exact against the CPU traversal with best_first=True."""
+    _bit_exact_case(gs, case, best_first=True)
 
 
 def _check_eps(gs, wl, eps=None, opts=None, sample=None):

@@ -162,6 +162,39 @@ def test_estimate_within_eps_and_theorem2_invariant(D, n, m, eps, tokens):
     assert (methods == T.FD).any() and (methods == T.BASE).any()
 
 
+@pytest.mark.parametrize("D,m,tokens", [(2, None, True), (3, None, True), (3, 700, True), (2, None, False)])
+def test_best_first_lower_bounds_hold_and_estimate_within_eps(D, m, tokens):
+    """Best-first look-ahead: every group's G^min (with the children's lower
+    bounds of the largest-gap pairs) is still below the exact sum of every
+    query of its node (or the floor / the self term that raised it), and the
+    estimate keeps Theorem 2's guarantee."""
+    q, r, w, mono = _problem(50 + D, 1200, D, m)
+    qt, rt = _trees(q, r, w, mono, 16)
+    h = synth.log_bandwidths(synth.bbox_diagonal(r), 6, 1e-3, 1.0)
+    eps = 1e-2
+    trav = T.traverse(qt, rt, mono, h, eps, tokens=tokens, w_max=float(w.max()), best_first=True)
+    assert trav.lookahead > 0
+    want = oracle_ex.gauss_sum(q, r, w, h)
+    W = float(np.sum(w.astype(np.float64)))
+    floorW = 2.0 ** -40 * W
+    # exact minimum over the queries of each query node, per bandwidth
+    sorted_want = want[qt.perm]
+    for it in trav.iters:
+        qs, js, G = it["q"], it["j"], it["G"]
+        mins = np.array([sorted_want[qt.begin[a]:qt.end[a], b].min() for a, b in zip(qs, js)])
+        lower = np.maximum(mins, floorW)
+        if mono:
+            lower = np.maximum(lower, qt.wmin[qs])
+        assert np.all(G <= lower * (1 + 1e-9))
+    got, charged = T.estimate(qt, rt, q, r, w, h, trav)
+    den = np.maximum(want, floorW)
+    assert np.all(charged <= trav.eps_t * den * (1 + 1e-9))
+    assert np.max(np.abs(got - want) / den) <= trav.eps_t * (1 + 1e-6)
+    # the look-ahead can only raise a pair's lower bound: same first iteration, G^min at least as large
+    plain = T.traverse(qt, rt, mono, h, eps, tokens=tokens, w_max=float(w.max()))
+    assert np.all(trav.iters[0]["G"] >= plain.iters[0]["G"])
+
+
 def test_series_methods_are_used_in_low_dimension():
     q, r, w, mono = _problem(40, 3000, 2)
     qt, rt = _trees(q, r, w, mono, 16)
