@@ -168,34 +168,6 @@ __device__ __forceinline__ void leaf_terms(const float (&xq)[QPL][DP], const flo
     }
 }
 
-// Two FP32 values in one 64-bit register pair, for the packed f32x2
-// instructions of sm_100-family GPUs: element-wise IEEE operations, so a
-// packed sum rounds exactly like the two scalar ones.
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
-    f2_t r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
-    f2_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
-    f2_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
 // leaf_terms for two query slots per register pair: the staged reference
 // records hold every float twice, (x_0, x_0, x_1, x_1, ..., l, l, ...), so a
 // 16-byte shared load gives two broadcast pairs.  Same operations, in the

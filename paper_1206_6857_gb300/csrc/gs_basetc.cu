@@ -302,26 +302,6 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t pk2(float lo, float hi) {
-    f2_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk2(f2_t v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
-    f2_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
-    f2_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
 // 16 reference columns for NJ bandwidths: gamma from the three accumulators,
 // the squared distance and each exponent argument two columns per packed
 // f32x2 operation; the exponentials are summed per column parity in scalar
@@ -331,19 +311,19 @@ template <int NJ>
 __device__ __forceinline__ void tc_cols16(const float (&a4)[16], const float (&a3)[16], const float (&a2)[16],
                                           const float *bl, f2_t alpha2, f2_t m2s2, const f2_t (&c2)[NJ],
                                           float (&part)[NJ][2]) {
-    const f2_t k1024 = pk2(1024.f, 1024.f);
+    const f2_t k1024 = f2_pack(1024.f, 1024.f);
 #pragma unroll
     for (int i = 0; i < 16; i += 2) {
         const float4 b = *reinterpret_cast<const float4 *>(bl + 2 * i);
-        f2_t g = fma2(pk2(a4[i], a4[i + 1]), k1024, pk2(a3[i], a3[i + 1]));
-        g = fma2(g, k1024, pk2(a2[i], a2[i + 1]));
-        const f2_t ab = add2(alpha2, pk2(b.x, b.y));
-        const f2_t d2 = fma2(g, m2s2, ab);
-        const f2_t lw = pk2(b.z, b.w);
+        f2_t g = f2_fma(f2_pack(a4[i], a4[i + 1]), k1024, f2_pack(a3[i], a3[i + 1]));
+        g = f2_fma(g, k1024, f2_pack(a2[i], a2[i + 1]));
+        const f2_t ab = f2_add(alpha2, f2_pack(b.x, b.y));
+        const f2_t d2 = f2_fma(g, m2s2, ab);
+        const f2_t lw = f2_pack(b.z, b.w);
 #pragma unroll
         for (int k = 0; k < NJ; ++k) {
             float x0, x1;
-            upk2(fma2(d2, c2[k], lw), x0, x1);
+            f2_unpack(f2_fma(d2, c2[k], lw), x0, x1);
             part[k][0] += ex2_approx(x0);
             part[k][1] += ex2_approx(x1);
         }
@@ -396,7 +376,7 @@ __device__ __forceinline__ void tc_entry(TcEntryCtx &x, int nchunks, const float
 #pragma unroll
         for (int k = 0; k < NJ; ++k) {
             const float c = negc[__ffs(mm) - 1];
-            c2[k] = pk2(c, c);
+            c2[k] = f2_pack(c, c);
             part[k][0] = part[k][1] = 0.f;
             mm &= mm - 1;
         }
@@ -606,7 +586,7 @@ k_basecase_tc(TcParams p, const MergedEntry *__restrict__ ent, const long long *
                 const int nj = __popc(m);
                 evals += (unsigned long long)nj * (unsigned long long)nr;
                 const float m2s = ldexpf(-2.f, 20 - sQ - __ldg(p.rscale + ri));
-                const f2_t m2s2 = pk2(m2s, m2s), alpha2 = pk2(alpha, alpha);
+                const f2_t m2s2 = f2_pack(m2s, m2s), alpha2 = f2_pack(alpha, alpha);
                 tc::bar_sync(x.bar_id, 128);   // (beta, lw) visible
                 const float *negc = p.negc + kTcBlk * jb;
                 switch (nj) {

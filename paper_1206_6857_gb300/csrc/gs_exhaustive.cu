@@ -146,6 +146,10 @@ template <typename T, int DP>
 struct TileCfg {
     static constexpr int NT = RefRec<T, DP>::NT;
     static constexpr int TILE = (NT * sizeof(T) <= 64) ? 128 : 64;
+    // FP32 records of at most 8 dimensions are staged with every float
+    // twice, for the packed path (two queries per f32x2 operation)
+    static constexpr bool X2 = sizeof(T) == 4 && DP <= 8;
+    static constexpr int SMEM = TILE * NT * (X2 ? 2 : 1);   // staged T slots
 };
 
 template <typename T, int NT>
@@ -197,44 +201,108 @@ __device__ __forceinline__ void exhaustive_tile(const T *__restrict__ qx, int64_
 
     const int64_t r0 = by * chunk;
     const int64_t r1 = min(r0 + chunk, Npad);
-    for (int64_t t0 = r0; t0 < r1; t0 += TILE) {
-        __syncthreads();
-        {
-            // TILE*NT elements of T = TILE*NT*sizeof(T)/16 vectors of 16 bytes
-            const float4 *src = reinterpret_cast<const float4 *>(rec + t0 * NT);
-            float4 *dst = reinterpret_cast<float4 *>(tile);
-            constexpr int NV = TILE * NT * (int)sizeof(T) / 16;
-            for (int v = threadIdx.x; v < NV; v += kThreads) dst[v] = src[v];
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int rr0 = 0; rr0 < TILE; rr0 += kRun) {
-            float part[QPT][NJ];
+    if constexpr (Cfg::X2) {
+        static_assert(QPT == 2, "the packed path takes two queries per thread");
+        // Two queries per register pair: the same FP32 operations as the
+        // scalar loop below, element by element (so the same sums), with
+        // one f32x2 instruction for both queries' differences, squared
+        // distances, exponent arguments and partial sums.
+        f2_t xq2[DP], nc2[NJ];
 #pragma unroll
-            for (int k = 0; k < QPT; ++k)
+        for (int d = 0; d < DP; ++d) xq2[d] = f2_pack(xq[0][d], xq[1][d]);
 #pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) part[k][jj] = 0.f;
-#pragma unroll 4
-            for (int rr = rr0; rr < rr0 + kRun; ++rr) {
-                T rv[NT];
-                load_rec<T, NT>(tile + rr * NT, rv);
-                const float l = (float)rv[DP];
-#pragma unroll
-                for (int k = 0; k < QPT; ++k) {
-                    float d2 = 0.f;
-#pragma unroll
-                    for (int d = 0; d < DP; ++d) {
-                        const float df = (float)(xq[k][d] - rv[d]);
-                        d2 = fmaf(df, df, d2);
-                    }
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) part[k][jj] += ex2_approx(fmaf(d2, nc[jj], l));
+        for (int jj = 0; jj < NJ; ++jj) nc2[jj] = f2_pack(nc[jj], nc[jj]);
+        for (int64_t t0 = r0; t0 < r1; t0 += TILE) {
+            __syncthreads();
+            {
+                // records staged as (x_0, x_0, x_1, x_1, ..., l, l, ...)
+                const float4 *src = reinterpret_cast<const float4 *>(rec + t0 * NT);
+                float4 *dst = reinterpret_cast<float4 *>(tile);
+                constexpr int NV = TILE * NT / 4;
+                for (int v = threadIdx.x; v < NV; v += kThreads) {
+                    const float4 f = src[v];
+                    dst[2 * v] = make_float4(f.x, f.x, f.y, f.y);
+                    dst[2 * v + 1] = make_float4(f.z, f.z, f.w, f.w);
                 }
             }
+            __syncthreads();
+            const ulonglong2 *tp = reinterpret_cast<const ulonglong2 *>(tile);
+#pragma unroll 1
+            for (int rr0 = 0; rr0 < TILE; rr0 += kRun) {
+                f2_t part[NJ];
 #pragma unroll
-            for (int k = 0; k < QPT; ++k)
+                for (int jj = 0; jj < NJ; ++jj) part[jj] = 0ull;
+#pragma unroll 4
+                for (int rr = rr0; rr < rr0 + kRun; ++rr) {
+                    f2_t rv[NT];
 #pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) acc[k][jj] += (double)part[k][jj];
+                    for (int v = 0; v < NT / 2; ++v) {
+                        const ulonglong2 u = tp[rr * (NT / 2) + v];
+                        rv[2 * v] = u.x;
+                        rv[2 * v + 1] = u.y;
+                    }
+                    f2_t d2 = 0ull;
+#pragma unroll
+                    for (int d = 0; d < DP; ++d) {
+                        const f2_t df = f2_sub(xq2[d], rv[d]);
+                        d2 = f2_fma(df, df, d2);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) {
+                        float a0, a1;
+                        f2_unpack(f2_fma(d2, nc2[jj], rv[DP]), a0, a1);
+                        part[jj] = f2_add(part[jj], f2_pack(ex2_approx(a0), ex2_approx(a1)));
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) {
+                    float p0, p1;
+                    f2_unpack(part[jj], p0, p1);
+                    acc[0][jj] += (double)p0;
+                    acc[1][jj] += (double)p1;
+                }
+            }
+        }
+    } else {
+        for (int64_t t0 = r0; t0 < r1; t0 += TILE) {
+            __syncthreads();
+            {
+                // TILE*NT elements of T = TILE*NT*sizeof(T)/16 vectors of 16 bytes
+                const float4 *src = reinterpret_cast<const float4 *>(rec + t0 * NT);
+                float4 *dst = reinterpret_cast<float4 *>(tile);
+                constexpr int NV = TILE * NT * (int)sizeof(T) / 16;
+                for (int v = threadIdx.x; v < NV; v += kThreads) dst[v] = src[v];
+            }
+            __syncthreads();
+    #pragma unroll 1
+            for (int rr0 = 0; rr0 < TILE; rr0 += kRun) {
+                float part[QPT][NJ];
+    #pragma unroll
+                for (int k = 0; k < QPT; ++k)
+    #pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) part[k][jj] = 0.f;
+    #pragma unroll 4
+                for (int rr = rr0; rr < rr0 + kRun; ++rr) {
+                    T rv[NT];
+                    load_rec<T, NT>(tile + rr * NT, rv);
+                    const float l = (float)rv[DP];
+    #pragma unroll
+                    for (int k = 0; k < QPT; ++k) {
+                        float d2 = 0.f;
+    #pragma unroll
+                        for (int d = 0; d < DP; ++d) {
+                            const float df = (float)(xq[k][d] - rv[d]);
+                            d2 = fmaf(df, df, d2);
+                        }
+    #pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) part[k][jj] += ex2_approx(fmaf(d2, nc[jj], l));
+                    }
+                }
+    #pragma unroll
+                for (int k = 0; k < QPT; ++k)
+    #pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) acc[k][jj] += (double)part[k][jj];
+            }
         }
     }
 
@@ -261,7 +329,7 @@ k_exhaustive(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ r
              int64_t chunk, int64_t Npad, NegC negc, int nh, const Ingest *__restrict__ ing,
              double *__restrict__ out, int atomic) {
     using Cfg = TileCfg<T, DP>;
-    __shared__ __align__(16) T tile[Cfg::TILE * Cfg::NT];
+    __shared__ __align__(16) T tile[Cfg::SMEM];
     const int j0 = blockIdx.z * NJ;
     float nc[NJ];
 #pragma unroll
@@ -450,7 +518,7 @@ template <int DP, int NJ>
 __global__ void __launch_bounds__(kThreads) k_group_exhaustive(const GroupProb *__restrict__ gp, int nprob) {
     using Cfg = TileCfg<float, DP>;
     constexpr int QPT = (DP <= 8) ? 2 : 1;
-    __shared__ __align__(16) float tile[Cfg::TILE * Cfg::NT];
+    __shared__ __align__(16) float tile[Cfg::SMEM];
     const long long t = blockIdx.x;
     int lo = 0, hi = nprob - 1;   // the problem owning tile t
     while (lo < hi) {
