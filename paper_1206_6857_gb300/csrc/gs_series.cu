@@ -729,9 +729,12 @@ __global__ void __launch_bounds__(kL2lWarps * 32) k_l2l_level(SeriesParams sp, i
 // one multiply-add per term, in a lane-interleaved shared buffer.  Longer
 // expansions: lanes over the terms, one query at a time.
 constexpr int kFinLane = 64;
-constexpr size_t kFinSmemPerWarp = (size_t)(kFinLane * 32 + 32 * 32) * sizeof(double);
+// doubles of shared memory per warp: the partial sums of the longest local
+// expansion evaluated per lane (at most kFinLane terms), then u for D dims
+__host__ __device__ inline int fin_terms(int T) { return T < kFinLane ? T : kFinLane; }
+__host__ __device__ inline size_t fin_doubles_per_warp(int T, int D) { return (size_t)(fin_terms(T) + D) * 32; }
 __global__ void __launch_bounds__(kSerTB) k_final(SeriesParams sp) {
-    extern __shared__ double fin_s[];   // per warp: partial sums S [kFinLane][32 lanes], u [32 dims][32 lanes]
+    extern __shared__ double fin_s[];   // per warp: partial sums S [terms][32 lanes], u [D][32 lanes]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int depth = sp.q_depth, D = sp.D;
     const int64_t nl = 1ll << depth;
@@ -751,8 +754,8 @@ __global__ void __launch_bounds__(kSerTB) k_final(SeriesParams sp) {
         const double is = sp.inv_s[j];
         const double *Bl = sp.B ? sp.B + (leaf * sp.nh + j) * sp.T : nullptr;
         const int64_t b = level_begin(sp.qn, depth, i), e = level_begin(sp.qn, depth, i + 1);
-        double *acc = fin_s + (size_t)w * (kFinLane * 32 + 32 * 32) + lane;
-        double *uw = acc - lane + kFinLane * 32;      // this warp's u region
+        double *acc = fin_s + (size_t)w * fin_doubles_per_warp(sp.T, D) + lane;
+        double *uw = acc - lane + fin_terms(sp.T) * 32;   // this warp's u region
         if (Tp <= kFinLane) {
             const double *cQ = sp.qcenter + leaf * D;
             for (int64_t pos = b + lane; pos < e; pos += 32) {
@@ -942,7 +945,7 @@ int run_series_and_final(const TraversalIn &in, FrontierBufs &fb, const SeriesTa
     }
     cx.phase(GS_PH_DOWN);
     allow_max_smem((const void *)k_final);
-    k_final<<<fb.grid_warps / 4, kSerTB, (kSerTB / 32) * kFinSmemPerWarp, st>>>(sp);
+    k_final<<<fb.grid_warps / 4, kSerTB, (kSerTB / 32) * fin_doubles_per_warp(sp.T, sp.D) * sizeof(double), st>>>(sp);
     cx.launches += 1;
     if (int rc2 = cx.check("k_final")) return rc2;
     cx.phase(GS_PH_OTHER);
