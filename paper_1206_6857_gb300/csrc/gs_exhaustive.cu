@@ -139,7 +139,7 @@ struct NegC {
     float v[64];   // -log2(e) / (2 h_j^2), j < nh
 };
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;   // three blocks per SM (at most 80 registers a thread)
 constexpr int kRun = 64;   // references per FP32 partial sum
 
 template <typename T, int DP>
@@ -324,7 +324,7 @@ __device__ __forceinline__ void exhaustive_tile(const T *__restrict__ qx, int64_
 }
 
 template <typename T, int DP, int NJ, int QPT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 k_exhaustive(const T *__restrict__ qx, int64_t M, int D, const T *__restrict__ rec,
              int64_t chunk, int64_t Npad, NegC negc, int nh, const Ingest *__restrict__ ing,
              double *__restrict__ out, int atomic) {
@@ -515,7 +515,7 @@ __global__ void k_group_pack(const GroupProb *__restrict__ gp) {
 }
 
 template <int DP, int NJ>
-__global__ void __launch_bounds__(kThreads) k_group_exhaustive(const GroupProb *__restrict__ gp, int nprob) {
+__global__ void __launch_bounds__(kThreads, 3) k_group_exhaustive(const GroupProb *__restrict__ gp, int nprob) {
     using Cfg = TileCfg<float, DP>;
     constexpr int QPT = (DP <= 8) ? 2 : 1;
     __shared__ __align__(16) float tile[Cfg::SMEM];
