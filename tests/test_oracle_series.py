@@ -211,6 +211,34 @@ def test_balanced_factor_small_cases():
     assert S.balanced_factor(2, 3) == pytest.approx(4 / math.sqrt(2))
 
 
+def test_lemma_bounds_hand_values():
+    """Lemmas 4-6 evaluated by hand for one node pair, so that a bound that
+    is too loose (a dropped sqrt 2, a wrong binomial, the I() exponent on the
+    wrong term) fails, not only one that is too tight.  D = 2, p = 3:
+    p' = 1, floor(p/D)! = 1, ceil(p/D)! = 2, C(D+p-1, D-1) = C(4, 1) = 4, so
+    the common factor is 4 / sqrt(1 * 2) = 2 sqrt 2; C(D+p-1, D) = C(4, 2) = 6.
+    W_R = 2.5, delta_min = 0.6, h = 0.5: e^{-delta^2 / 4h^2} = e^{-0.36}.
+    Lemma 6's I() multiplies the term that carries C(D+p-1, D): it counts the
+    Taylor terms |beta| < p of the converted expansion, each at most
+    (sqrt 2 r_Q)^{|beta|} (the E_1 part of the proof)."""
+    e = math.exp(-0.36)
+    r2 = math.sqrt(2.0)
+    # E_DH, r_R = 0.4: 2.5 * 2 sqrt2 * 0.064 = 0.32 sqrt2
+    assert S.bound_dh(3, 2, 2.5, 0.6, 0.5, 0.4) == pytest.approx(0.32 * r2 * e, rel=1e-14)
+    # E_DL, r_Q = 0.3: 2.5 * 2 sqrt2 * 0.027 = 0.135 sqrt2
+    assert S.bound_dl(3, 2, 2.5, 0.6, 0.5, 0.3) == pytest.approx(0.135 * r2 * e, rel=1e-14)
+    # E_H2L, r_Q = 0.3 (sqrt2 r_Q <= 1: I = 0), r_R = 0.4:
+    #   5 sqrt2 (0.027 + (0.4 sqrt2)^3 * 6) = 5 sqrt2 (0.027 + 0.768 sqrt2) = 0.135 sqrt2 + 7.68
+    assert S.bound_h2l(3, 2, 2.5, 0.6, 0.5, 0.3, 0.4) == pytest.approx((0.135 * r2 + 7.68) * e, rel=1e-14)
+    # E_H2L, r_Q = 0.8 (sqrt2 r_Q > 1: I = p - 1 = 2, (0.8 sqrt2)^2 = 1.28):
+    #   5 sqrt2 (0.512 + 0.768 sqrt2 * 1.28) = 2.56 sqrt2 + 9.8304
+    assert S.bound_h2l(3, 2, 2.5, 0.6, 0.5, 0.8, 0.4) == pytest.approx((2.56 * r2 + 9.8304) * e, rel=1e-14)
+    # D = 3, p = 4: p' = 1, factor C(6, 2) / sqrt(1 * 1 * 2) = 15 / sqrt2; at delta_min = 0
+    assert S.bound_dh(4, 3, 1.0, 0.0, 1.0, 0.5) == pytest.approx(15 / r2 * 0.0625, rel=1e-14)
+    # D = 5, p = 7: p' = 2, floor = 1, ceil = 2 -> sqrt(1^3 * 2^2) = 2, C(11, 4) = 330 -> 165
+    assert S.balanced_factor(5, 7) == pytest.approx(165.0, rel=1e-15)
+
+
 def test_fd_estimate_brackets_the_true_contribution():
     rng = np.random.default_rng(80)
     for trial in range(20):
