@@ -335,6 +335,143 @@ __global__ void k_part_scatter(const T *__restrict__ xs, const int32_t *__restri
 }
 
 // --------------------------------------------------------------------------
+// one level of small nodes in one launch: a CTA per node takes the node's
+// bounding box, its split dimension, the radix select of the split rank and
+// the stable scatter, with the same arithmetic and order as the per-level
+// kernels above (so the tree is identical); used for the levels whose nodes
+// hold at most kNodeFused points, where the per-level kernels are launch-bound
+// --------------------------------------------------------------------------
+constexpr int64_t kNodeFused = 16384;
+
+template <typename T>
+__global__ void __launch_bounds__(kTB)
+k_level_node(const T *__restrict__ xs, const int32_t *__restrict__ perm, int64_t n, int D, int k,
+             int32_t *split_dim, T *xs_out, int32_t *perm_out, unsigned *status) {
+    using K = typename Key<T>::K;
+    __shared__ K s_min[32], s_max[32];
+    __shared__ uint32_t s_hist[256];
+    __shared__ K s_prefix;
+    __shared__ uint32_t s_rem;
+    __shared__ int s_dim;
+    __shared__ unsigned long long s_tot;
+    const int64_t nn = 1ll << k;
+    const int64_t i = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = level_begin(n, k, i), e = level_begin(n, k, i + 1);
+    const int64_t mid = ((2 * i + 1) * n) >> (k + 1);
+    // bounding box (order-preserving keys)
+    for (int d = threadIdx.x; d < D; d += blockDim.x) {
+        s_min[d] = ~(K)0;
+        s_max[d] = (K)0;
+    }
+    __syncthreads();
+    for (int d = 0; d < D; ++d) {
+        K mn = ~(K)0, mx = (K)0;
+        for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+            const K v = Key<T>::enc(xs[p * D + d]);
+            mn = v < mn ? v : mn;
+            mx = v > mx ? v : mx;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const K a = __shfl_xor_sync(0xffffffffu, mn, o), c = __shfl_xor_sync(0xffffffffu, mx, o);
+            mn = a < mn ? a : mn;
+            mx = c > mx ? c : mx;
+        }
+        if (lane == 0) {
+            atomicMin(&s_min[d], mn);
+            atomicMax(&s_max[d], mx);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sd = 0;
+        double best = -1.0;
+        for (int d = 0; d < D; ++d) {
+            const double ext = (double)Key<T>::dec(s_max[d]) - (double)Key<T>::dec(s_min[d]);
+            if (ext > best) {
+                best = ext;
+                sd = d;
+            }
+        }
+        split_dim[nn - 1 + i] = sd;
+        s_dim = sd;
+        s_prefix = 0;
+        s_rem = (uint32_t)(mid - b);
+    }
+    __syncthreads();
+    const int dim = s_dim;
+    // radix select of rank (mid - b), 8 bits per pass from the top
+    for (int shift = Key<T>::BITS - 8; shift >= 0; shift -= 8) {
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_hist[t] = 0u;
+        __syncthreads();
+        const K prefix = s_prefix;
+        const bool all_match = shift + 8 >= Key<T>::BITS;
+        for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+            const K key = Key<T>::enc(xs[p * D + dim]);
+            if (all_match || ((key ^ prefix) >> (shift + 8)) == 0)
+                atomicAdd(&s_hist[(unsigned)(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t c[8], tot = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                c[t] = s_hist[lane * 8 + t];
+                tot += c[t];
+            }
+            uint32_t incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t excl = incl - tot;
+            const uint32_t rem = s_rem;
+            if (excl <= rem && rem < incl) {
+                uint32_t cum = excl;
+                int digit = lane * 8;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    if (rem < cum + c[t]) {
+                        digit = lane * 8 + t;
+                        break;
+                    }
+                    cum += c[t];
+                }
+                s_prefix = prefix | (((K)digit) << shift);
+                s_rem = rem - cum;
+            }
+        }
+        __syncthreads();
+    }
+    const K prefix = s_prefix;
+    const int64_t r_eq = s_rem;
+    // stable scatter: (less, equal) counts before each point by a block scan
+    unsigned long long carry = 0;
+    for (int64_t t0 = b; t0 < e; t0 += blockDim.x) {
+        const int64_t p = t0 + threadIdx.x;
+        const bool valid = p < e;
+        const K key = valid ? Key<T>::enc(xs[p * D + dim]) : (K)0;
+        const unsigned long long f =
+            valid ? (((unsigned long long)(key < prefix) << 32) | (unsigned long long)(key == prefix)) : 0ull;
+        const unsigned long long ex = carry + block_excl_scan_u64(f, &s_tot);
+        carry += s_tot;
+        if (!valid) continue;
+        const int64_t lt_before = (int64_t)(ex >> 32);
+        const int64_t eq_before = (int64_t)(ex & 0xffffffffull);
+        const int64_t left_before = lt_before + (eq_before < r_eq ? eq_before : r_eq);
+        const bool left = key < prefix || (key == prefix && eq_before < r_eq);
+        const int64_t np = left ? b + left_before : mid + (p - b - left_before);
+        if (np < b || np >= e || (left && np >= mid) || (!left && np < mid)) {
+            atomicOr(status, ST_INTERNAL);   // inconsistent split: never write outside the node
+            continue;
+        }
+        perm_out[np] = perm[p];
+        for (int d = 0; d < D; ++d) xs_out[np * D + d] = xs[p * D + d];
+    }
+}
+
+// --------------------------------------------------------------------------
 // node statistics
 // --------------------------------------------------------------------------
 template <typename T>
@@ -750,6 +887,16 @@ static int build_impl(const T *x, const float *w, int64_t n, int D, int L, const
 
     for (int k = 0; k < t.depth; ++k) {
         const int64_t nn = 1ll << k;
+        if (((n + nn - 1) >> k) <= kNodeFused) {
+            // every node of this level has at most kNodeFused points: one launch
+            k_level_node<T><<<(unsigned)nn, kTB, 0, st>>>(xa, pa, n, D, k, t.split_dim, xb, pb,
+                                                         (unsigned *)&ing->status);
+            cx.launches += 1;
+            if (int rc = cx.check("tree level (per node)")) return rc;
+            T *tx = xa; xa = xb; xb = tx;
+            int32_t *tp = pa; pa = pb; pb = tp;
+            continue;
+        }
         GS_CUDA_TRY(cudaMemsetAsync(bmin, 0xff, nn * D * sizeof(K), st));
         GS_CUDA_TRY(cudaMemsetAsync(bmax, 0x00, nn * D * sizeof(K), st));
         k_level_bbox<T><<<gridn(n), kTB, 0, st>>>(xa, n, D, k, bmin, bmax);
