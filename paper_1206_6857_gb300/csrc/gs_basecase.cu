@@ -176,6 +176,7 @@ int run_basecase(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, Ca
         cx.phase(GS_PH_OTHER);
         return GS_OK;
     }
+    cx.mark(CallCtx::kTimerBase + 1);
     switch (DP) {
         case 1: launch_dp<1>(qpl, anch, bp, fb.fs, fb.base_groups, fb.base_r, grid, cx.st); break;
         case 2: launch_dp<2>(qpl, anch, bp, fb.fs, fb.base_groups, fb.base_r, grid, cx.st); break;
@@ -190,6 +191,7 @@ int run_basecase(const TraversalIn &in, FrontierBufs &fb, double *Gq, int DP, Ca
         case 24: launch_dp<24>(qpl, anch, bp, fb.fs, fb.base_groups, fb.base_r, grid, cx.st); break;
         default: launch_dp<32>(qpl, anch, bp, fb.fs, fb.base_groups, fb.base_r, grid, cx.st); break;
     }
+    cx.mark(-1);
     cx.launches += 1;
     cx.launches_base += 1;
     if (int rc = cx.check("k_basecase")) return rc;

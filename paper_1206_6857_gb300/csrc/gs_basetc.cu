@@ -742,8 +742,10 @@ int run_basecase_tc(const TraversalIn &in, const MergedEntry *ent, const long lo
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             const int64_t grid = lq < sms ? lq : sms;
             cx.phase(GS_PH_BASE_TC);
+            cx.mark(CallCtx::kTimerBase);
             k_basecase_tc<<<(unsigned)(grid > 0 ? grid : 1), kTcWG * 128, TcSmem::TOTAL, st>>>(tp, ent_tc, cnt_tc,
                                                                                                 lq);
+            cx.mark(-1);
             cx.phase(GS_PH_BASE);
             cx.launches += 1;
             cx.launches_base += 1;

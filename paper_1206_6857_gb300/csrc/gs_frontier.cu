@@ -829,11 +829,11 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
         const double W = rW[0];
         const double wmax = (double)__uint_as_float(ing->wmax_bits);
         const double u = 5.9604644775390625e-08;   // 2^-24
-        double rho = 0.6931471805599453 * 64.0 * (double)(D + 4) * u;
+        double rho = 0.6931471805599453 * 64.0 * (double)(D + 5) * u;   // d^2 (D+3), the FMA, l
         rho = rho + 4.76837158203125e-07;          // 2^-21
         rho = rho + (double)(run + 1) * u;      // FP32 sums over one reference leaf, then compensated
         rho = rho + ldexp(1.0, -63 - floor_log2) * (((double)N * wmax) / W);
-        rho = rho + extra_rho;                   // the tensor-core base case's charge, when enabled
+        rho = rho + extra_rho;                   // the tensor-core or expanded-distance base case's charge
         fs->rho = rho;
         fs->eps_t = eps - rho;
         fs->Wtot = W;
@@ -882,6 +882,10 @@ static double factd(int m) {
     for (int q = 2; q <= m; ++q) f = f * (double)q;
     return f;
 }
+
+// worst-case list memory below which a traversal runs without per-iteration
+// host reads of its totals
+constexpr double kPresizedBytes = 64.0 * 1024 * 1024;
 
 // Grow a device array to hold at least `need` elements, keeping the first
 // `keep` elements.
@@ -940,23 +944,54 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
     fp.Dpow[0] = 1.0;
     for (int k = 1; k < 34; ++k) fp.Dpow[k] = fp.Dpow[k - 1] * (double)D;
 
+    // Small problems: every list at its worst-case size up front, so that the
+    // iterations run without reading their totals on the host (one read after
+    // the last).  The pairs of iteration t are distinct (query node, reference
+    // node, bandwidth) triples of levels min(t, depth), so there are at most
+    // nh 2^min(t, dQ) 2^min(t, dR) of them, and every action list holds at most
+    // the sum of that over the iterations.
+    const int T = in.qt->depth > in.rt->depth ? in.qt->depth : in.rt->depth;
+    const int qd = in.qt->depth, rd = in.rt->depth;
+    bool presized = !in.log && !fb.trace && qd + rd <= 40;
+    int64_t pmax = 0, psum = 0;
+    if (presized) {
+        for (int t = 0; t <= T; ++t) {
+            const int64_t p = (int64_t)in.nh << ((t < qd ? t : qd) + (t < rd ? t : rd));
+            pmax = p > pmax ? p : pmax;
+            psum += p;
+        }
+        const double bytes = (double)pmax * (2 * sizeof(int32_t) + 1 + 4 * sizeof(float)) +
+                             (double)psum * (sizeof(int32_t) + 3 * sizeof(SeriesEntry));
+        presized = bytes <= kPresizedBytes;
+    }
+    if (presized) {
+        for (int b = 0; b < 2; ++b)
+            if ((rc = grow(&fb.pr[b], &fb.cap_pr[b], pmax, 0, st))) return rc;
+        if ((rc = grow(&fb.dec, &fb.cap_pairs, pmax, 0, st))) return rc;
+        if ((rc = grow(&fb.geo, &fb.cap_geo, 4 * pmax, 0, st))) return rc;
+        if ((rc = grow(&fb.base_r, &fb.cap_base, psum, 0, st))) return rc;
+        for (int m = 0; m < 3; ++m)
+            if ((rc = grow(&fb.series[m], &fb.cap_series[m], psum, 0, st))) return rc;
+    }
     k_front_init<<<1, 64, 0, st>>>(fb.fs, fb.groups[0], fb.pr[0], in.nh, in.rt->W, in.rt->lo, in.rt->hi,
                                    (Ingest *)in.ing, in.rt->n, in.D, in.floor_log2, in.eps,
                                    (in.rt->n + (1ll << in.rt->depth) - 1) >> in.rt->depth,
                                    tc_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth, in.rt->n,
                                                    in.rt->depth, in.nh)
                                        ? tc_charge()
-                                       : 0.0);
+                                       : (xp_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth,
+                                                          in.rt->n, in.rt->depth, in.nh)
+                                              ? xp_charge()
+                                              : 0.0));
     cx.launches += 1;
     if ((rc = cx.check("k_front_init"))) return rc;
-    const int T = in.qt->depth > in.rt->depth ? in.qt->depth : in.rt->depth;
     int cur = 0;
     int64_t ng = in.nh, npairs = in.nh;
     int64_t base_count = 0, bgroups = 0, ser_count[3] = {0, 0, 0};
     int64_t log_base = 0;
     const int max_grid = fb.grid_warps / 8;
     fp.mlp = in.mlp;
-    for (int t = 0; t <= T && ng > 0; ++t) {
+    for (int t = 0; t <= T && (presized || ng > 0); ++t) {
         fp.t = t;
         fp.q_depth = t < in.qt->depth ? t : in.qt->depth;
         fp.r_depth = t < in.rt->depth ? t : in.rt->depth;
@@ -976,8 +1011,10 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         }
         for (int p = 1; p <= 16 && p <= in.P; ++p) fp.cH2L[p] = fp.Dpow[2 * p + 1] * fp.cw[2];
         // this iteration's per-pair arrays
-        if ((rc = grow(&fb.dec, &fb.cap_pairs, npairs, 0, st))) return rc;
-        if ((rc = grow(&fb.geo, &fb.cap_geo, 4 * npairs, 0, st))) return rc;
+        if (!presized) {
+            if ((rc = grow(&fb.dec, &fb.cap_pairs, npairs, 0, st))) return rc;
+            if ((rc = grow(&fb.geo, &fb.cap_geo, 4 * npairs, 0, st))) return rc;
+        }
         fp.geo = fb.geo;
         PairLog *lg = in.log;
         if (lg) {
@@ -1002,7 +1039,10 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
             fp.pid = t == 0 ? nullptr : lg->pid[cur];
             fp.log_base = log_base;
         }
-        const int grid = (int)((ng + 7) / 8 < max_grid ? (ng + 7) / 8 : max_grid);
+        // presized: the grid for this level's largest possible group count
+        // (the kernels read the actual count on the device)
+        const int64_t ngb = presized ? (int64_t)in.nh << (t < qd ? t : qd) : ng;
+        const int grid = (int)((ngb + 7) / 8 < max_grid ? (ngb + 7) / 8 : max_grid);
         if (lg)
             k_front_decide<2><<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
                                                     fb.trace_cap);
@@ -1018,6 +1058,23 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         k_cols_offsets<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial, fb.off);
         cx.launches += 4;
         if ((rc = cx.check("k_cols_*"))) return rc;
+        if (presized) {
+            EmitOut eo;
+            eo.groups_next = fb.groups[cur ^ 1];
+            eo.pr_next = fb.pr[cur ^ 1];
+            eo.base_groups = fb.base_groups;
+            eo.base_r = fb.base_r;
+            for (int m = 0; m < 3; ++m) eo.series[m] = fb.series[m];
+            eo.pid_next = nullptr;
+            eo.log_base = 0;
+            k_front_emit<<<grid, 256, 0, st>>>(fb.fs, t, fp.q_leaf, fp.r_leaf, fb.groups[cur], fb.pr[cur], fb.dec,
+                                               fb.cnt, fb.off, eo);
+            k_front_advance<<<1, 1, 0, st>>>(fb.fs, t);
+            cx.launches += 2;
+            if ((rc = cx.check("k_front_emit"))) return rc;
+            cur ^= 1;
+            continue;
+        }
         // read this iteration's totals and make room for what it will write
         GS_CUDA_TRY(cudaMemcpyAsync(fb.host_totals, &fb.fs->totals[0], kCols * sizeof(int64_t),
                                     cudaMemcpyDeviceToHost, st));
@@ -1061,6 +1118,14 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         bgroups += tot[C_BGROUPS];
         for (int m = 0; m < 3; ++m) ser_count[m] += tot[C_DH + m];
         cur ^= 1;
+    }
+    if (presized) {
+        // the action-list lengths, read once
+        GS_CUDA_TRY(cudaMemcpyAsync(fb.host_totals, &fb.fs->base_count, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    st));
+        GS_CUDA_TRY(cudaStreamSynchronize(st));
+        bgroups = fb.host_totals[1];
+        for (int m = 0; m < 3; ++m) ser_count[m] = fb.host_totals[3 + m];
     }
     for (int m = 0; m < 3; ++m) fb.n_series[m] = ser_count[m];
     fb.n_base_groups = bgroups;

@@ -58,9 +58,12 @@ struct CallCtx {
         open_phase = ph;
     }
     void end() { phase(-1); }
-    // Time one launch into stats->ms_series[slot]: mark(slot) before it,
-    // mark(-1) after.  No-op without stats.
-    static constexpr int kMaxTimers = 16;
+    // Time one launch into stats->ms_series[slot] (slot 0-2) or
+    // stats->ms_base_kernels[slot - kTimerBase] (kTimerBase: the tensor-core
+    // or expanded-distance kernel, kTimerBase + 1: the direct one):
+    // mark(slot) before it, mark(-1) after.  No-op without stats.
+    static constexpr int kMaxTimers = 24;
+    static constexpr int kTimerBase = 3;
     cudaEvent_t tev[kMaxTimers];
     int tslot[kMaxTimers];
     int ntev = 0;
@@ -84,9 +87,13 @@ struct CallCtx {
             if (cudaEventElapsedTime(&ms, ev[0], ev[nev - 1]) == cudaSuccess) stats->ms_total = ms;
         }
         for (int i = 0; i + 1 < ntev; ++i) {
-            if (tslot[i] < 0 || tslot[i] >= 3) continue;
+            if (tslot[i] < 0 || tslot[i] > kTimerBase + 1) continue;
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, tev[i], tev[i + 1]) == cudaSuccess) stats->ms_series[tslot[i]] += ms;
+            if (cudaEventElapsedTime(&ms, tev[i], tev[i + 1]) != cudaSuccess) continue;
+            if (tslot[i] >= kTimerBase)
+                stats->ms_base_kernels[tslot[i] - kTimerBase] += ms;
+            else
+                stats->ms_series[tslot[i]] += ms;
         }
         stats->launches = launches;
         stats->launches_base = launches_base;
@@ -242,6 +249,11 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
 // Tensor-core base case (9 <= D <= 16, FP32 points, leaves of at most 128
 // points): whether a call takes it, and the extra FP32 charge it needs.
 bool tc_base_enabled(int D, int dtype, int flags, int64_t qn, int q_depth, int64_t rn, int r_depth, int nh);
+// Expanded-distance base case (FP32 points, D <= 8, query leaves of 33..128
+// points): whether a call's FP32 charge includes it (GS_FLAG_NO_MERGE leaves
+// the charge in place but runs the per-bandwidth kernel), and that charge.
+bool xp_base_enabled(int D, int dtype, int flags, int64_t qn, int q_depth, int64_t rn, int r_depth, int nh);
+double xp_charge();
 double tc_charge();
 // Splits the merged entries (ent, off over lq query-leaf rows) between the
 // tensor-core kernel (entries whose pair passes the error guard) and the

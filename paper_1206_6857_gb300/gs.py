@@ -38,6 +38,7 @@ GS_FLAG_NO_MERGE = 1
 GS_FLAG_SMALL_EXHAUSTIVE = 2
 GS_FLAG_NO_TC = 4
 GS_FLAG_BEST_FIRST = 8
+GS_FLAG_NO_XP = 16
 GS_SMALL_WORK = 549755813888.0
 
 GS_MLP_NIN = 12
@@ -74,10 +75,13 @@ class gs_stats(ctypes.Structure):
                 ("retries", ctypes.c_int32), ("fp32_rel_bound", ctypes.c_double),
                 ("eps_traversal", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_phase", ctypes.c_double * GS_NPHASE), ("ms_series", ctypes.c_double * 3),
-                ("point_pairs_tc", ctypes.c_int64)]
+                ("point_pairs_tc", ctypes.c_int64), ("point_pairs_xp", ctypes.c_int64),
+                ("ms_base_kernels", ctypes.c_double * 2)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "ms_phase", "ms_series")}
+        d = {k: getattr(self, k) for k, _ in self._fields_
+             if k not in ("reserved", "ms_phase", "ms_series", "ms_base_kernels")}
+        d["ms_base_kernels"] = [self.ms_base_kernels[0], self.ms_base_kernels[1]]
         d["ms_phase"] = {PHASE_NAMES[i]: self.ms_phase[i] for i in range(GS_NPHASE)}
         d["ms_series"] = {"dh": self.ms_series[0], "dl": self.ms_series[1], "h2l": self.ms_series[2]}
         return d
