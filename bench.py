@@ -47,9 +47,6 @@ def parse():
     ap.add_argument("--selector", default="rule", choices=["rule", "mlp", "fd_only"],
                     help="pair selector: Fig. 6's rule, the stored learned network, or FD pruning only "
                          "(the paper's DFD/DFDO comparison: no series approximations)")
-    ap.add_argument("--no-xp", action="store_true",
-                    help="FP32, D <= 8: sum every leaf pair with the direct FP32 kernel (no expanded-distance "
-                         "base case)")
     ap.add_argument("--best-first", action="store_true",
                     help="ablation: best-first look-ahead of each group's largest bound gaps (GS_FLAG_BEST_FIRST)")
     ap.add_argument("--no-tokens", action="store_true",
@@ -212,7 +209,6 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # sources of each kernel whose DRAM traffic profiles/traffic.json records
 KERNEL_SOURCES = {"k_basecase": ("gs_basemerge.cu", "gs_device.cuh"),
-                  "k_basecase_xp": ("gs_basemerge.cu", "gs_device.cuh"),
                   "k_basecase_tc": ("gs_basetc.cu", "gs_tc.cuh", "gs_device.cuh"),
                   "k_exhaustive": ("gs_exhaustive.cu", "gs_device.cuh")}
 
@@ -341,7 +337,6 @@ def run_gs(args):
         tuned["selector"] = args.selector
         tuned["tokens"] = not args.no_tokens
         tuned["best_first"] = bool(args.best_first)
-        tuned["expanded_distance"] = not args.no_xp
 
     def step(stats=None):
         if args.mode == "search":
@@ -387,23 +382,22 @@ def run_gs(args):
 
     units = float(wl.M) * wl.N * hs.size            # kernel evaluations one step stands for
     value = reps.throughput(units, ms)
-    # the dominant kernel: of the base case's kernels (the tensor-core or
-    # expanded-distance one, the direct one; each timed by CUDA events around
-    # its launch on the library's stream) the one that summed more terms; the
-    # exhaustive kernel for eps = 0 (its phase holds that one launch)
+    # the dominant kernel: of the base case's kernels (the tensor-core one,
+    # the direct one; each timed by CUDA events around its launch on the
+    # library's stream) the one that summed more terms; the exhaustive kernel
+    # for eps = 0 (its phase holds that one launch)
     all_terms = float(np.mean([s.point_pairs_base for s in stats_list]))
-    fast_terms = float(np.mean([s.point_pairs_tc + s.point_pairs_xp for s in stats_list]))
-    use_tc = float(np.mean([s.point_pairs_tc for s in stats_list])) > 0.5 * all_terms
-    use_xp = float(np.mean([s.point_pairs_xp for s in stats_list])) > 0.5 * all_terms
+    tc_terms = float(np.mean([s.point_pairs_tc for s in stats_list]))
+    use_tc = tc_terms > 0.5 * all_terms
     if eps == 0.0:
         base_ms = float(np.mean([s.ms_phase[gs.GS_PH_BASE] / max(1, s.launches_base) for s in stats_list]))
         evals_base = float(np.mean([s.point_pairs_base / max(1, s.launches_base) for s in stats_list]))
-    elif use_tc or use_xp:
+    elif use_tc:
         base_ms = float(np.mean([s.ms_base_kernels[0] for s in stats_list]))
-        evals_base = fast_terms
+        evals_base = tc_terms
     else:
         base_ms = float(np.mean([s.ms_base_kernels[1] for s in stats_list]))
-        evals_base = all_terms - fast_terms
+        evals_base = all_terms - tc_terms
     launches = int(np.mean([s.launches for s in stats_list]))
 
     # roofline: the base-case / exhaustive kernel is bound by the MUFU ex2 rate
@@ -412,8 +406,7 @@ def run_gs(args):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak = ex2_rate * props.multi_processor_count * sm_mhz * 1e6 / 1e12
     achieved = evals_base / (base_ms / 1e3) / 1e12 if base_ms > 0 else None
-    kname = "k_exhaustive" if eps == 0.0 else ("k_basecase_tc" if use_tc else
-                                               ("k_basecase_xp" if use_xp else "k_basecase"))
+    kname = "k_exhaustive" if eps == 0.0 else ("k_basecase_tc" if use_tc else "k_basecase")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
             "frac": achieved / peak if (peak and achieved) else None,
             "traffic": load_traffic(kname, source_sha(kname), "%s/%s/scale%g/leaf%d" % (
@@ -556,13 +549,11 @@ def selector_opts(args, opts):
     """Options for --selector (the stored learned network for mlp, FD
     pruning only for fd_only) and --no-tokens."""
     from paper_1206_6857_gb300 import gs
-    if args.selector == "rule" and not args.no_tokens and not args.best_first and not args.no_xp:
+    if args.selector == "rule" and not args.no_tokens and not args.best_first:
         return opts, None
     o = opts if opts is not None else gs.gs_opts_default()
     if args.best_first:
         o.flags |= gs.GS_FLAG_BEST_FIRST
-    if args.no_xp:
-        o.flags |= gs.GS_FLAG_NO_XP
     if args.no_tokens:
         o.no_tokens = 1
     if args.selector == "fd_only":

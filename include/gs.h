@@ -102,14 +102,6 @@ typedef struct gs_opts {
                                before the group's decisions, and their children's lower
                                bound replaces theirs in G^min when larger.  Same eps
                                guarantee; an ablation, off by default                    */
-#define GS_FLAG_NO_XP 16    /* FP32 points, D <= 8: no expanded-distance base case (every
-                               leaf pair summed by the direct FP32 kernel, and the FP32
-                               charge without its share).  By default the leaf pairs whose
-                               reference leaf passes the error guard at a bandwidth take
-                               ||u||^2 + ||v||^2 - 2 u.v about the reference leaf's centre
-                               (D FMAs per point pair instead of 2D operations); the
-                               charge grows by ln2 (2^-17 + 2^-13) (about 9.0e-5).
-                               Not in the paper.                                           */
 
 /* Default cost weights: a series action runs in FP64 on the GPU while a
  * direct (base-case) term is an FP32 exponential, so on GB300 one unit of
@@ -153,13 +145,11 @@ typedef struct gs_stats {
     double  ms_series[3];     /* device time of the DH, DL and H2L kernels (within GS_PH_SERIES) */
     int64_t point_pairs_tc;  /* of point_pairs_base, those summed by the tensor-core base
                                 case (9 <= D <= 16)                                     */
-    int64_t point_pairs_xp;  /* of point_pairs_base, those summed by the expanded-distance
-                                base case (FP32 points, D <= 8)                         */
     double  ms_base_kernels[2]; /* device time of the base-case summation kernels proper
                                 (CUDA events around their launches, without the list
-                                building): [0] the tensor-core or expanded-distance
-                                kernel (point_pairs_tc + point_pairs_xp terms), [1] the
-                                direct kernel (the other base-case terms)              */
+                                building): [0] the tensor-core kernel (point_pairs_tc
+                                terms), [1] the direct kernel (the other base-case
+                                terms)                                                  */
 } gs_stats;
 
 /* Library version string (static storage). */

@@ -312,40 +312,7 @@ def tc_rho() -> float:
     return 0.6931471805599453 * (64.0 * 2.0 * u + 2.0 ** TC_GUARD_LOG2)
 
 
-XP_GUARD_LOG2 = -13     # absolute exponent error the expanded-distance base case may add (log2 units)
-
-
-def xp_enabled(D: int, f32: bool, nh: int, max_q_leaf: int, max_r_leaf: int, no_xp: bool = False) -> bool:
-    """Whether the FP32 charge of a call includes the expanded-distance base
-    case: FP32 points, D <= 8, at most 32 bandwidths, query leaves of 33 to
-    128 points (two or four per lane of the packed kernel), reference leaves
-    of at most 128."""
-    return (not no_xp) and D <= 8 and f32 and nh <= 32 and 32 < max_q_leaf <= 128 and max_r_leaf <= 128
-
-
-def xp_rho() -> float:
-    """Extra charge when the expanded-distance base case is enabled: two more
-    roundings of the exponent argument over exponents down to 2^-64 (its
-    relative part is (D+6) u against the direct form's (D+5) u, one rounding
-    is slack) and, on the leaf pairs its guard admits, an absolute exponent
-    error of at most 2^XP_GUARD_LOG2 (ln2 times that)."""
-    u = 2.0 ** -24
-    return 0.6931471805599453 * (64.0 * 2.0 * u + 2.0 ** XP_GUARD_LOG2)
-
-
-def xp_arg_bound(D: int, d: float, rho_r: float, c: float, arg: float) -> float:
-    """First-order bound on the error of the expanded-distance exponent
-    argument c ||q - r||^2 + l, formed as c ((|v|^2 - 2 u.v) + |u|^2) + l
-    about the reference leaf's centre (u = q - c_R, v = r - c_R, all FP32,
-    |u|^2 and |v|^2 and the dot product as FMA chains, one FMA for the
-    argument): |c| u [(D+4) d^2 + (4D+4) d rho_R + 5D rho_R^2] + u |arg|,
-    with rho_R the Euclidean radius of the reference leaf about c_R."""
-    u = 2.0 ** -24
-    return abs(c) * u * ((D + 4) * d * d + (4 * D + 4) * d * rho_r + 5 * D * rho_r * rho_r) + u * abs(arg)
-
-
-def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int, run: int, tc: bool = False,
-             xp: bool = False) -> float:
+def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int, run: int, tc: bool = False) -> float:
     """A-priori relative error of the FP32 base case: per-term argument
     rounding for exponents down to 2^-64 (ln2 * 64 * (D+5) u: the squared
     distance (D+3) u relative -- the differences, the FMA chain, c -- the
@@ -361,8 +328,6 @@ def fp32_rho(D: int, N: int, w_max: float, W: float, floor_log2: int, run: int, 
     rho = rho + 2.0 ** (-63 - floor_log2) * ((N * w_max) / W)
     if tc:
         rho = rho + tc_rho()
-    elif xp:
-        rho = rho + xp_rho()
     return rho
 
 
@@ -451,7 +416,6 @@ def _argmax_certified(scores, certified):
 def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None = None,
              selector: int = SEL_RULE, tokens: bool = True, floor_log2: int = -40,
              w_max: float = None, cost_weight=COST_WEIGHTS, mlp_params=None, no_tc: bool = False,
-             no_xp: bool = False,
              best_first: bool = False):
     """Run the level-synchronous traversal; returns a Traversal whose iters[t]
     holds the frontier (q, r, j) and the decision (method, p, E) of every
@@ -484,8 +448,7 @@ def traverse(qt: Tree, rt: Tree, mono: bool, h, eps: float, plimit: int | None =
     run = -(-rt.n // (1 << rt.depth))          # largest reference leaf
     qrun = -(-qt.n // (1 << qt.depth))         # largest query leaf
     tc = tc_enabled(D, qt.f32, nh, qrun, run, no_tc)
-    xp = xp_enabled(D, qt.f32, nh, qrun, run, no_xp)
-    rho = fp32_rho(D, rt.n, w_max, W, floor_log2, run, tc, xp)
+    rho = fp32_rho(D, rt.n, w_max, W, floor_log2, run, tc)
     eps_t = eps - rho
     F, BT = bound_factor_table(D, P)
     Dpow = [1.0]

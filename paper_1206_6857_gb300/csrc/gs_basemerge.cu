@@ -20,26 +20,6 @@
 // (Section 1's sum term, DITOBase of Fig. 7).  Sums: FP32 over the terms of
 // one reference leaf, then compensated (Kahan) FP32 per (bandwidth, query)
 // across leaves, then FP64 across warps.
-//
-// Expanded squared distance (FP32 points, D <= 8, not in the paper): with u =
-// q - c_R and v = r - c_R about the reference leaf's FP32 centre,
-// ||q - r||^2 = (|v|^2 - 2 u.v) + |u|^2.  Per reference the records hold
-// -2v, |v|^2 and l = log2(w / w_max); per (query, leaf pair) |u|^2 is formed
-// once; per (query, reference) D fused multiply-adds and one addition replace
-// the D subtractions and D multiply-adds of the direct form.  Error (first
-// order in u = 2^-24, rho_R the Euclidean radius of R about c_R, d =
-// ||q - r||, arg = c d^2 + l):
-//   |arg~ - arg| <= |c| u [(D+4) d^2 + (4D+4) d rho_R + 5D rho_R^2] + u |arg~|
-// (u and v rounded once each: 2 d (|u| + |v|); |u|^2 and |v|^2 as FMA chains:
-// D |u|^2 and D |v|^2; the chain -2 u.v + |v|^2: D (|v|^2 + 2 |u| |v|); the
-// addition of |u|^2 and c's rounding: d^2 each; the last FMA: |arg|), with
-// |u| <= d + rho_R and |v| <= rho_R.  The relative part is charged like the
-// direct kernel's argument rounding (D+5 there with l's rounding, D+6 here),
-// over exponents down to 2^-64; the absolute part, at d <= 9.42 h and the bandwidth h of
-// each mask bit, must stay within tau = 2^kXpGuardLog2 in log2 units, else
-// that bit of the leaf pair stays with the direct kernel.  The traversal's
-// FP32 charge carries ln2 (128 u + tau) whenever this path is enabled (two
-// roundings of the argument, one of them slack).
 #include <limits.h>
 #include <math.h>
 
@@ -153,15 +133,7 @@ struct MergedParams {
     double *Gq;
     const Ingest *ing;
     unsigned long long *evals;
-    // expanded-distance path
-    const float *rxp;        // per reference: (-2 v_d, -2 v_d) for d < DP, (|v|^2, |v|^2), (l, l), padding
-    const float *rc32;       // per reference leaf: FP32 centre c_R (8 floats)
-    unsigned long long *evals_x;   // terms of this kernel (besides evals)
 };
-
-// floats per expanded-distance reference record: DP + 2 duplicated pairs,
-// rounded up to 16-byte units
-__host__ __device__ constexpr int xp_rec_floats(int DP) { return ((2 * (DP + 2)) + 3) / 4 * 4; }
 
 // Sum over one reference leaf (staged in shared memory) for NJ bandwidths
 // at once: one squared distance per (query, reference), NJ exponentials.
@@ -238,46 +210,6 @@ __device__ __forceinline__ void leaf_terms_x2(const f2_t (&xq)[QPL / 2][DP], con
     }
 }
 
-// leaf_terms_x2 on the expanded squared distance: two query slots per
-// register pair; the staged record of a reference is (m_d, m_d) for
-// m_d = -2 v_d, then (|v|^2, |v|^2) and (l, l), l = log2(w / w_max); per slot
-// pair u2 holds the queries' u = q - c_R and b2 their |u|^2.  Per (query,
-// reference) D FFMAs (|v|^2 - 2 u.v) and one FADD (+ |u|^2); per bandwidth
-// one FFMA (argument c_k d^2 + l), one ex2 and one FADD, as the direct form.
-template <int DP, int QPL, int NJ>
-__device__ __forceinline__ void leaf_terms_xp(const f2_t (&u2)[QPL / 2][DP], const f2_t (&b2)[QPL / 2],
-                                              const ulonglong2 *rp, int nr, const f2_t (&c)[8],
-                                              f2_t (&part)[QPL / 2][8]) {
-    constexpr int NP = xp_rec_floats(DP) / 2;   // pairs per staged record
-#pragma unroll
-    for (int s = 0; s < QPL / 2; ++s)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) part[s][k] = 0ull;
-#pragma unroll 4
-    for (int i = 0; i < nr; ++i) {
-        f2_t rv[NP];
-#pragma unroll
-        for (int v = 0; v < NP / 2; ++v) {
-            const ulonglong2 u = rp[i * (NP / 2) + v];
-            rv[2 * v] = u.x;
-            rv[2 * v + 1] = u.y;
-        }
-#pragma unroll
-        for (int s = 0; s < QPL / 2; ++s) {
-            f2_t t = rv[DP];
-#pragma unroll
-            for (int d = 0; d < DP; ++d) t = f2_fma(u2[s][d], rv[d], t);
-            t = f2_add(t, b2[s]);
-#pragma unroll
-            for (int k = 0; k < NJ; ++k) {
-                float a0, a1;
-                f2_unpack(f2_fma(t, c[k], rv[DP + 1]), a0, a1);
-                part[s][k] = f2_add(part[s][k], f2_pack(ex2_approx(a0), ex2_approx(a1)));
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
@@ -294,18 +226,13 @@ constexpr int kBlk = 8;   // bandwidths accumulated per pass
 // the bandwidths a leaf pair needs are consecutive; the CTA makes one pass
 // over its entries per block of kBlk bandwidths, blocks starting at the
 // lowest bandwidth any of its entries needs.
-//
-// XP: the expanded squared distance (packed path, FP32 points only): the
-// staged records are the expanded-distance ones and each leaf pair's query
-// values are taken about the reference leaf's centre.
-template <int DP, int QPL, bool ANCH, bool XP>
-__global__ void __launch_bounds__(32 * kMW, XP ? (QPL == 2 ? 5 : 4) : 1)
+template <int DP, int QPL, bool ANCH>
+__global__ void __launch_bounds__(32 * kMW)
 k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const long long *__restrict__ off,
                   int64_t lq, int lmax) {
     constexpr int NT = RefRec<float, DP>::NT;
     constexpr bool X2 = merged_x2(DP, QPL);
-    static_assert(!XP || (X2 && !ANCH), "the expanded form runs on the packed FP32 path");
-    constexpr int NS = XP ? xp_rec_floats(DP) : (X2 ? 2 * NT : NT);   // floats per staged reference record
+    constexpr int NS = X2 ? 2 * NT : NT;   // floats per staged reference record
     constexpr int KS = kBlk * QPL * 32;
     extern __shared__ float sm_f[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -334,7 +261,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
         const int64_t ri = ent[e].r - rleaf0;
         const int64_t rb = level_begin(bp.rn, bp.r_depth, ri), re = level_begin(bp.rn, bp.r_depth, ri + 1);
         const int nv = (int)(re - rb) * (NS / 4);
-        const float4 *src = reinterpret_cast<const float4 *>((XP ? bp.rxp : (X2 ? bp.rrec2 : bp.rrec)) + rb * NS);
+        const float4 *src = reinterpret_cast<const float4 *>((X2 ? bp.rrec2 : bp.rrec) + rb * NS);
         float4 *dst = reinterpret_cast<float4 *>(stage + (size_t)b * lmax * NS);
         for (int v = lane; v < nv; v += 32) cp_async16(dst + v, src + v);
         cp_async_commit();
@@ -353,7 +280,6 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
     un = 0u;
 #pragma unroll
     for (int ww = 0; ww < kMW; ++ww) un |= s_union[ww];
-    if (un == 0u) return;   // every entry of this row belongs to the other kernel
     const int b0 = __ffs(un) - 1, b1 = 31 - __clz(un);
     const int nblk = (b1 - b0) / kBlk + 1;
     for (int jb = 0; jb < nblk; ++jb) {
@@ -388,32 +314,6 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
             const float *rp = stage + (size_t)buf * lmax * NS;
             uint32_t m = (E.mask & bmask) >> sh;
             evals += (unsigned long long)__popc(m) * (unsigned long long)nr;
-            // expanded form: u = q - c_R and |u|^2 per query slot (one leaf pair)
-            constexpr int QX = XP ? QPL / 2 : 1;
-            f2_t xu2[QX][DP], xb2[QX];
-            if constexpr (XP) {
-                float cr[DP];
-#pragma unroll
-                for (int d = 0; d < DP; ++d) cr[d] = bp.rc32[ri * 8 + d];
-#pragma unroll
-                for (int h2 = 0; h2 < QX; ++h2) {
-                    float ua[DP], ub[DP];
-#pragma unroll
-                    for (int d = 0; d < DP; ++d) {
-                        ua[d] = xq[2 * h2][d] - cr[d];
-                        ub[d] = xq[2 * h2 + 1][d] - cr[d];
-                    }
-                    float ba = ua[0] * ua[0], bb = ub[0] * ub[0];
-#pragma unroll
-                    for (int d = 1; d < DP; ++d) {
-                        ba = fmaf(ua[d], ua[d], ba);
-                        bb = fmaf(ub[d], ub[d], bb);
-                    }
-#pragma unroll
-                    for (int d = 0; d < DP; ++d) xu2[h2][d] = f2_pack(ua[d], ub[d]);
-                    xb2[h2] = f2_pack(ba, bb);
-                }
-            }
             while (m) {
                 int ks[8];
                 float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -426,27 +326,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                     ++nj;
                 }
                 float part[QPL][8];
-                if constexpr (XP) {
-                    constexpr int QH = QPL / 2;
-                    f2_t c2[8], part2[QH][8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) c2[k] = f2_pack(c[k], c[k]);
-                    const ulonglong2 *rp2 = reinterpret_cast<const ulonglong2 *>(rp);
-                    switch (nj) {
-                        case 1: leaf_terms_xp<DP, QPL, 1>(xu2, xb2, rp2, nr, c2, part2); break;
-                        case 2: leaf_terms_xp<DP, QPL, 2>(xu2, xb2, rp2, nr, c2, part2); break;
-                        case 3: leaf_terms_xp<DP, QPL, 3>(xu2, xb2, rp2, nr, c2, part2); break;
-                        case 4: leaf_terms_xp<DP, QPL, 4>(xu2, xb2, rp2, nr, c2, part2); break;
-                        case 5: leaf_terms_xp<DP, QPL, 5>(xu2, xb2, rp2, nr, c2, part2); break;
-                        case 6: leaf_terms_xp<DP, QPL, 6>(xu2, xb2, rp2, nr, c2, part2); break;
-                        case 7: leaf_terms_xp<DP, QPL, 7>(xu2, xb2, rp2, nr, c2, part2); break;
-                        default: leaf_terms_xp<DP, QPL, 8>(xu2, xb2, rp2, nr, c2, part2); break;
-                    }
-#pragma unroll
-                    for (int h2 = 0; h2 < QH; ++h2)
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) f2_unpack(part2[h2][k], part[2 * h2][k], part[2 * h2 + 1][k]);
-                } else if constexpr (X2) {
+                if constexpr (X2) {
                     constexpr int QH = QPL / 2 > 0 ? QPL / 2 : 1;
                     f2_t xq2[QH][DP], dc2[DP], c2[8], part2[QH][8];
 #pragma unroll
@@ -481,9 +361,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                         default: leaf_terms<DP, QPL, ANCH, 4>(xq, dc, rp4, nr, c, part); break;
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (k >= nj) break;
+                for (int k = 0; k < nj; ++k) {
 #pragma unroll
                     for (int s = 0; s < QPL; ++s) {
                         const int slot = (ks[k] * QPL + s) * 32 + lane;
@@ -514,35 +392,25 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
         __syncthreads();
     }
     if (bp.evals && lane == 0 && evals) atomicAdd(bp.evals, evals * (unsigned long long)nq);
-    if (XP && bp.evals_x && lane == 0 && evals) atomicAdd(bp.evals_x, evals * (unsigned long long)nq);
 }
 
 template <int DP>
-static int launch_merged_dp(int qpl, bool anch, bool xp, const MergedParams &bp, const MergedEntry *ent,
-                            const long long *off, int64_t lq, int lmax, cudaStream_t st) {
+static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const MergedEntry *ent, const long long *off,
+                            int64_t lq, int lmax, cudaStream_t st) {
     constexpr int NT = RefRec<float, DP>::NT;
     // shared memory sized from the instantiated QPL (the kernel indexes with it)
-#define GS_M(Q, A, X)                                                                               \
+#define GS_M(Q, A)                                                                                  \
     do {                                                                                            \
-        const size_t ns = (X) ? xp_rec_floats(DP) : (merged_x2(DP, Q) ? 2 * NT : NT);                \
+        const size_t ns = merged_x2(DP, Q) ? 2 * NT : NT;                                            \
         const size_t sm = (size_t)kMW * (2 * kBlk * (Q) * 32 + 2 * lmax * ns) * sizeof(float);     \
         if (sm > 220 * 1024) return GS_ERR_UNSUPPORTED;                                             \
-        allow_max_smem((const void *)k_basecase_merged<DP, Q, A, X>);                                \
-        k_basecase_merged<DP, Q, A, X><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq, lmax); \
+        allow_max_smem((const void *)k_basecase_merged<DP, Q, A>);                                   \
+        k_basecase_merged<DP, Q, A><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq, lmax);    \
     } while (0)
-    if (xp) {
-        if constexpr (DP <= 8) {
-            if (qpl <= 1 || anch) return GS_ERR_UNSUPPORTED;
-            if (qpl <= 2) GS_M(2, false, true); else GS_M(4, false, true);
-            return GS_OK;
-        } else {
-            return GS_ERR_UNSUPPORTED;
-        }
-    }
     if (anch) {
-        if (qpl <= 1) GS_M(1, true, false); else if (qpl <= 2) GS_M(2, true, false); else GS_M(4, true, false);
+        if (qpl <= 1) GS_M(1, true); else if (qpl <= 2) GS_M(2, true); else GS_M(4, true);
     } else {
-        if (qpl <= 1) GS_M(1, false, false); else if (qpl <= 2) GS_M(2, false, false); else GS_M(4, false, false);
+        if (qpl <= 1) GS_M(1, false); else if (qpl <= 2) GS_M(2, false); else GS_M(4, false);
     }
 #undef GS_M
     return GS_OK;
@@ -550,9 +418,9 @@ static int launch_merged_dp(int qpl, bool anch, bool xp, const MergedParams &bp,
 
 // shared memory of the merged kernel for records of NT floats, query slots
 // per lane qpl (instantiated as 1, 2 or 4) and leaves of at most lmax points
-static size_t merged_smem(int DP, int NT, int qpl, int lmax, bool xp = false) {
+static size_t merged_smem(int DP, int NT, int qpl, int lmax) {
     const int Q = qpl <= 1 ? 1 : (qpl <= 2 ? 2 : 4);
-    const size_t ns = xp ? xp_rec_floats(DP) : (merged_x2(DP, Q) ? 2 * NT : NT);
+    const size_t ns = merged_x2(DP, Q) ? 2 * NT : NT;
     return (size_t)kMW * (2 * kBlk * Q * 32 + 2 * lmax * ns) * sizeof(float);
 }
 
@@ -571,130 +439,7 @@ bool merged_base_possible(const TraversalIn &in) {
     const int NT = (int)(((DP + 1) * sizeof(float) + 15) / 16) * 4;
     (void)lq;
     (void)lr;
-    return in.nh <= 32 && qpl <= 4 && merged_smem(DP, NT, qpl, lmax) <= 220 * 1024 &&
-           (DP > 8 || merged_smem(DP, NT, qpl, lmax, true) <= 220 * 1024);
-}
-
-// ---------------------------------------------------------------------------
-// expanded-distance path: per reference leaf its FP32 centre, the records
-// about it and the mask bits whose bandwidth passes the error guard
-// ---------------------------------------------------------------------------
-constexpr int kXpGuardLog2 = -13;   // tau: absolute exponent error allowed (log2 units)
-
-struct XpGuard {
-    double k_lin;       // u log2(e) / 2 (4D+7) 9.42        (times rho_R / h)
-    double k_sq;        // u log2(e) / 2 (5D+2)             (times rho_R^2 / h^2)
-    double tau;
-    double inv_h[32];   // by mask bit: 1 / h
-    int nh;
-};
-
-// One CTA (128 threads) per reference leaf.  Records: m_d = -2 fl(r_d - c_d),
-// |v|^2 (the FMA chain the error bound assumes) and the direct records' l,
-// each duplicated; the Euclidean radius about c_R in FP64 (x and c are FP32,
-// so x - c is exact), rounded up; pass[i] = the mask bits b whose guard
-// u log2(e)/2 [(4D+7) 9.42 rho_R / h_b + (5D+2) rho_R^2 / h_b^2] <= tau
-// (coefficients above the bound's first-order ones: second-order slack).
-// The guard decreases with h and bits rank bandwidths by ascending h, so the
-// passing bits are the top ones.
-template <int DP>
-__global__ void __launch_bounds__(128) k_xp_leaves(const float *__restrict__ rec, int rec_stride, int64_t n,
-                                                   int depth, const double *__restrict__ center, int D,
-                                                   XpGuard g, float *rxp, float *c32, uint32_t *pass) {
-    constexpr int NS = xp_rec_floats(DP);
-    __shared__ double s_rad[4];
-    const int64_t i = blockIdx.x;
-    const int t = threadIdx.x;
-    const int64_t node = ((int64_t)1 << depth) - 1 + i;
-    const int64_t b = level_begin(n, depth, i), e = level_begin(n, depth, i + 1);
-    float c[DP];
-#pragma unroll
-    for (int d = 0; d < DP; ++d) c[d] = d < D ? (float)center[node * D + d] : 0.f;
-    double r2 = 0.0;
-    for (int64_t p = b + t; p < e; p += blockDim.x) {
-        float v[DP];
-        double q2 = 0.0;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) {
-            const float x = d < D ? rec[p * rec_stride + d] : 0.f;
-            v[d] = x - c[d];
-            const double dx = (double)x - (double)c[d];
-            q2 += dx * dx;
-        }
-        r2 = fmax(r2, q2);
-        float s = v[0] * v[0];
-#pragma unroll
-        for (int d = 1; d < DP; ++d) s = fmaf(v[d], v[d], s);
-        const float l = rec[p * rec_stride + DP];   // log2(w / w_max), as the direct kernel's records
-        float *o = rxp + p * NS;
-#pragma unroll
-        for (int d = 0; d < DP; ++d) {
-            o[2 * d] = -2.f * v[d];
-            o[2 * d + 1] = -2.f * v[d];
-        }
-        o[2 * DP] = s;
-        o[2 * DP + 1] = s;
-        o[2 * DP + 2] = l;
-        o[2 * DP + 3] = l;
-#pragma unroll
-        for (int k = 2 * DP + 4; k < NS; ++k) o[k] = 0.f;
-    }
-    for (int o = 16; o > 0; o >>= 1) r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
-    if ((t & 31) == 0) s_rad[t >> 5] = r2;
-    __syncthreads();
-    if (t == 0) {
-        r2 = fmax(fmax(s_rad[0], s_rad[1]), fmax(s_rad[2], s_rad[3]));
-        const double rad = sqrt(r2) * (1.0 + 1e-12);
-        for (int d = 0; d < 8; ++d) c32[i * 8 + d] = d < DP ? c[d] : 0.f;
-        int bmin = 32;
-        for (int bit = 0; bit < g.nh; ++bit) {
-            const double x = rad * g.inv_h[bit];
-            if (g.k_lin * x + g.k_sq * x * x <= g.tau) {
-                bmin = bit;
-                break;
-            }
-        }
-        pass[i] = bmin >= 32 ? 0u : (0xFFFFFFFFu << bmin);
-    }
-}
-
-// Every merged entry split by its reference leaf's passing bits: those go to
-// ent_x (same offsets), the rest stay in ent.
-__global__ void k_xp_split(MergedEntry *ent, int64_t total, const uint32_t *__restrict__ pass, int64_t rleaf0,
-                           MergedEntry *ent_x) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        MergedEntry E = ent[e];
-        const uint32_t pm = pass[E.r - rleaf0];
-        MergedEntry X;
-        X.r = E.r;
-        X.mask = E.mask & pm;
-        ent_x[e] = X;
-        E.mask &= ~pm;
-        ent[e] = E;
-    }
-}
-
-bool xp_base_enabled(int D, int dtype, int flags, int64_t qn, int q_depth, int64_t rn, int r_depth, int nh) {
-    if (D > 8 || dtype != GS_F32 || (flags & GS_FLAG_NO_XP) || nh > 32) return false;
-    const int64_t maxq = (qn + (1ll << q_depth) - 1) >> q_depth;
-    const int64_t maxr = (rn + (1ll << r_depth) - 1) >> r_depth;
-    return maxq > 32 && maxq <= 128 && maxr <= 128;
-}
-
-// extra charge on top of the direct base case's: two more roundings of the
-// exponent argument over exponents down to 2^-64 (one needed, one slack) and
-// the guard's tau
-double xp_charge() {
-    const double u = 5.9604644775390625e-08;
-    return 0.6931471805599453 * (64.0 * 2.0 * u + ldexp(1.0, kXpGuardLog2));
-}
-
-template <int DP>
-static void launch_xp_leaves(const TraversalIn &in, const XpGuard &g, float *rxp, float *c32, uint32_t *pass,
-                             cudaStream_t st) {
-    const TreeDev &t = *in.rt;
-    k_xp_leaves<DP><<<(unsigned)(1ll << t.depth), 128, 0, st>>>(t.rec, t.rec_stride, t.n, t.depth, t.center, t.D,
-                                                               g, rxp, c32, pass);
+    return in.nh <= 32 && qpl <= 4 && merged_smem(DP, NT, qpl, lmax) <= 220 * 1024;
 }
 
 // records with every float duplicated, for the packed path
@@ -716,10 +461,9 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
     }
     int32_t *gidx = nullptr;   // lq x 32: base group of (query leaf, mask bit), -1 if none
     long long *off = nullptr;
-    MergedEntry *ent = nullptr, *ent_dir = nullptr, *ent_x = nullptr;
+    MergedEntry *ent = nullptr, *ent_dir = nullptr;
     long long *off_dir = nullptr;
-    float *rec2 = nullptr, *rxp = nullptr, *xc32 = nullptr;
-    uint32_t *xpass = nullptr;
+    float *rec2 = nullptr;
     // a failed call frees what this phase holds, so the pool gets it back
     auto release = [&]() {
         if (gidx) cudaFreeAsync(gidx, st);
@@ -728,10 +472,6 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         if (ent_dir) cudaFreeAsync(ent_dir, st);
         if (off_dir) cudaFreeAsync(off_dir, st);
         if (rec2) cudaFreeAsync(rec2, st);
-        if (ent_x) cudaFreeAsync(ent_x, st);
-        if (rxp) cudaFreeAsync(rxp, st);
-        if (xc32) cudaFreeAsync(xc32, st);
-        if (xpass) cudaFreeAsync(xpass, st);
     };
 #define GS_TRY_M(call)                        \
     do {                                      \
@@ -767,9 +507,18 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         release();
         return rc0;
     }
+    // the entries: at most one per base-list entry (each has a bandwidth bit),
+    // so small calls size them by that and skip reading the exact count; the
+    // tensor-core split needs the count on the host
+    const bool tc = tc_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth, in.rt->n, in.rt->depth,
+                                    in.nh);
     long long total = 0;
-    GS_TRY_M(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
-    GS_TRY_M(cudaStreamSynchronize(st));
+    if (!tc && (double)fb.n_base * sizeof(MergedEntry) <= 64.0 * 1024 * 1024) {
+        total = fb.n_base;
+    } else {
+        GS_TRY_M(cudaMemcpyAsync(&total, off + lq, sizeof(total), cudaMemcpyDeviceToHost, st));
+        GS_TRY_M(cudaStreamSynchronize(st));
+    }
     GS_TRY_M(dev_malloc_async((void **)&ent, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
     k_row_masks<true><<<mgrid, kMergeThreads, kSlice * sizeof(uint32_t), st>>>(fb.base_groups, fb.base_r, gidx, lq, lr,
                                                                             rleaf0, off, ent);
@@ -802,7 +551,7 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         // summed there; the direct kernel below takes the rest
         const MergedEntry *ent_run = ent;
         const long long *off_run = off;
-        if (tc_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth, in.rt->n, in.rt->depth, in.nh)) {
+        if (tc) {
             double h_by_bit[32];
             for (int b = 0; b < 32; ++b) h_by_bit[b] = b < in.nh ? in.h[order[b]] : 1.0;
             rc = run_basecase_tc(in, ent, off, lq, total, bp.negc, bp.jcol, h_by_bit, Gq, &ent_dir, &off_dir,
@@ -819,89 +568,32 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
         merged_shape(in, qpl, lmax);
         const bool anch = in.qt->dtype == GS_F64;
         const int Q = qpl <= 1 ? 1 : (qpl <= 2 ? 2 : 4);
-        // FP32, D <= 8: the bits whose reference leaf passes the guard go to
-        // the expanded-distance kernel (launched first), the rest stay here
-        const bool xp = xp_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth, in.rt->n,
-                                        in.rt->depth, in.nh) &&
-                        DP <= 8 && merged_x2(DP, Q) && !anch && ent_run == ent;
-        if (xp) {
-            constexpr double u = 5.9604644775390625e-08, hl2e = 0.5 * 1.4426950408889634;
-            XpGuard g;
-            memset(&g, 0, sizeof(g));
-            g.k_lin = u * hl2e * (4.0 * in.D + 7.0) * 9.42;
-            g.k_sq = u * hl2e * (5.0 * in.D + 2.0);
-            g.tau = ldexp(1.0, kXpGuardLog2);
-            g.nh = in.nh;
-            for (int b = 0; b < in.nh; ++b) g.inv_h[b] = 1.0 / in.h[order[b]];
-            const int NSX = xp_rec_floats(DP);
-            GS_TRY_M(dev_malloc_async((void **)&rxp, (size_t)in.rt->n * NSX * sizeof(float), st));
-            GS_TRY_M(dev_malloc_async((void **)&xc32, (size_t)lr * 8 * sizeof(float), st));
-            GS_TRY_M(dev_malloc_async((void **)&xpass, (size_t)lr * sizeof(uint32_t), st));
-            GS_TRY_M(dev_malloc_async((void **)&ent_x, (size_t)(total > 0 ? total : 1) * sizeof(MergedEntry), st));
-            switch (DP) {
-                case 1: launch_xp_leaves<1>(in, g, rxp, xc32, xpass, st); break;
-                case 2: launch_xp_leaves<2>(in, g, rxp, xc32, xpass, st); break;
-                case 3: launch_xp_leaves<3>(in, g, rxp, xc32, xpass, st); break;
-                case 4: launch_xp_leaves<4>(in, g, rxp, xc32, xpass, st); break;
-                case 5: launch_xp_leaves<5>(in, g, rxp, xc32, xpass, st); break;
-                case 6: launch_xp_leaves<6>(in, g, rxp, xc32, xpass, st); break;
-                case 7: launch_xp_leaves<7>(in, g, rxp, xc32, xpass, st); break;
-                default: launch_xp_leaves<8>(in, g, rxp, xc32, xpass, st); break;
-            }
-            if (total > 0)
-                k_xp_split<<<grid, 256, 0, st>>>(ent, total, xpass, rleaf0, ent_x);
-            cx.launches += 2;
-            rc = cx.check("expanded-distance records");
-            if (!rc) {
-                MergedParams bx = bp;
-                bx.rxp = rxp;
-                bx.rc32 = xc32;
-                bx.evals_x = fb.evals ? fb.evals + 2 : nullptr;
-                cx.mark(CallCtx::kTimerBase);
-                switch (DP) {
-                    case 1: rc = launch_merged_dp<1>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                    case 2: rc = launch_merged_dp<2>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                    case 3: rc = launch_merged_dp<3>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                    case 4: rc = launch_merged_dp<4>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                    case 5: rc = launch_merged_dp<5>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                    case 6: rc = launch_merged_dp<6>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                    case 7: rc = launch_merged_dp<7>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                    default: rc = launch_merged_dp<8>(qpl, false, true, bx, ent_x, off, lq, lmax, st); break;
-                }
-                cx.mark(-1);
-                cx.launches += 1;
-                cx.launches_base += 1;
-                if (!rc) rc = cx.check("k_basecase_merged (expanded)");
-            }
-        }
-        if (!rc && merged_x2(DP, Q)) {
+        if (merged_x2(DP, Q)) {
             const int64_t nf = in.rt->n * (int64_t)in.rt->rec_stride;
             GS_TRY_M(dev_malloc_async((void **)&rec2, (size_t)nf * 2 * sizeof(float), st));
             k_dup_records<<<grid, 256, 0, st>>>(in.rt->rec, nf, (float2 *)rec2);
             cx.launches += 1;
             bp.rrec2 = rec2;
         }
-        if (!rc) {
-            cx.mark(CallCtx::kTimerBase + 1);
-            switch (DP) {
-                case 1: rc = launch_merged_dp<1>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 2: rc = launch_merged_dp<2>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 3: rc = launch_merged_dp<3>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 4: rc = launch_merged_dp<4>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 5: rc = launch_merged_dp<5>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 6: rc = launch_merged_dp<6>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 7: rc = launch_merged_dp<7>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 8: rc = launch_merged_dp<8>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 12: rc = launch_merged_dp<12>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 16: rc = launch_merged_dp<16>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                case 24: rc = launch_merged_dp<24>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-                default: rc = launch_merged_dp<32>(qpl, anch, false, bp, ent_run, off_run, lq, lmax, st); break;
-            }
-            cx.mark(-1);
-            cx.launches += 1;
-            cx.launches_base += 1;
-            if (!rc) rc = cx.check("k_basecase_merged");
+        cx.mark(CallCtx::kTimerBase + 1);
+        switch (DP) {
+            case 1: rc = launch_merged_dp<1>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 2: rc = launch_merged_dp<2>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 3: rc = launch_merged_dp<3>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 4: rc = launch_merged_dp<4>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 5: rc = launch_merged_dp<5>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 6: rc = launch_merged_dp<6>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 7: rc = launch_merged_dp<7>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 8: rc = launch_merged_dp<8>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 12: rc = launch_merged_dp<12>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 16: rc = launch_merged_dp<16>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            case 24: rc = launch_merged_dp<24>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
+            default: rc = launch_merged_dp<32>(qpl, anch, bp, ent_run, off_run, lq, lmax, st); break;
         }
+        cx.mark(-1);
+        cx.launches += 1;
+        cx.launches_base += 1;
+        if (!rc) rc = cx.check("k_basecase_merged");
     }
     release();
 #undef GS_TRY_M

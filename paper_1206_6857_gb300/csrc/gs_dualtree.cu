@@ -111,10 +111,9 @@ static int alloc_bufs(FrontierBufs &fb, int64_t nodesQ, int nh, const double *h,
     }
     // pageable source: the runtime stages hc before returning, so it may go out of scope
     GS_CUDA_TRY(cudaMemcpyAsync(fb.inv_2h2, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
-    // evals[0]: every base-case term; evals[1]: those of the tensor-core
-    // kernel; evals[2]: those of the expanded-distance kernel
-    GS_ALLOC(fb.evals, 3 * sizeof(unsigned long long));
-    GS_CUDA_TRY(cudaMemsetAsync(fb.evals, 0, 3 * sizeof(unsigned long long), st));
+    // evals[0]: every base-case term; evals[1]: those of the tensor-core kernel
+    GS_ALLOC(fb.evals, 2 * sizeof(unsigned long long));
+    GS_CUDA_TRY(cudaMemsetAsync(fb.evals, 0, 2 * sizeof(unsigned long long), st));
     return GS_OK;
 }
 
@@ -249,7 +248,7 @@ int dualtree_run(const TreeDev &qt_in, const TreeDev &rt_in, bool mono, const fl
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(&hfs, fb.fs, sizeof(hfs), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hing, ing, sizeof(hing), cudaMemcpyDeviceToHost, st);
-        unsigned long long hev2[3] = {0, 0, 0};
+        unsigned long long hev2[2] = {0, 0};
         if (e == cudaSuccess) e = cudaMemcpyAsync(hev2, fb.evals, sizeof(hev2), cudaMemcpyDeviceToHost, st);
         const unsigned long long hev = hev2[0];
         cx.end();
@@ -265,7 +264,6 @@ int dualtree_run(const TreeDev &qt_in, const TreeDev &rt_in, bool mono, const fl
             s->pairs_split = (int64_t)hfs.method_count[M_SPLIT];
             s->point_pairs_base = (int64_t)hev;
             s->point_pairs_tc = (int64_t)hev2[1];
-            s->point_pairs_xp = (int64_t)hev2[2];
             s->levels = (qt.depth > rt.depth ? qt.depth : rt.depth) + 1;
             s->retries = 0;
             s->fp32_rel_bound = hfs.rho;

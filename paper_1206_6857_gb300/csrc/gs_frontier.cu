@@ -691,6 +691,27 @@ k_cols_offsets(const FrontierState *fs, int t, const int32_t *__restrict__ cnt, 
     }
 }
 
+// the same column scan by one CTA, for frontiers of at most kColSmall groups
+// (one launch instead of three)
+constexpr int64_t kColSmall = 4096;
+
+__global__ void __launch_bounds__(kColTB)
+k_cols_small(FrontierState *fs, int t, const int32_t *__restrict__ cnt, long long *off) {
+    __shared__ long long tot;
+    const int64_t ng = fs->ngroups[t];
+    for (int c = 0; c < kCols; ++c) {
+        long long carry = 0;
+        for (int64_t t0 = 0; t0 < ng; t0 += blockDim.x) {
+            const int64_t g = t0 + threadIdx.x;
+            const long long v = g < ng ? cnt[g * kCols + c] : 0;
+            const long long e = block_excl_scan_ll(v, &tot);
+            if (g < ng) off[g * kCols + c] = carry + e;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) fs->totals[c] = carry;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K2: write the child frontier, base pairs and series actions
 // ---------------------------------------------------------------------------
@@ -833,7 +854,7 @@ __global__ void k_front_init(FrontierState *fs, Group *groups, int32_t *pr, int 
         rho = rho + 4.76837158203125e-07;          // 2^-21
         rho = rho + (double)(run + 1) * u;      // FP32 sums over one reference leaf, then compensated
         rho = rho + ldexp(1.0, -63 - floor_log2) * (((double)N * wmax) / W);
-        rho = rho + extra_rho;                   // the tensor-core or expanded-distance base case's charge
+        rho = rho + extra_rho;                   // the tensor-core base case's charge, when enabled
         fs->rho = rho;
         fs->eps_t = eps - rho;
         fs->Wtot = W;
@@ -979,10 +1000,7 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
                                    tc_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth, in.rt->n,
                                                    in.rt->depth, in.nh)
                                        ? tc_charge()
-                                       : (xp_base_enabled(in.D, in.qt->dtype, in.flags, in.qt->n, in.qt->depth,
-                                                          in.rt->n, in.rt->depth, in.nh)
-                                              ? xp_charge()
-                                              : 0.0));
+                                       : 0.0);
     cx.launches += 1;
     if ((rc = cx.check("k_front_init"))) return rc;
     int cur = 0;
@@ -1053,10 +1071,15 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
             k_front_decide<0><<<grid, 256, 0, st>>>(fp, fb.fs, fb.groups[cur], fb.pr[cur], fb.dec, fb.cnt, fb.trace,
                                                     fb.trace_cap);
         if ((rc = cx.check("k_front_decide"))) return rc;
-        k_cols_partial<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial);
-        k_cols_scan_partials<<<1, kColTB, 0, st>>>(fb.fs, fb.partial);
-        k_cols_offsets<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial, fb.off);
-        cx.launches += 4;
+        if (ngb <= kColSmall) {
+            k_cols_small<<<1, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.off);
+            cx.launches += 2;
+        } else {
+            k_cols_partial<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial);
+            k_cols_scan_partials<<<1, kColTB, 0, st>>>(fb.fs, fb.partial);
+            k_cols_offsets<<<kColGrid, kColTB, 0, st>>>(fb.fs, t, fb.cnt, fb.partial, fb.off);
+            cx.launches += 4;
+        }
         if ((rc = cx.check("k_cols_*"))) return rc;
         if (presized) {
             EmitOut eo;
@@ -1124,11 +1147,13 @@ int run_frontier(const TraversalIn &in, FrontierBufs &fb, CallCtx &cx) {
         GS_CUDA_TRY(cudaMemcpyAsync(fb.host_totals, &fb.fs->base_count, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost,
                                     st));
         GS_CUDA_TRY(cudaStreamSynchronize(st));
+        base_count = fb.host_totals[0];
         bgroups = fb.host_totals[1];
         for (int m = 0; m < 3; ++m) ser_count[m] = fb.host_totals[3 + m];
     }
     for (int m = 0; m < 3; ++m) fb.n_series[m] = ser_count[m];
     fb.n_base_groups = bgroups;
+    fb.n_base = base_count;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "frontier launch");
     return GS_OK;

@@ -60,8 +60,8 @@ struct CallCtx {
     void end() { phase(-1); }
     // Time one launch into stats->ms_series[slot] (slot 0-2) or
     // stats->ms_base_kernels[slot - kTimerBase] (kTimerBase: the tensor-core
-    // or expanded-distance kernel, kTimerBase + 1: the direct one):
-    // mark(slot) before it, mark(-1) after.  No-op without stats.
+    // kernel, kTimerBase + 1: the direct one): mark(slot) before it, mark(-1)
+    // after.  No-op without stats.
     static constexpr int kMaxTimers = 24;
     static constexpr int kTimerBase = 3;
     cudaEvent_t tev[kMaxTimers];
@@ -230,6 +230,7 @@ struct FrontierBufs {
     int64_t cap_geo = 0;
     int64_t n_series[3] = {0, 0, 0};// actions per list after the traversal (host copy)
     int64_t n_base_groups = 0;
+    int64_t n_base = 0;             // base-case list entries (query leaf, bandwidth, reference leaf)
     int grid_warps = 0;
     int64_t *host_totals = nullptr; // pinned host scratch (kCols + 8 int64)
 };
@@ -249,11 +250,6 @@ int run_basecase_merged(const TraversalIn &in, FrontierBufs &fb, double *Gq, int
 // Tensor-core base case (9 <= D <= 16, FP32 points, leaves of at most 128
 // points): whether a call takes it, and the extra FP32 charge it needs.
 bool tc_base_enabled(int D, int dtype, int flags, int64_t qn, int q_depth, int64_t rn, int r_depth, int nh);
-// Expanded-distance base case (FP32 points, D <= 8, query leaves of 33..128
-// points): whether a call's FP32 charge includes it (GS_FLAG_NO_MERGE leaves
-// the charge in place but runs the per-bandwidth kernel), and that charge.
-bool xp_base_enabled(int D, int dtype, int flags, int64_t qn, int q_depth, int64_t rn, int r_depth, int nh);
-double xp_charge();
 double tc_charge();
 // Splits the merged entries (ent, off over lq query-leaf rows) between the
 // tensor-core kernel (entries whose pair passes the error guard) and the

@@ -339,15 +339,49 @@ __global__ void k_part_scatter(const T *__restrict__ xs, const int32_t *__restri
 // bounding box, its split dimension, the radix select of the split rank and
 // the stable scatter, with the same arithmetic and order as the per-level
 // kernels above (so the tree is identical); used for the levels whose nodes
-// hold at most kNodeFused points, where the per-level kernels are launch-bound
+// hold at most kNodeFused points, where the per-level kernels are launch-bound.
+// The node's keys in the split dimension are staged in shared memory once, so
+// the select passes and the scatter read no global memory.
 // --------------------------------------------------------------------------
 constexpr int64_t kNodeFused = 16384;
 
-template <typename T>
-__global__ void __launch_bounds__(kTB)
+// exclusive block-wide scan for NT threads (NT a multiple of 32, at most 1024)
+template <int NT>
+__device__ __forceinline__ unsigned long long block_excl_scan_n(unsigned long long v, unsigned long long *tot) {
+    __shared__ unsigned long long wsum[NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned long long s = lane < NT / 32 ? wsum[lane] : 0ull;
+        unsigned long long si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += u;
+        }
+        if (lane < NT / 32) wsum[lane] = si - s;
+        if (lane == NT / 32 - 1) *tot = si;
+    }
+    __syncthreads();
+    const unsigned long long r = wsum[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
 k_level_node(const T *__restrict__ xs, const int32_t *__restrict__ perm, int64_t n, int D, int k,
              int32_t *split_dim, T *xs_out, int32_t *perm_out, unsigned *status) {
     using K = typename Key<T>::K;
+    extern __shared__ unsigned long long s_dyn[];
+    K *s_key = reinterpret_cast<K *>(s_dyn);   // the node's keys in the split dimension
     __shared__ K s_min[32], s_max[32];
     __shared__ uint32_t s_hist[256];
     __shared__ K s_prefix;
@@ -358,6 +392,7 @@ k_level_node(const T *__restrict__ xs, const int32_t *__restrict__ perm, int64_t
     const int64_t i = blockIdx.x;
     const int lane = threadIdx.x & 31;
     const int64_t b = level_begin(n, k, i), e = level_begin(n, k, i + 1);
+    const int cnt = (int)(e - b);
     const int64_t mid = ((2 * i + 1) * n) >> (k + 1);
     // bounding box (order-preserving keys)
     for (int d = threadIdx.x; d < D; d += blockDim.x) {
@@ -400,16 +435,24 @@ k_level_node(const T *__restrict__ xs, const int32_t *__restrict__ perm, int64_t
     }
     __syncthreads();
     const int dim = s_dim;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) s_key[q] = Key<T>::enc(xs[(b + q) * D + dim]);
     // radix select of rank (mid - b), 8 bits per pass from the top
     for (int shift = Key<T>::BITS - 8; shift >= 0; shift -= 8) {
         for (int t = threadIdx.x; t < 256; t += blockDim.x) s_hist[t] = 0u;
         __syncthreads();
         const K prefix = s_prefix;
         const bool all_match = shift + 8 >= Key<T>::BITS;
-        for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
-            const K key = Key<T>::enc(xs[p * D + dim]);
-            if (all_match || ((key ^ prefix) >> (shift + 8)) == 0)
-                atomicAdd(&s_hist[(unsigned)(key >> shift) & 255u], 1u);
+        // warp-aggregated: lanes with the same digit add once (the top digits
+        // of nearby coordinates are mostly equal)
+        for (int q0 = threadIdx.x & ~31; q0 < cnt; q0 += blockDim.x) {
+            const int q = q0 + lane;
+            unsigned digit = 256u;   // no count
+            if (q < cnt) {
+                const K key = s_key[q];
+                if (all_match || ((key ^ prefix) >> (shift + 8)) == 0) digit = (unsigned)(key >> shift) & 255u;
+            }
+            const unsigned same = __match_any_sync(0xffffffffu, digit);
+            if (digit < 256u && lane == __ffs(same) - 1) atomicAdd(&s_hist[digit], (unsigned)__popc(same));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -448,15 +491,16 @@ k_level_node(const T *__restrict__ xs, const int32_t *__restrict__ perm, int64_t
     const int64_t r_eq = s_rem;
     // stable scatter: (less, equal) counts before each point by a block scan
     unsigned long long carry = 0;
-    for (int64_t t0 = b; t0 < e; t0 += blockDim.x) {
-        const int64_t p = t0 + threadIdx.x;
-        const bool valid = p < e;
-        const K key = valid ? Key<T>::enc(xs[p * D + dim]) : (K)0;
+    for (int q0 = 0; q0 < cnt; q0 += blockDim.x) {
+        const int q = q0 + threadIdx.x;
+        const bool valid = q < cnt;
+        const K key = valid ? s_key[q] : (K)0;
         const unsigned long long f =
             valid ? (((unsigned long long)(key < prefix) << 32) | (unsigned long long)(key == prefix)) : 0ull;
-        const unsigned long long ex = carry + block_excl_scan_u64(f, &s_tot);
+        const unsigned long long ex = carry + block_excl_scan_n<NT>(f, &s_tot);
         carry += s_tot;
         if (!valid) continue;
+        const int64_t p = b + q;
         const int64_t lt_before = (int64_t)(ex >> 32);
         const int64_t eq_before = (int64_t)(ex & 0xffffffffull);
         const int64_t left_before = lt_before + (eq_before < r_eq ? eq_before : r_eq);
@@ -514,6 +558,24 @@ __global__ void k_internal_stats(int D, int k, double *lo, double *hi, double *W
         }
         W[node] = W[l] + W[r];
         wmin[node] = fminf(wmin[l], wmin[r]);
+    }
+}
+
+// every internal level, bottom up, in one CTA (small trees: one launch
+// instead of one per level); same operations as k_internal_stats
+__global__ void k_internal_stats_all(int D, int depth, double *lo, double *hi, double *W, float *wmin) {
+    for (int k = depth - 1; k >= 0; --k) {
+        const int64_t nn = 1ll << k;
+        for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) {
+            const int64_t node = nn - 1 + i, l = 2 * node + 1, r = 2 * node + 2;
+            for (int d = 0; d < D; ++d) {
+                lo[node * D + d] = fmin(lo[l * D + d], lo[r * D + d]);
+                hi[node * D + d] = fmax(hi[l * D + d], hi[r * D + d]);
+            }
+            W[node] = W[l] + W[r];
+            wmin[node] = fminf(wmin[l], wmin[r]);
+        }
+        __syncthreads();
     }
 }
 
@@ -889,8 +951,16 @@ static int build_impl(const T *x, const float *w, int64_t n, int D, int L, const
         const int64_t nn = 1ll << k;
         if (((n + nn - 1) >> k) <= kNodeFused) {
             // every node of this level has at most kNodeFused points: one launch
-            k_level_node<T><<<(unsigned)nn, kTB, 0, st>>>(xa, pa, n, D, k, t.split_dim, xb, pb,
-                                                         (unsigned *)&ing->status);
+            const int64_t seg = (n + nn - 1) >> k;   // the largest node of the level
+            const size_t sm = (size_t)seg * sizeof(K);
+            if (seg > 2048) {
+                GS_CUDA_TRY(allow_max_smem((const void *)k_level_node<T, 1024>));
+                k_level_node<T, 1024><<<(unsigned)nn, 1024, sm, st>>>(xa, pa, n, D, k, t.split_dim, xb, pb,
+                                                                      (unsigned *)&ing->status);
+            } else {
+                k_level_node<T, 256><<<(unsigned)nn, 256, sm, st>>>(xa, pa, n, D, k, t.split_dim, xb, pb,
+                                                                    (unsigned *)&ing->status);
+            }
             cx.launches += 1;
             if (int rc = cx.check("tree level (per node)")) return rc;
             T *tx = xa; xa = xb; xb = tx;
@@ -919,9 +989,14 @@ static int build_impl(const T *x, const float *w, int64_t n, int D, int L, const
     }
     k_leaf_stats<T><<<gridn(1ll << t.depth), kTB, 0, st>>>(xa, pa, w, n, D, t.depth, t.lo, t.hi, t.W, t.wmin);
     cx.launches += 1;
-    for (int k = t.depth - 1; k >= 0; --k) {
-        k_internal_stats<<<gridn(1ll << k), kTB, 0, st>>>(D, k, t.lo, t.hi, t.W, t.wmin);
+    if (t.depth <= 12) {
+        k_internal_stats_all<<<1, 1024, 0, st>>>(D, t.depth, t.lo, t.hi, t.W, t.wmin);
         cx.launches += 1;
+    } else {
+        for (int k = t.depth - 1; k >= 0; --k) {
+            k_internal_stats<<<gridn(1ll << k), kTB, 0, st>>>(D, k, t.lo, t.hi, t.W, t.wmin);
+            cx.launches += 1;
+        }
     }
     k_center_rad<<<gridn(nodes), kTB, 0, st>>>(nodes, D, t.lo, t.hi, t.center, t.rad, t.rad32, t.lo32, t.hi32, t.W, t.W32d, t.W32u);
     k_pack_sorted<T><<<gridn(n), kTB, 0, st>>>(xa, pa, with_weights ? w : nullptr, n, D, DP, rec_stride, t.depth,

@@ -38,7 +38,6 @@ GS_FLAG_NO_MERGE = 1
 GS_FLAG_SMALL_EXHAUSTIVE = 2
 GS_FLAG_NO_TC = 4
 GS_FLAG_BEST_FIRST = 8
-GS_FLAG_NO_XP = 16
 GS_SMALL_WORK = 549755813888.0
 
 GS_MLP_NIN = 12
@@ -75,8 +74,7 @@ class gs_stats(ctypes.Structure):
                 ("retries", ctypes.c_int32), ("fp32_rel_bound", ctypes.c_double),
                 ("eps_traversal", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_phase", ctypes.c_double * GS_NPHASE), ("ms_series", ctypes.c_double * 3),
-                ("point_pairs_tc", ctypes.c_int64), ("point_pairs_xp", ctypes.c_int64),
-                ("ms_base_kernels", ctypes.c_double * 2)]
+                ("point_pairs_tc", ctypes.c_int64), ("ms_base_kernels", ctypes.c_double * 2)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_

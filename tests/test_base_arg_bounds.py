@@ -1,25 +1,20 @@
-"""CPU pins of the base-case kernels' exponent-argument error bounds.
+"""CPU pin of the direct base-case kernel's exponent-argument error bound.
 
 The direct kernel forms c ||q - r||^2 + l as fma(d2, c, l) with d2 an FMA
 chain of the rounded coordinate differences; its charge per term is
 (D+5) u |arg| (the differences 2, the chain D, c 1, the FMA 1, the rounding
-of l 1).  The expanded-distance kernel forms the exponent argument c ||q - r||^2 + l as
-c ((|v|^2 - 2 u.v) + |u|^2) + l with u = q - c_R, v = r - c_R about the
-reference leaf's FP32 centre, in FP32 with fused multiply-adds.  This test
-replays that exact sequence of FP32 operations in exact rational arithmetic
-(every operation rounded once to FP32, round-to-nearest-even) on random and
-adversarial leaf pairs and checks the first-order bound the library charges
-(oracle.dualtree.xp_arg_bound plus the rounding of l) against the exact
-argument.  A dropped term in the bound (the input roundings, the |u|^2
-chain, the final FMA) or a wrong anchor radius fails it.
+of l 1).  This test replays that exact sequence of FP32 operations in exact
+rational arithmetic (every operation rounded once to FP32,
+round-to-nearest-even) on random leaf pairs and checks the bound against the
+exact argument.
 """
+
 from fractions import Fraction as Fr
 import math
 
 import numpy as np
 import pytest
 
-from oracle import dualtree as T
 
 U = 2.0 ** -24
 
@@ -47,27 +42,6 @@ def rnd32(x: Fr) -> Fr:
 
 def f32(x: float) -> Fr:
     return Fr(float(np.float32(x)))
-
-
-def kernel_arg(q, r, c, cf, l):
-    """The kernel's FP32 operations, each rounded once: v = fl(r - c),
-    m = -2 v, s = |v|^2 by an FMA chain, u = fl(q - c), b = |u|^2 by an FMA
-    chain, t = fma chain of u_d m_d onto s, t = fl(t + b), arg = fma(t, cf, l)."""
-    D = len(q)
-    v = [rnd32(r[d] - c[d]) for d in range(D)]
-    m = [-2 * vd for vd in v]
-    s = rnd32(v[0] * v[0])
-    for d in range(1, D):
-        s = rnd32(v[d] * v[d] + s)
-    u = [rnd32(q[d] - c[d]) for d in range(D)]
-    b = rnd32(u[0] * u[0])
-    for d in range(1, D):
-        b = rnd32(u[d] * u[d] + b)
-    t = s
-    for d in range(D):
-        t = rnd32(u[d] * m[d] + t)
-    t = rnd32(t + b)
-    return rnd32(t * cf + l)
 
 
 def direct_arg(q, r, cf, l):
@@ -99,55 +73,6 @@ def _case(rng, D, h, rho_frac, d_frac, centre_scale):
     dirq /= np.linalg.norm(dirq)
     q = [f32(float(r[d]) + dirq[d] * d_frac * h) for d in range(D)]
     return q, r, c, rho
-
-
-@pytest.mark.parametrize("D", [1, 2, 3, 5, 8])
-def test_expanded_argument_within_bound(D):
-    rng = np.random.default_rng(1206685700 + D)
-    worst = 0.0
-    for k in range(150):
-        h = float(10.0 ** rng.uniform(-4, 0))
-        rho_frac = float(10.0 ** rng.uniform(-2, 2))          # leaf radius from 0.01 h to 100 h
-        d_frac = float(rng.choice([0.0, 1e-3, 0.3, 2.0, 9.42]) * rng.uniform(0.5, 1.0))
-        centre_scale = float(10.0 ** rng.uniform(-1, 2))
-        q, r, c, rho = _case(rng, D, h, rho_frac, d_frac, centre_scale)
-        cexact = -1.4426950408889634 / (2.0 * h * h)
-        cf = f32(cexact)
-        w = float(rng.uniform(0.01, 1.0))
-        lexact = math.log2(w)
-        l = f32(lexact)
-        got = kernel_arg(q, r, c, cf, l)
-        d2 = sum((q[i] - r[i]) ** 2 for i in range(D))
-        exact = Fr(cexact) * d2 + Fr(lexact)
-        d = math.sqrt(float(d2))
-        bound = T.xp_arg_bound(D, d, rho, cexact, float(exact)) + U * abs(lexact)
-        err = abs(float(got - exact))
-        assert err <= bound * (1 + 1e-9) + 1e-300, (D, h, rho_frac, d_frac, err, bound)
-        worst = max(worst, err / bound if bound > 0 else 0.0)
-    assert worst > 0.0
-
-
-def test_guard_threshold_matches_bound():
-    """The guard's coefficients dominate the bound's absolute part at
-    d = 9.42 h: (4D+7) 9.42 x + (5D+2) x^2 >= (4D+4) 9.42 x + 5D x^2 for
-    x = rho_R / h, and at d = 9.42 h the term is 2^-64: c d^2 >= 64."""
-    for D in range(1, 9):
-        for x in (0.01, 1.0, 20.0):
-            assert (4 * D + 7) * 9.42 * x + (5 * D + 2) * x * x >= (4 * D + 4) * 9.42 * x + 5 * D * x * x
-    assert 1.4426950408889634 / 2.0 * 9.42 ** 2 >= 64.0
-
-
-def test_xp_charge_and_enabling():
-    u = U
-    assert T.xp_rho() == pytest.approx(math.log(2) * (128 * u + 2.0 ** -13), rel=1e-15)
-    assert T.xp_enabled(3, True, 32, 64, 64)
-    assert not T.xp_enabled(3, True, 32, 32, 64)      # one query per lane: scalar kernel
-    assert not T.xp_enabled(3, False, 32, 64, 64)     # FP64 points
-    assert not T.xp_enabled(9, True, 32, 64, 64)
-    assert not T.xp_enabled(3, True, 33, 64, 64)
-    assert not T.xp_enabled(3, True, 32, 64, 64, no_xp=True)
-    base = T.fp32_rho(3, 1000, 1.0, 1000.0, -40, 64)
-    assert T.fp32_rho(3, 1000, 1.0, 1000.0, -40, 64, xp=True) == pytest.approx(base + T.xp_rho(), rel=1e-15)
 
 
 @pytest.mark.parametrize("D", [1, 2, 3, 5, 8, 16])

@@ -75,8 +75,8 @@ CASES = [
     (10, 6000, 2, None, 1e-2, 32, 0, True, 0, [0.02, 0.1, 0.4], DEF),
     (11, 4000, 3, None, 1e-4, 32, 0, True, 0, [0.05, 0.3], DEF),
     (12, 1500, 12, 1000, 1e-2, 16, 0, True, 0, [0.3, 1.0], DEF),    # tensor-core base case and its charge
-    (13, 5000, 3, None, 1e-2, 64, 0, True, 0, [0.01, 0.05, 0.2], DEF),   # expanded-distance base case
-    (14, 4000, 5, 3000, 1e-3, 128, 0, True, 0, [0.05, 0.3], DEF),        # ... four query slots per lane
+    (13, 5000, 3, None, 1e-2, 64, 0, True, 0, [0.01, 0.05, 0.2], DEF),   # two query slots per lane
+    (14, 4000, 5, 3000, 1e-3, 128, 0, True, 0, [0.05, 0.3], DEF),        # four query slots per lane
 ]
 
 
