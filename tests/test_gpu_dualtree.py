@@ -103,11 +103,21 @@ def _bit_exact_case(gs, case, best_first=False):
     exact = oracle_ex.gauss_sum(q, r, w, h)
     err = rel_err(out.cpu().numpy(), exact, float(w.astype(np.float64).sum()))
     assert err.max() <= eps, err.max()
+    return out
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "s%d_n%d_d%d" % (c[0], c[1], c[2]))
 def test_traversal_bit_exact_and_within_eps(gs, case):
-    _bit_exact_case(gs, case)
+    out = _bit_exact_case(gs, case)
+    # the traced call sizes its lists iteration by iteration on the host; a
+    # plain call of this size reserves them at their worst case and reads no
+    # totals until the end: same decisions, same kernels, same sums
+    seed, n, D, m, eps, leaf, sel, tok, plim, h, cw = case
+    q, r, w = synth.small_random(seed, n, D, m=m)
+    tq = _dev(q)
+    plain = gs.gs_sum(tq, tq if m is None else _dev(r), _dev(w), np.asarray(h, np.float64), eps,
+                      opts=_opts(gs, leaf, sel, tok, plim, cw))
+    assert np.array_equal(plain.cpu().numpy(), out.cpu().numpy())
 
 
 @pytest.mark.parametrize("case", [c for c in CASES if c[0] in (1, 2, 3, 6, 11)],
