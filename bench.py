@@ -53,6 +53,9 @@ def parse():
                     help="Theorem 2 without the token scheme (each pair within its own W_R share)")
     ap.add_argument("--count", type=int, default=256, help="problems in --mode batch")
     ap.add_argument("--workers", type=int, default=16, help="concurrent problems in --mode batch")
+    ap.add_argument("--small-work", type=float, default=0.0,
+                    help="--mode batch: problems with M N nh at most this are summed exhaustively "
+                         "(0: the library's GS_SMALL_WORK)")
     ap.add_argument("--no-small-exhaustive", action="store_true",
                     help="--mode batch: dual tree even for problems whose exact sum is cheaper")
     ap.add_argument("--eps", type=float, default=None, help="override eps (0 = exhaustive)")
@@ -585,9 +588,12 @@ def run_batch(args):
     opts = gs.gs_opts_default()
     if not args.no_small_exhaustive:
         opts.flags |= gs.GS_FLAG_SMALL_EXHAUSTIVE     # small problems: the exact sum is cheaper
+        opts.small_work = args.small_work
     opts, keep = selector_opts(args, opts)
     units = float(sum(float(wl.M) * wl.N * wl.h.size for wl in wls))
-    n_small = sum(1 for wl in wls if float(wl.M) * wl.N * wl.h.size <= gs.GS_SMALL_WORK)
+    def small_work(D):
+        return args.small_work if args.small_work > 0 else (gs.GS_SMALL_WORK_D2 if D <= 2 else gs.GS_SMALL_WORK)
+    n_small = sum(1 for wl in wls if float(wl.M) * wl.N * wl.h.size <= small_work(wl.D))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):

@@ -77,20 +77,29 @@ typedef struct gs_opts {
     const float *selector_params;  /* GS_SEL_MLP: DEVICE array of GS_MLP_NPARAM floats (the
                                pair-selector network, see gs_mlp_train); read during the
                                call; required for GS_SEL_MLP, ignored otherwise        */
-    int64_t reserved[3];
+    double  small_work;     /* GS_FLAG_SMALL_EXHAUSTIVE threshold on M N nh; 0 -> GS_SMALL_WORK */
+    int64_t reserved[2];
 } gs_opts;
 
 /* gs_opts.flags */
 #define GS_FLAG_NO_MERGE 1  /* base case per bandwidth, without merging the leaf pairs
                                that several bandwidths share                           */
 #define GS_FLAG_SMALL_EXHAUSTIVE 2  /* eps > 0 problems whose exhaustive work M N nh is at
-                               most GS_SMALL_WORK are summed exhaustively (their error,
+                               most gs_opts.small_work (0: GS_SMALL_WORK, or GS_SMALL_WORK_D2
+                               for D <= 2) are summed exhaustively (their error,
                                about 1e-5, is within eps).  GS_SMALL_WORK = 2^39 is the
                                crossover measured on GB300 for D = 3: 1e5 points x 16
                                bandwidths (1.6e11 terms) take 21 ms exhaustively and 35 ms
                                by the dual tree; 1e6 points x 16 (1.6e13) take 2.1 s and
                                1.1 s.  In higher D the crossover is later still.        */
 #define GS_SMALL_WORK 549755813888.0
+#define GS_SMALL_WORK_D2 68719476736.0  /* the same threshold for D <= 2 (2^36), where the tree
+                               prunes best: measured per problem on 256 uneven batch problems
+                               (8 bandwidths from 1e-3 to 1 times the diameter, eps 1e-2),
+                               the dual tree wins from about 4e10 terms in D = 2 (1e5 points:
+                               7.4 ms against 12.7 ms exhaustively; 2e5: 14.3 against 42.8) and
+                               loses up to 2e5 points for every D >= 3 (D = 8, 1.3e5 points:
+                               79 ms against 23 ms)                                    */
 #define GS_FLAG_NO_TC 4     /* 9 <= D <= 16: no tensor-core base case (every leaf pair summed
                                by the direct FP32 kernel; the FP32 charge drops its extra
                                tensor-core term)                                         */

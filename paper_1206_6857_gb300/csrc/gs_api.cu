@@ -309,8 +309,9 @@ int gs::sum_impl(const void *queries, int64_t M, const void *refs, const float *
     }
     if (stats) memset(stats, 0, sizeof(*stats));
     cudaStream_t st = (cudaStream_t)stream;
+    const double small_work = o.small_work > 0.0 ? o.small_work : (D <= 2 ? GS_SMALL_WORK_D2 : GS_SMALL_WORK);
     const bool exhaustive = eps == 0.0 || ((o.flags & GS_FLAG_SMALL_EXHAUSTIVE) && !trace && !log &&
-                                           (double)M * (double)N * (double)nh <= GS_SMALL_WORK);
+                                           (double)M * (double)N * (double)nh <= small_work);
 
     CallCtx cx;
     cx.st = st;

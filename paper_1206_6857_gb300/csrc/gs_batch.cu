@@ -39,10 +39,12 @@ extern "C" int gs_sum_batched(int nprob, const gs_problem *probs, const gs_opts 
     cudaStream_t caller = (cudaStream_t)stream;
     // exhaustive problems the grouped path takes; the rest, largest first (M N nh)
     const bool small_ex = opts && (opts->flags & GS_FLAG_SMALL_EXHAUSTIVE);
+    const double small_work = opts && opts->small_work > 0.0 ? opts->small_work : 0.0;   // 0: by D
     std::vector<int> grouped, order;
     for (int i = 0; i < nprob; ++i) {
         const gs_problem &p = probs[i];
-        const bool exh = p.eps == 0.0 || (small_ex && (double)p.M * (double)p.N * (double)p.nh <= GS_SMALL_WORK);
+        const double sw = small_work > 0.0 ? small_work : (p.D <= 2 ? GS_SMALL_WORK_D2 : GS_SMALL_WORK);
+        const bool exh = p.eps == 0.0 || (small_ex && (double)p.M * (double)p.N * (double)p.nh <= sw);
         if (exh && exhaustive_groupable(p) &&
             check_common(p.queries, p.M, p.refs, p.weights, p.N, p.D, p.dtype, p.h, p.nh, p.eps, p.out) == GS_OK)
             grouped.push_back(i);

@@ -39,6 +39,7 @@ GS_FLAG_SMALL_EXHAUSTIVE = 2
 GS_FLAG_NO_TC = 4
 GS_FLAG_BEST_FIRST = 8
 GS_SMALL_WORK = 549755813888.0
+GS_SMALL_WORK_D2 = 68719476736.0
 
 GS_MLP_NIN = 12
 GS_MLP_NOUT = 5
@@ -50,7 +51,8 @@ class gs_opts(ctypes.Structure):
                 ("selector", ctypes.c_int32), ("no_tokens", ctypes.c_int32),
                 ("floor_log2", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("pair_capacity", ctypes.c_int64), ("cost_weight", ctypes.c_double * 4),
-                ("selector_params", ctypes.c_void_p), ("reserved", ctypes.c_int64 * 3)]
+                ("selector_params", ctypes.c_void_p), ("small_work", ctypes.c_double),
+                ("reserved", ctypes.c_int64 * 2)]
 
 
 GS_PH_INGEST, GS_PH_TREE, GS_PH_FRONTIER, GS_PH_SERIES, GS_PH_BASE, GS_PH_DOWN, GS_PH_OTHER, GS_PH_BASE_TC = range(8)

@@ -133,3 +133,23 @@ def test_grouped_exhaustive_problems(gs):
     with pytest.raises(gs.GSError) as ei:
         gs.gs_sum_batched(bad, opts=o, nworkers=4)
     assert ei.value.code == gs.GS_ERR_WEIGHT and "problem 7" in str(ei.value)
+
+
+def test_small_work_threshold_depends_on_dimension(gs):
+    """GS_FLAG_SMALL_EXHAUSTIVE: a two-dimensional problem above
+    GS_SMALL_WORK_D2 takes the dual tree, a three-dimensional one of the same
+    size the exhaustive sum (below GS_SMALL_WORK); both within eps."""
+    n, nh = 100000, 8
+    assert gs.GS_SMALL_WORK_D2 < float(n) * n * nh <= gs.GS_SMALL_WORK
+    for D, traversal in ((2, True), (3, False)):
+        x, _, w = synth.small_random(70 + D, n, D)
+        h = synth.log_bandwidths(synth.bbox_diagonal(x), nh)
+        o = gs.gs_opts_default()
+        o.flags = gs.GS_FLAG_SMALL_EXHAUSTIVE
+        st = gs.gs_stats()
+        tx = _dev(x)
+        out = gs.gs_sum(tx, tx, _dev(w), h, 1e-2, opts=o, stats=st).cpu().numpy()
+        assert (st.pairs_split > 0) == traversal, st.as_dict()
+        idx = np.random.default_rng(D).choice(n, 200, replace=False)
+        exact = oracle_ex.gauss_sum(x[idx], x, w, h)
+        assert rel_err(out[idx], exact, float(w.astype(np.float64).sum())).max() <= 1e-2
