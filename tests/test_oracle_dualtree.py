@@ -285,3 +285,26 @@ def test_summation_charge_covers_adversarial_runs(run):
     assert rel <= charge
     if run == 128:
         assert rel > 64.0 * u
+
+
+@pytest.mark.parametrize("D,n,m,leaf", [(2, 1500, None, 16), (3, 1200, 700, 8), (5, 900, None, 32)])
+def test_pairs_per_iteration_within_the_reserved_lists(D, n, m, leaf):
+    """Small traversals reserve their work lists once, at the worst case: the
+    pairs of iteration t are distinct (query node, reference node, bandwidth)
+    triples of levels min(t, depth), at most nh 2^min(t, d_Q) 2^min(t, d_R) of
+    them, and each action list holds at most the sum of that over the
+    iterations (checked on the CPU traversal, which the GPU one reproduces)."""
+    q, r, w, mono = _problem(50 + D, n, D, m)
+    qt, rt = _trees(q, r, w, mono, leaf)
+    h = synth.log_bandwidths(synth.bbox_diagonal(r), 4, 1e-3, 1.0)
+    trav = T.traverse(qt, rt, mono, h, 1e-2, w_max=float(w.max()), cost_weight=(1, 1, 1, 1))
+    total, counts = 0, {}
+    for t, it in enumerate(trav.iters):
+        bound = h.size << (min(t, qt.depth) + min(t, rt.depth))
+        trip = set(zip(it["q"].tolist(), it["r"].tolist(), it["j"].tolist()))
+        assert len(trip) == len(it["q"]) <= bound
+        total += bound
+        for mth in (T.DH, T.DL, T.H2L, T.BASE):
+            counts[mth] = counts.get(mth, 0) + int(np.sum(it["method"] == mth))
+    assert all(c <= total for c in counts.values())
+    assert counts[T.BASE] > 0
