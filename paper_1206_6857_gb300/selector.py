@@ -205,7 +205,7 @@ def _collect(problems, factors=(1.0, 1.0, 1.0)):
     return torch.cat(xs), torch.cat(ys), torch.cat(ss), info
 
 
-def main(epochs=40, rounds=2, out=PARAMS_FILE):
+def main(epochs=40, rounds=4, out=PARAMS_FILE):
     """Collect samples from the training problems, train, store the network.
 
     The first pass takes the series unit costs measured on the rule's own actions.
