@@ -220,9 +220,28 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 constexpr int kBlk = 8;   // bandwidths accumulated per pass
 
+// shared memory a CTA can use on one SM (228 KB, less 1 KB reserved per CTA
+// at three CTAs)
+constexpr size_t kSmemPerSm = 225 * 1024;
+
+// staging buffers per warp: two unless two would leave fewer than three CTAs
+// per SM at leaves of 32 QPL points (the shape the launch takes for
+// monochromatic data)
+__host__ __device__ constexpr int merged_nbuf(int DP, int QPL) {
+    return 3 * (size_t)kMW *
+                       (2 * kBlk * QPL * 32 +
+                        2 * 32 * QPL * (merged_x2(DP, QPL) ? 2 : 1) * (((DP + 1) * 4 + 15) / 16 * 4)) *
+                       sizeof(float) >
+                   kSmemPerSm
+               ? 1
+               : 2;
+}
+
 // Shared memory per warp: Kahan sums and compensations for one block of
-// kBlk bandwidths (2 x kBlk x QPL x 32 floats), then two staging buffers of
-// lmax reference records each.  Mask bits are bandwidths in ascending h, so
+// kBlk bandwidths (2 x kBlk x QPL x 32 floats), then nbuf staging buffers of
+// lmax reference records each (two: the next leaf is copied while this one is
+// summed; one, where two would leave fewer than three CTAs per SM: the next
+// leaf is copied after this one).  Mask bits are bandwidths in ascending h, so
 // the bandwidths a leaf pair needs are consecutive; the CTA makes one pass
 // over its entries per block of kBlk bandwidths, blocks starting at the
 // lowest bandwidth any of its entries needs.
@@ -232,6 +251,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                   int64_t lq, int lmax) {
     constexpr int NT = RefRec<float, DP>::NT;
     constexpr bool X2 = merged_x2(DP, QPL);
+    constexpr int nbuf = merged_nbuf(DP, QPL);
     constexpr int NS = X2 ? 2 * NT : NT;   // floats per staged reference record
     constexpr int KS = kBlk * QPL * 32;
     extern __shared__ float sm_f[];
@@ -240,10 +260,10 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
     const int64_t e0 = off[i], e1 = off[i + 1];
     if (e0 == e1) return;
     const int nh = bp.nh;
-    const size_t per_warp = (size_t)2 * KS + (size_t)2 * lmax * NS;
+    const size_t per_warp = (size_t)2 * KS + (size_t)nbuf * lmax * NS;
     float *ksum = sm_f + (size_t)w * per_warp;
     float *kcmp = ksum + KS;
-    float *stage = ksum + 2 * KS;   // 2 x lmax x NT floats, 16-byte aligned
+    float *stage = ksum + 2 * KS;   // nbuf x lmax x NS floats, 16-byte aligned
     const int64_t qleaf0 = (1ll << bp.q_depth) - 1, rleaf0 = (1ll << bp.r_depth) - 1;
     const int64_t qnode = qleaf0 + i;
     const int64_t qb = level_begin(bp.qn, bp.q_depth, i), qe = level_begin(bp.qn, bp.q_depth, i + 1);
@@ -295,7 +315,7 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
         if (e < e1) stage_leaf(e, 0);
         while (e < e1) {
             const int64_t en = next_used(e + kMW);
-            if (en < e1) {
+            if (nbuf == 2 && en < e1) {   // a compile-time test
                 stage_leaf(en, buf ^ 1);
                 cp_async_wait<1>();
             } else {
@@ -373,7 +393,10 @@ k_basecase_merged(MergedParams bp, const MergedEntry *__restrict__ ent, const lo
                 }
             }
             __syncwarp();   // everyone is done with this buffer before it is refilled
-            buf ^= 1;
+            if constexpr (nbuf == 2)
+                buf ^= 1;
+            else if (en < e1)
+                stage_leaf(en, 0);
             e = en;
         }
         __syncthreads();
@@ -402,7 +425,8 @@ static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const Me
 #define GS_M(Q, A)                                                                                  \
     do {                                                                                            \
         const size_t ns = merged_x2(DP, Q) ? 2 * NT : NT;                                            \
-        const size_t sm = (size_t)kMW * (2 * kBlk * (Q) * 32 + 2 * lmax * ns) * sizeof(float);     \
+        const size_t sm =                                                                           \
+            (size_t)kMW * (2 * kBlk * (Q) * 32 + merged_nbuf(DP, Q) * lmax * ns) * sizeof(float);    \
         if (sm > 220 * 1024) return GS_ERR_UNSUPPORTED;                                             \
         allow_max_smem((const void *)k_basecase_merged<DP, Q, A>);                                   \
         k_basecase_merged<DP, Q, A><<<(unsigned)lq, 32 * kMW, sm, st>>>(bp, ent, off, lq, lmax);    \
@@ -421,7 +445,7 @@ static int launch_merged_dp(int qpl, bool anch, const MergedParams &bp, const Me
 static size_t merged_smem(int DP, int NT, int qpl, int lmax) {
     const int Q = qpl <= 1 ? 1 : (qpl <= 2 ? 2 : 4);
     const size_t ns = merged_x2(DP, Q) ? 2 * NT : NT;
-    return (size_t)kMW * (2 * kBlk * Q * 32 + 2 * lmax * ns) * sizeof(float);
+    return (size_t)kMW * (2 * kBlk * Q * 32 + merged_nbuf(DP, Q) * lmax * ns) * sizeof(float);
 }
 
 static void merged_shape(const TraversalIn &in, int &qpl, int &lmax) {
