@@ -77,7 +77,8 @@ typedef struct gs_opts {
     const float *selector_params;  /* GS_SEL_MLP: DEVICE array of GS_MLP_NPARAM floats (the
                                pair-selector network, see gs_mlp_train); read during the
                                call; required for GS_SEL_MLP, ignored otherwise        */
-    double  small_work;     /* GS_FLAG_SMALL_EXHAUSTIVE threshold on M N nh; 0 -> GS_SMALL_WORK */
+    double  small_work;     /* GS_FLAG_SMALL_EXHAUSTIVE threshold on M N nh; 0 -> GS_SMALL_WORK,
+                               or GS_SMALL_WORK_D2 when D <= 2                          */
     int64_t reserved[2];
 } gs_opts;
 

@@ -81,3 +81,24 @@ def test_tree_argument_checks(gs):
     assert ei.value.code == gs.GS_ERR_WEIGHT
     for t in (qtree, rtree, other):
         t.close()
+
+
+@pytest.mark.parametrize("n,D,m,dtype,leaf", [(40000, 3, None, np.float32, 32), (70000, 2, 20000, np.float64, 64)])
+def test_tree_levels_across_the_per_node_threshold(gs, n, D, m, dtype, leaf):
+    """Trees whose upper levels hold nodes of more than 16384 points (built by
+    the device-wide level kernels) and whose lower levels are built one CTA
+    per node: the permutations equal the CPU tree's bit for bit."""
+    from oracle import dualtree as T
+    q, r, w = synth.small_random(60 + D, n, D, m=m, dtype=dtype)
+    mono = m is None
+    tr = _dev(r)
+    tq = tr if mono else _dev(q)
+    o = gs.gs_opts_default()
+    o.leaf_size = leaf
+    h = np.array([4.0 * synth.bbox_diagonal(r)])       # everything pruned near the root
+    _, _, qperm, rperm = gs.gs_sum_trace(tq, tr, _dev(w), h, 1e-2, opts=o, trace_cap=1 << 16)
+    rt = T.build_tree(r, w, leaf)
+    assert np.array_equal(rperm.cpu().numpy(), rt.perm)
+    if not mono:
+        qt = T.build_tree(q, np.ones(q.shape[0], np.float32), leaf)
+        assert np.array_equal(qperm.cpu().numpy(), qt.perm)
